@@ -1,0 +1,266 @@
+"""FP64 CPU oracle for the BMND two-stage denoiser (ctypes binding).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path; the library it loads is compiled from ``bmnd_oracle.c`` in
+this folder (see :func:`build`).
+
+Every function follows the paper's definitions in double precision; the C file
+names the definition, equation or proposition each step follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bmnd_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+MAXD = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (OpenMP, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("shape", ctypes.c_int64 * MAXD),
+        ("patch", ctypes.c_int * MAXD),
+        ("step", ctypes.c_int * MAXD),
+        ("search", ctypes.c_int * MAXD),
+        ("noise_kind", ctypes.c_int),
+        ("sigma", ctypes.c_double),
+        ("s_p", ctypes.c_double),
+        ("group_max", ctypes.c_int * 2),
+        ("stages", ctypes.c_int),
+        ("mass_conserve", ctypes.c_int),
+        ("lambda_ht", ctypes.c_double),
+        ("gamma_ht", ctypes.c_double),
+        ("gamma_wie", ctypes.c_double),
+        ("tau_ht", ctypes.c_double),
+        ("tau_wie", ctypes.c_double),
+        ("s_v", ctypes.c_double),
+        ("kaiser_beta", ctypes.c_double),
+        ("shift_density", ctypes.c_double),
+        ("passes", ctypes.c_int),
+        ("schedule", ctypes.c_int),
+        ("power_mode", ctypes.c_int),
+        ("group_transform", ctypes.c_int),
+        ("min_group", ctypes.c_int),
+        ("weight_model", ctypes.c_int),
+        ("weight_scope", ctypes.c_int),
+    ]
+
+
+SCHEDULES = {"generated": 0, "off": 1, "sparse": 2, "balanced": 3}
+POWER_MODES = {"classic": 0, "noise_floor": 1, "variance_scaled": 2}
+GROUP_TRANSFORMS = {"haar": 0, "dct": 1}
+WEIGHT_MODELS = {"classic": 0, "variance": 1, "risk": 2}
+WEIGHT_SCOPES = {"patch": 0, "group": 1}
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, i64 = P(ctypes.c_double), P(ctypes.c_int64)
+        _lib.or_schedule.argtypes = [P(_Params), i64, ctypes.c_int64]
+        _lib.or_schedule.restype = ctypes.c_int64
+        _lib.or_match_ref.argtypes = [P(_Params), d, ctypes.c_int, ctypes.c_int64, ctypes.c_int, i64, d]
+        _lib.or_match_ref.restype = ctypes.c_int
+        _lib.or_stage.argtypes = [P(_Params), d, d, ctypes.c_int, d, d, i64, P(ctypes.c_int), ctypes.c_int]
+        _lib.or_stage.restype = ctypes.c_int64
+        _lib.or_denoise.argtypes = [P(_Params), d, d, d]
+        _lib.or_stage_points.argtypes = [P(_Params), d, d, ctypes.c_int, ctypes.c_int64, i64, d]
+        _lib.or_filter_group.argtypes = [P(_Params), ctypes.c_int, d, d, ctypes.c_int, i64, d, d, d, d, d]
+        _lib.or_group_transform.argtypes = [P(_Params), ctypes.c_int, d, ctypes.c_int]
+        _lib.or_dct_matrix.argtypes = [ctypes.c_int, d]
+        _lib.or_haar_matrix.argtypes = [ctypes.c_int, d]
+        _lib.or_kaiser.argtypes = [ctypes.c_int, ctypes.c_double, d]
+        _lib.or_bessel_i0.argtypes = [ctypes.c_double]
+        _lib.or_bessel_i0.restype = ctypes.c_double
+        _lib.or_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 32), stages=2,
+           mass_conserve=0, **kw) -> _Params:
+    """Build the parameter block.  Defaults are the standard configuration of
+    App. A (generated schedule with shift density 2 and 2 passes, lambda_HT = 3,
+    gamma_HT = 3, s_v = 0.4, Kaiser beta = 2, minimum group 2, variance
+    weights in patch scope, Haar along the group axis, DCT on the patch axes)."""
+    D = len(shape)
+    if D > MAXD:
+        raise ValueError("oracle supports up to %d axes" % MAXD)
+    p = _Params()
+    p.ndim = D
+    for a in range(D):
+        p.shape[a] = int(shape[a])
+        p.patch[a] = int(patch[a])
+        p.step[a] = int(step[a])
+        p.search[a] = int(search[a])
+    kind, val = noise
+    if kind == "gaussian":
+        p.noise_kind, p.sigma, p.s_p = 0, float(val), 1.0
+    elif kind == "poisson":
+        p.noise_kind, p.sigma, p.s_p = 1, 0.0, float(val)
+    else:
+        raise ValueError(kind)
+    p.group_max[0], p.group_max[1] = int(group_size[0]), int(group_size[1])
+    p.stages = int(stages)
+    p.mass_conserve = int(mass_conserve)
+    p.lambda_ht = kw.pop("lambda_ht", 3.0)
+    p.gamma_ht = kw.pop("gamma_ht", 3.0)
+    p.gamma_wie = kw.pop("gamma_wie", 0.0)
+    p.tau_ht = kw.pop("tau_ht", 0.0)
+    p.tau_wie = kw.pop("tau_wie", 0.0)
+    p.s_v = kw.pop("s_v", 0.4)
+    p.kaiser_beta = kw.pop("kaiser_beta", 2.0)
+    p.shift_density = kw.pop("shift_density", 2.0)
+    p.passes = kw.pop("passes", 2)
+    p.schedule = SCHEDULES[kw.pop("schedule", "generated")]
+    p.power_mode = POWER_MODES[kw.pop("power_mode", "classic")]
+    p.group_transform = GROUP_TRANSFORMS[kw.pop("group_transform", "haar")]
+    p.min_group = kw.pop("min_group", 2)
+    p.weight_model = WEIGHT_MODELS[kw.pop("weight_model", "variance")]
+    p.weight_scope = WEIGHT_SCOPES[kw.pop("weight_scope", "patch")]
+    if kw:
+        raise TypeError("unknown oracle parameters: %s" % sorted(kw))
+    return p
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def schedule(p: _Params) -> np.ndarray:
+    lib = _load()
+    n = lib.or_schedule(ctypes.byref(p), None, 0)
+    out = np.empty(n, np.int64)
+    lib.or_schedule(ctypes.byref(p), _iptr(out), n)
+    return out
+
+
+def match_ref(p: _Params, guide, stage: int, ref_lin: int):
+    lib = _load()
+    g = _f64(guide).ravel()
+    M = p.group_max[stage - 1]
+    mem = np.empty(64, np.int64)
+    sc = np.empty(64, np.float64)
+    n = lib.or_match_ref(ctypes.byref(p), _dptr(g), stage, int(ref_lin), M, _iptr(mem), _dptr(sc))
+    return mem[:n].copy(), sc[:n].copy()
+
+
+def stage(p: _Params, y, pilot, stage: int, want_den=False, want_groups=False):
+    lib = _load()
+    yy = _f64(y).ravel()
+    pl = _f64(pilot).ravel() if pilot is not None else None
+    out = np.empty_like(yy)
+    den = np.empty_like(yy) if want_den else None
+    R = lib.or_schedule(ctypes.byref(p), None, 0)
+    gmax = p.group_max[stage - 1]
+    groups = np.empty((R, gmax), np.int64) if want_groups else None
+    counts = np.empty(R, np.int32) if want_groups else None
+    lib.or_stage(ctypes.byref(p), _dptr(yy), _dptr(pl) if pl is not None else None, stage, _dptr(out),
+                 _dptr(den) if den is not None else None,
+                 _iptr(groups) if groups is not None else None,
+                 counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if counts is not None else None,
+                 gmax)
+    shape = np.asarray(y).shape
+    res = [out.reshape(shape)]
+    if want_den:
+        res.append(den.reshape(shape))
+    if want_groups:
+        res += [groups, counts]
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def denoise(p: _Params, y):
+    """Both stages; returns (estimate, stage-1 pilot)."""
+    lib = _load()
+    yy = _f64(y).ravel()
+    out = np.empty_like(yy)
+    pilot = np.empty_like(yy)
+    lib.or_denoise(ctypes.byref(p), _dptr(yy), _dptr(out), _dptr(pilot))
+    shape = np.asarray(y).shape
+    return out.reshape(shape), pilot.reshape(shape)
+
+
+def stage_points(p: _Params, y, pilot, stage: int, points_lin):
+    lib = _load()
+    yy = _f64(y).ravel()
+    pl = _f64(pilot).ravel() if pilot is not None else None
+    pts = np.ascontiguousarray(points_lin, dtype=np.int64)
+    out = np.empty(len(pts), np.float64)
+    lib.or_stage_points(ctypes.byref(p), _dptr(yy), _dptr(pl) if pl is not None else None, stage,
+                        len(pts), _iptr(pts), _dptr(out))
+    return out
+
+
+def filter_group(p: _Params, stage: int, y, pilot, members):
+    lib = _load()
+    yy = _f64(y).ravel()
+    pl = _f64(pilot).ravel() if pilot is not None else None
+    mem = np.ascontiguousarray(members, dtype=np.int64)
+    n = len(mem)
+    P = int(np.prod([p.patch[a] for a in range(p.ndim)]))
+    Y, var, C, pt = (np.empty(n * P) for _ in range(4))
+    w = np.empty(n)
+    lib.or_filter_group(ctypes.byref(p), stage, _dptr(yy), _dptr(pl) if pl is not None else None, n,
+                        _iptr(mem), _dptr(Y), _dptr(var), _dptr(C), _dptr(pt), _dptr(w))
+    sh = (n, P)
+    return dict(Y=Y.reshape(sh), var=var.reshape(sh), C=C.reshape(sh), p=pt.reshape(sh), w=w)
+
+
+def group_transform(p: _Params, x, mode: int = 0):
+    """mode 0: T x, 1: T^T x, 2: (T.^2) x for a group tensor x of shape
+    (count, *patch)."""
+    lib = _load()
+    a = _f64(x).copy()
+    lib.or_group_transform(ctypes.byref(p), a.shape[0], _dptr(a), mode)
+    return a
+
+
+def dct_matrix(n: int) -> np.ndarray:
+    a = np.empty(n * n)
+    _load().or_dct_matrix(n, _dptr(a))
+    return a.reshape(n, n)
+
+
+def haar_matrix(n: int) -> np.ndarray:
+    a = np.empty(n * n)
+    _load().or_haar_matrix(n, _dptr(a))
+    return a.reshape(n, n)
+
+
+def kaiser(n: int, beta: float) -> np.ndarray:
+    a = np.empty(n)
+    _load().or_kaiser(n, beta, _dptr(a))
+    return a
+
+
+def bessel_i0(x: float) -> float:
+    return _load().or_bessel_i0(x)
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()

@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+library routines (scipy DCT, numpy Kaiser, scipy Bessel I0), hand-derived values,
+closed forms stated in the paper, brute force on tiny inputs, Monte-Carlo checks
+of the variance propagation lemma, and invariants (orthonormality, identity at
+zero threshold, mass conservation, N-D consistency).
+
+Each test names the passage it pins.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.special
+
+from paper_2609_34622_b300 import synth
+
+
+# ---------------------------------------------------------------------------
+# transforms
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 11, 16, 32])
+def test_dct_matrix_matches_scipy(oracle, n):
+    """Orthonormal DCT-II (App. A spatial transform) equals scipy's dct(norm='ortho')."""
+    ref = scipy.fft.dct(np.eye(n), type=2, norm="ortho", axis=0)
+    np.testing.assert_allclose(oracle.dct_matrix(n), ref, atol=1e-14)
+
+
+def test_haar_hand_values(oracle):
+    """Haar group transform (App. A): hand-written 1-, 2- and 4-point orthonormal Haar."""
+    s = 1 / math.sqrt(2)
+    np.testing.assert_allclose(oracle.haar_matrix(1), [[1.0]])
+    np.testing.assert_allclose(oracle.haar_matrix(2), [[s, s], [s, -s]], atol=1e-15)
+    h4 = np.array([[0.5, 0.5, 0.5, 0.5], [0.5, 0.5, -0.5, -0.5], [s, -s, 0, 0], [0, 0, s, -s]])
+    np.testing.assert_allclose(oracle.haar_matrix(4), h4, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64])
+def test_haar_orthonormal_and_dyadic(oracle, n):
+    H = oracle.haar_matrix(n)
+    np.testing.assert_allclose(H @ H.T, np.eye(n), atol=1e-13)
+    # every detail row is constant on the two halves of one dyadic block
+    for row in H[1:]:
+        nz = np.nonzero(row)[0]
+        b = len(nz)
+        assert b & (b - 1) == 0 and nz[0] % b == 0 and nz[-1] == nz[0] + b - 1
+        np.testing.assert_allclose(row[nz[: b // 2]], 1 / math.sqrt(b))
+        np.testing.assert_allclose(row[nz[b // 2:]], -1 / math.sqrt(b))
+
+
+@pytest.mark.parametrize("n,beta", [(1, 2.0), (4, 2.0), (8, 2.0), (32, 2.0), (5, 0.5), (9, 6.0)])
+def test_kaiser_matches_numpy(oracle, n, beta):
+    """Kaiser aggregation window (App. A, beta = 2) equals numpy.kaiser."""
+    np.testing.assert_allclose(oracle.kaiser(n, beta), np.kaiser(n, beta), rtol=1e-13)
+
+
+def test_bessel_i0_matches_scipy(oracle):
+    for x in [0.0, 0.3, 1.0, 2.0, 5.5, 12.0]:
+        assert oracle.bessel_i0(x) == pytest.approx(scipy.special.i0(x), rel=1e-14)
+
+
+def _full_T(oracle, count, patch, group_transform="haar"):
+    """Full matrix of the group transform, built with numpy.kron from matrices
+    that come from scipy (DCT) and from the hand-checked Haar."""
+    A0 = scipy.fft.dct(np.eye(count), norm="ortho", axis=0) if group_transform == "dct" \
+        else oracle.haar_matrix(count)
+    T = A0
+    for j in patch:
+        T = np.kron(T, scipy.fft.dct(np.eye(j), norm="ortho", axis=0))
+    return T
+
+
+@pytest.mark.parametrize("count,patch,gt", [(4, (3, 2), "haar"), (2, (4,), "haar"), (3, (2, 2, 2), "dct"),
+                                            (8, (2, 3), "haar"), (1, (5,), "haar")])
+def test_group_transform_is_kronecker_and_orthonormal(oracle, count, patch, gt):
+    """Patch-group observation model: T = (group axis) (x) DCT_j0 (x) ...;
+    T T^T = I, mode 1 inverts, mode 2 is the entrywise square (the factor of
+    Eq. transformed-coefficient-variance for diagonal covariance)."""
+    D = len(patch)
+    p = oracle.params(tuple(4 * j for j in patch), patch, (1,) * D, (3,) * D, group_transform=gt)
+    d = count * int(np.prod(patch))
+    E = np.eye(d).reshape((d, count) + patch)
+    Tcols = np.stack([oracle.group_transform(p, E[i], 0).ravel() for i in range(d)], axis=1)
+    T = _full_T(oracle, count, patch, gt)
+    np.testing.assert_allclose(Tcols, T, atol=1e-13)
+    np.testing.assert_allclose(T @ T.T, np.eye(d), atol=1e-13)
+    x = np.random.default_rng(1).normal(size=(count,) + patch)
+    y = oracle.group_transform(p, x, 0)
+    np.testing.assert_allclose(oracle.group_transform(p, y, 1), x, atol=1e-13)
+    np.testing.assert_allclose(oracle.group_transform(p, x, 2).ravel(), (T * T) @ x.ravel(), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# reference schedule (Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def test_shift_list_example_2d(oracle):
+    """Eq. number-shifts / candidate-shift-list for j = 8, h = 3, rho_s = 2 give
+    n = ceil(2*7/3) = 5 and S = (0, 2, 4, 5, 7) (hand derived).  Under the
+    generated schedule axis 0 is shifted by S[(q_1 + k) mod 5], so an interior
+    axis-0 slot q_0 (nominal 3 q_0) yields exactly the origins 3 q_0 - S."""
+    p = oracle.params((64, 64), (8, 8), (3, 3), (19, 19))
+    R = oracle.schedule(p)
+    r0, r1 = R // 64, R % 64
+    S = (0, 2, 4, 5, 7)
+    for q1 in range(5, 12):
+        # the last axis is unshifted: column r1 = 3 q1 holds slot q1's origins
+        col = sorted(r0[(r1 == 3 * q1) & (r0 >= 12) & (r0 <= 36)].tolist())
+        expect = sorted({3 * q0 - S[(q1 + k) % 5] for q0 in range(0, 20) for k in (0, 1)} & set(range(12, 37)))
+        assert col == expect, (q1, col, expect)
+
+
+def test_off_schedule_1d_lattice(oracle):
+    """Def. off reference schedule: 0, h, 2h, ..., l, with l appended.  In 1-D
+    the generated schedule leaves its only (last) axis unshifted, so it gives
+    the same lattice."""
+    L, j, h = 100, 8, 3
+    ell = L - j
+    expect = list(range(0, ell + 1, h))
+    if expect[-1] != ell:
+        expect.append(ell)
+    for sched in ("off", "generated"):
+        p = oracle.params((L,), (j,), (h,), (9,), schedule=sched)
+        assert oracle.schedule(p).tolist() == expect
+
+
+@pytest.mark.parametrize("shape,patch,step,sched", [
+    ((64, 64), (8, 8), (3, 3), "generated"), ((37, 29), (5, 4), (3, 2), "generated"),
+    ((20, 18, 16), (4, 4, 4), (2, 2, 2), "generated"), ((37, 29), (5, 4), (3, 2), "balanced"),
+    ((1, 40, 17), (1, 6, 5), (1, 4, 3), "sparse"), ((23, 31), (6, 6), (4, 5), "off")])
+def test_schedule_valid_and_covering(oracle, shape, patch, step, sched):
+    """Clipped reference origin: every origin is valid, the far boundary l_d is
+    reached on every axis, there are at most K_s prod Z_d distinct origins,
+    and the reference patches cover the whole array (steps <= patch sizes)."""
+    p = oracle.params(shape, patch, step, (3,) * len(shape), schedule=sched)
+    R = oracle.schedule(p)
+    coords = np.stack(np.unravel_index(R, shape), axis=1)
+    ell = np.array(shape) - np.array(patch)
+    assert (coords >= 0).all() and (coords <= ell).all()
+    assert len(np.unique(R)) == len(R) and (np.diff(R) > 0).all()
+    for d in range(len(shape)):
+        assert (coords[:, d] == ell[d]).any() and (coords[:, d] == 0).any()
+    Z = [math.ceil(e / h) + 1 for e, h in zip(ell, step)]
+    assert len(R) <= 2 * int(np.prod(Z))
+    cov = np.zeros(shape, np.int32)
+    for c in coords:
+        cov[tuple(slice(int(a), int(a) + j) for a, j in zip(c, patch))] += 1
+    assert (cov > 0).all()
+
+
+def test_generated_vs_sparse_singleton(oracle):
+    """Sparse schedule (Def.): singleton axes leave the hierarchy.  With a
+    leading singleton axis both schedules coincide with the 1-D lattice; the
+    survey reading notes that a trailing singleton axis changes the generated
+    schedule but not the sparse one."""
+    L = 50
+    p1 = oracle.params((L,), (6,), (4,), (9,))
+    base = oracle.schedule(p1).tolist()
+    for sched in ("generated", "sparse"):
+        p = oracle.params((1, L), (1, 6), (1, 4), (1, 9), schedule=sched)
+        assert oracle.schedule(p).tolist() == base
+    p = oracle.params((L, 1), (6, 1), (4, 1), (9, 1), schedule="sparse")
+    assert oracle.schedule(p).tolist() == base
+
+
+# ---------------------------------------------------------------------------
+# block matching (Sec. 4.2, 4.4; App. A group rules), brute force
+# ---------------------------------------------------------------------------
+
+def _brute_match(y, ref, patch, search, noise, gamma, tau, M, min_group=2, pow2=True):
+    """Independent numpy brute force: score every origin in the clipped window."""
+    shape = y.shape
+    ell = [L - j for L, j in zip(shape, patch)]
+    rad = [(w - 1) // 2 for w in search]
+    pref = y[tuple(slice(r, r + j) for r, j in zip(ref, patch))].astype(np.float64)
+    cands = []
+    ranges = [range(max(r - a, 0), min(r + a, e) + 1) for r, a, e in zip(ref, rad, ell)]
+    for c in itertools.product(*ranges):
+        if tuple(c) == tuple(ref):
+            continue
+        q = y[tuple(slice(a, a + j) for a, j in zip(c, patch))].astype(np.float64)
+        ssd = float(((q - pref) ** 2).sum())
+        if noise[0] == "poisson":
+            B = noise[1] * float(np.maximum(q + pref, 0).sum())
+        else:
+            B = 2 * pref.size * noise[1] ** 2
+        s = ssd - gamma * B if gamma > 0 else ssd
+        cands.append((s, int(np.ravel_multi_index(c, shape))))
+    cands.sort()
+    nacc = sum(1 for s, _ in cands if s < tau)
+    take = min(nacc, M - 1)
+    if 1 + take < min_group:
+        take = min(min_group - 1, M - 1, len(cands))
+    cnt = 1 + take
+    if pow2:
+        cnt = 1 << (cnt.bit_length() - 1)
+    return [int(np.ravel_multi_index(tuple(ref), shape))] + [l for _, l in cands[: cnt - 1]]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_matching_brute_force(oracle, case):
+    rng = np.random.default_rng(10 + case)
+    # dyadic data (counts times 2^-k, or multiples of 1/64) keep every score
+    # exact in double precision, so exact ties are broken by the index rule
+    # on both sides rather than by summation order
+    if case == 0:
+        shape, patch, search, noise, M = (12, 12), (3, 3), (5, 5), ("poisson", 0.25), 8
+    elif case == 1:
+        shape, patch, search, noise, M = (16,), (4,), (7,), ("poisson", 0.5), 4
+    elif case == 2:
+        shape, patch, search, noise, M = (6, 6, 6), (2, 2, 2), (3, 3, 3), ("poisson", 0.25), 16
+    else:
+        shape, patch, search, noise, M = (12, 10), (3, 2), (7, 5), ("gaussian", 0.125), 8
+    x = rng.uniform(0.2, 1.0, size=shape)
+    if noise[0] == "poisson":
+        y = rng.poisson(x / noise[1]) * noise[1]
+    else:
+        y = np.round(64 * (x + rng.normal(0, noise[1], shape))) / 64
+    for stage in (1, 2):
+        for tau in (0.0, 0.05, 1e9):
+            p = oracle.params(shape, patch, (1,) * len(shape), search, noise, (M, M),
+                              tau_ht=tau if tau > 0 else 1e-300, tau_wie=tau if tau > 0 else 1e-300)
+            gamma = 3.0 if stage == 1 else 0.0
+            t = tau if tau > 0 else 1e-300
+            for ref in [(0,) * len(shape), tuple(s // 2 for s in shape), tuple(s - j for s, j in zip(shape, patch))]:
+                rl = int(np.ravel_multi_index(ref, shape))
+                mem, _ = oracle.match_ref(p, y, stage, rl)
+                assert mem.tolist() == _brute_match(y, ref, patch, search, noise, gamma, t, M)
+
+
+# ---------------------------------------------------------------------------
+# variances (Lemma covariance propagation, Cor. white noise, Prop. diagonal Poisson)
+# ---------------------------------------------------------------------------
+
+def _group_setup(oracle, noise, shape=(16, 16), patch=(4, 4), seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.1, 1.0, size=shape)
+    p = oracle.params(shape, patch, (2, 2), (7, 7), noise, (8, 8))
+    members = np.array([np.ravel_multi_index(c, shape) for c in [(3, 3), (5, 4), (0, 9), (10, 2)]])
+    return p, x, members, rng
+
+
+def test_white_noise_variance(oracle):
+    """Cor. white-noise transform variance: sigma_k^2 = sigma^2 for every k."""
+    p, x, members, _ = _group_setup(oracle, ("gaussian", 0.3))
+    g = oracle.filter_group(p, 1, x, None, members)
+    np.testing.assert_allclose(g["var"], 0.09, rtol=1e-13)
+
+
+def test_poisson_variance_monte_carlo(oracle):
+    """Lemma covariance propagation / Prop. diagonal Poisson variance: with the
+    exact clean mean as surrogate, sum_i T_ki^2 s_P X(u_i) is the variance of
+    the transformed coefficient of Poisson observations (independent counts,
+    distinct source voxels).  Checked against 20000 Monte-Carlo draws."""
+    s_p = 0.05
+    p, x, _, rng = _group_setup(oracle, ("poisson", s_p))
+    offs = [np.ravel_multi_index((a, b), x.shape) for a in range(4) for b in range(4)]
+
+    def empirical(members, n=20000):
+        Ys = []
+        idx = np.array([[m + o for o in offs] for m in members]).ravel()
+        for _ in range(n // 500):
+            y = rng.poisson(x[None] / s_p, size=(500,) + x.shape) * s_p
+            grp = y.reshape(500, -1)[:, idx].reshape(500, 4, 4, 4)
+            Ys.append(np.stack([oracle.group_transform(p, gi, 0).ravel() for gi in grp]))
+        return np.concatenate(Ys).var(axis=0, ddof=1)
+
+    disjoint = np.array([np.ravel_multi_index(c, x.shape) for c in [(0, 0), (0, 9), (6, 4), (10, 11)]])
+    var = oracle.filter_group(p, 1, x, None, disjoint)["var"].ravel()
+    # relative standard error of a variance estimate ~ sqrt(2/n) ~ 1%
+    np.testing.assert_allclose(empirical(disjoint), var, rtol=0.06)
+    # overlapping patches share source voxels: there the diagonal model is an
+    # approximation (Eq. shared-voxel-group-covariance), and it visibly misses
+    overlap = np.array([np.ravel_multi_index(c, x.shape) for c in [(3, 3), (4, 3), (3, 4), (4, 4)]])
+    var_o = oracle.filter_group(p, 1, x, None, overlap)["var"].ravel()
+    assert np.max(np.abs(empirical(overlap) / var_o - 1)) > 0.2
+
+
+def test_patch_weights_equal_exact_synthesized_noise(oracle):
+    """Def. coefficient-domain hard-thresholding weighting (variance model,
+    patch scope) under white noise: R_j = sum_l |V_jl|^2 sum_q a_lq sigma^2
+    equals the trace of the noise covariance of synthesized patch j,
+    computed here with the full matrices U A T sigma^2 T^T A U^T."""
+    sig = 0.2
+    p, x, members, rng = _group_setup(oracle, ("gaussian", sig))
+    y = x + rng.normal(0, sig, x.shape)
+    g = oracle.filter_group(p, 1, y, None, members)
+    a = (g["C"].ravel() != 0).astype(float)
+    T = _full_T(oracle, 4, (4, 4))
+    U = T.T
+    cov = U @ np.diag(a) @ (sig ** 2 * np.eye(64)) @ np.diag(a) @ U.T
+    R = np.array([np.trace(cov[j * 16:(j + 1) * 16, j * 16:(j + 1) * 16]) for j in range(4)])
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-12)
+
+
+def test_hard_threshold_mask(oracle):
+    """Def. coefficient thresholding: C_k = Y_k if |Y_k| > lambda sigma_k else 0."""
+    p, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    y = rng.poisson(x / 0.1) * 0.1
+    g = oracle.filter_group(p, 1, y, None, members)
+    keep = np.abs(g["Y"]) > 3.0 * np.sqrt(g["var"])
+    np.testing.assert_array_equal(g["C"], np.where(keep, g["Y"], 0.0))
+
+
+@pytest.mark.parametrize("mode,a", [("noise_floor", 1.0), ("variance_scaled", 0.4)])
+def test_wiener_dead_zone_closed_form(oracle, mode, a):
+    """Prop. corrected pilot-power Wiener gain: G = 0 for |Gamma|^2 <= a sigma^2,
+    else (|Gamma|^2 - a sigma^2) / (|Gamma|^2 - a sigma^2 + s_v sigma^2)."""
+    sig = 0.15
+    shape, patch = (16, 16), (4, 4)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.1, 1.0, size=shape)
+    y = x + rng.normal(0, sig, shape)
+    pilot = x + rng.normal(0, 0.05, shape)
+    p = oracle.params(shape, patch, (2, 2), (7, 7), ("gaussian", sig), (8, 8), power_mode=mode)
+    members = np.array([np.ravel_multi_index(c, shape) for c in [(3, 3), (5, 4), (0, 9), (10, 2)]])
+    g = oracle.filter_group(p, 2, y, pilot, members)
+    offs = [np.ravel_multi_index((i, j), shape) for i in range(4) for j in range(4)]
+    T = _full_T(oracle, 4, patch)
+    gam = T @ pilot.ravel()[np.array([[m + o for o in offs] for m in members]).ravel()]
+    s2 = sig ** 2
+    G = np.where(gam ** 2 <= a * s2, 0.0, (gam ** 2 - a * s2) / (gam ** 2 - a * s2 + 0.4 * s2))
+    np.testing.assert_allclose(g["C"].ravel(), G * g["Y"].ravel(), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# whole-stage invariants
+# ---------------------------------------------------------------------------
+
+def test_identity_at_zero_threshold(oracle):
+    """With sigma = 0 and lambda_HT = 0 every nonzero coefficient passes, every
+    Wiener gain is 1 where the coefficient is nonzero, and weighted overlap-add
+    of unmodified patches returns the observation exactly."""
+    rng = np.random.default_rng(5)
+    y = rng.uniform(0, 1, size=(24, 20))
+    p = oracle.params(y.shape, (4, 4), (2, 2), (7, 7), ("gaussian", 0.0), (8, 16), lambda_ht=0.0)
+    out, pilot = oracle.denoise(p, y)
+    np.testing.assert_allclose(pilot, y, atol=1e-12)
+    np.testing.assert_allclose(out, y, atol=1e-12)
+
+
+def test_constant_array_closed_form(oracle):
+    """A constant group has only its all-axis DC coefficient Y = c sqrt(n P).
+    Stage 1: it survives the threshold, so overlap-add returns c (Def. weighted
+    overlap-add).  Stage 2 (classic power): every group is full (n = 16, all
+    distances 0), the gain is G = Y^2 / (Y^2 + s_v sigma^2) (Def. practical
+    Wiener gain), so the output is the constant c G."""
+    c, sig = 0.7, 0.05
+    y = np.full((20, 22), c)
+    p = oracle.params(y.shape, (4, 4), (3, 3), (7, 7), ("gaussian", sig), (8, 16))
+    out, pilot = oracle.denoise(p, y)
+    np.testing.assert_allclose(pilot, c, atol=1e-12)
+    Y2 = c * c * 16 * 16
+    np.testing.assert_allclose(out, c * Y2 / (Y2 + 0.4 * sig * sig), atol=1e-12)
+
+
+@pytest.mark.parametrize("noise", [("poisson", 0.2), ("gaussian", 0.1)])
+def test_mass_conservation(oracle, noise):
+    """Thm. mass conservation after normalized overlap-add: with the two-sweep
+    correction in both stages, sum x^ = sum y; without it the sums differ."""
+    rng = np.random.default_rng(7)
+    x = synth.disc_rect_image((28, 30), rng)
+    y = rng.poisson(x / noise[1]) * noise[1] if noise[0] == "poisson" else x + rng.normal(0, noise[1], x.shape)
+    for mc in (1, 2, 3):
+        p = oracle.params(y.shape, (4, 4), (2, 2), (9, 9), noise, (8, 16), mass_conserve=mc)
+        out, pilot = oracle.denoise(p, y)
+        if mc & 1:
+            assert pilot.sum() == pytest.approx(y.sum(), rel=1e-12)
+        if mc & 2:
+            assert out.sum() == pytest.approx(y.sum(), rel=1e-12)
+    p = oracle.params(y.shape, (4, 4), (2, 2), (9, 9), noise, (8, 16), mass_conserve=0)
+    out, _ = oracle.denoise(p, y)
+    assert abs(out.sum() - y.sum()) > 1e-6 * abs(y.sum())
+
+
+def test_nd_consistency_singleton_axis(oracle):
+    """A 2-D array with a leading axis of length 1 gives the 1-D result."""
+    rng = np.random.default_rng(9)
+    x = synth.ecg_signal(600, 250.0, rng)
+    y = rng.poisson(x * 20) / 20.0
+    p1 = oracle.params((600,), (16,), (4,), (33,), ("poisson", 0.05), (16, 32))
+    p2 = oracle.params((1, 600), (1, 16), (1, 4), (1, 33), ("poisson", 0.05), (16, 32))
+    o1, pl1 = oracle.denoise(p1, y)
+    o2, pl2 = oracle.denoise(p2, y[None])
+    np.testing.assert_allclose(pl2[0], pl1, atol=1e-12)
+    np.testing.assert_allclose(o2[0], o1, atol=1e-12)
+
+
+def test_stage_points_agree_with_full_stage(oracle):
+    job = synth.config1()
+    p = oracle.params(job.y.shape, job.patch, job.step, job.search, job.noise, job.group_size)
+    full, pilot = oracle.denoise(p, job.y)
+    pts = np.array([0, 63, 64 * 31 + 17, 64 * 64 - 1, 64 * 40 + 3])
+    np.testing.assert_allclose(oracle.stage_points(p, job.y, None, 1, pts), pilot.ravel()[pts], rtol=1e-13)
+    np.testing.assert_allclose(oracle.stage_points(p, job.y, pilot, 2, pts), full.ravel()[pts], rtol=1e-13)
+
+
+def test_group_scope_and_dct_group_transform(oracle):
+    """Group scope gives one weight per group; the DCT group transform keeps
+    non-power-of-two group sizes (no truncation)."""
+    p, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    p2 = oracle.params(x.shape, (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8), weight_scope="group")
+    g = oracle.filter_group(p2, 1, x, None, members)
+    assert np.allclose(g["w"], g["w"][0])
+    y = rng.poisson(x / 0.1) * 0.1
+    p3 = oracle.params(x.shape, (4, 4), (1, 1), (7, 7), ("poisson", 0.1), (7, 7), group_transform="dct",
+                       tau_ht=1e9)
+    mem, _ = oracle.match_ref(p3, y, 1, 5 * 16 + 5)
+    assert len(mem) == 7
+
+
+def test_classic_group_weight_is_retained_count(oracle):
+    """Def. hard-thresholding weighting: the classic group-scope surrogate is
+    R = sum_k a_k = N_g^HT (Def. retained coefficient count)."""
+    p0, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    y = rng.poisson(x / 0.1) * 0.1
+    p = oracle.params(x.shape, (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8),
+                      weight_model="classic", weight_scope="group")
+    g = oracle.filter_group(p, 1, y, None, members)
+    n_ht = int(np.count_nonzero(g["C"]))
+    np.testing.assert_allclose(g["w"], 1.0 / n_ht, rtol=1e-14)
+
+
+def test_wiener_risk_weight_minimum_risk(oracle):
+    """Thm. optimal scalar Wiener gain: at G = S / (S + sigma^2) the risk
+    (1-G)^2 S + G^2 sigma^2 equals G sigma^2.  With s_v = 1 and the classic
+    pilot power, the risk model in group scope therefore gives
+    w = 1 / sum_k G_k sigma^2 with G_k = Gamma_k^2 / (Gamma_k^2 + sigma^2)."""
+    sig = 0.2
+    shape, patch = (16, 16), (4, 4)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0.1, 1.0, size=shape)
+    y = x + rng.normal(0, sig, shape)
+    pilot = x + rng.normal(0, 0.05, shape)
+    p = oracle.params(shape, patch, (2, 2), (7, 7), ("gaussian", sig), (8, 8), s_v=1.0,
+                      weight_model="risk", weight_scope="group")
+    members = np.array([np.ravel_multi_index(c, shape) for c in [(3, 3), (5, 4), (0, 9), (10, 2)]])
+    g = oracle.filter_group(p, 2, y, pilot, members)
+    offs = [np.ravel_multi_index((i, j), shape) for i in range(4) for j in range(4)]
+    gam = _full_T(oracle, 4, patch) @ pilot.ravel()[np.array([[m + o for o in offs] for m in members]).ravel()]
+    G = gam ** 2 / (gam ** 2 + sig ** 2)
+    np.testing.assert_allclose(g["w"], 1.0 / np.sum(G * sig ** 2), rtol=1e-12)
