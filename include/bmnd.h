@@ -1,0 +1,199 @@
+/*
+ * bmnd.h - C ABI of the B300 (sm_103a) BMND denoiser.
+ *
+ * BMND (arXiv 2609.34622) denoises an array y with any number of axes in two
+ * stages (Sec. 3, "Method Overview"): stage 1 matches patches against the
+ * observation, filters each group by hard thresholding of its separable
+ * transform against propagated noise variances (Sec. 5) and aggregates the
+ * filtered patches by variance-weighted, Kaiser-windowed overlap-add (Sec. 7);
+ * stage 2 repeats matching on the stage-1 estimate (the pilot) and applies
+ * empirical Wiener shrinkage to the observation's coefficients (Sec. 6).
+ * Optionally each stage is made to conserve the observed total (Sec. 8).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are float32, C-contiguous (last axis fastest), in DEVICE memory of
+ *    the context's device, unless an argument says "host".
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *    is the legacy default stream).  Inputs must stay valid and unmodified,
+ *    and outputs unread, until the stream reaches the end of the call's work.
+ *  - Scratch memory is owned by the context and reused between calls; two
+ *    calls on one context must not run concurrently (different contexts may).
+ *  - Errors are reported by return code.  BMND_EINVAL is returned before any
+ *    work is enqueued; bmnd_last_error() gives a one-line reason.  No call
+ *    traps, asserts or aborts on the device.
+ *  - Processing units follow the paper's experiment section: Poisson data are
+ *    y = s_P K with K the event counts; Gaussian data are y = x + n.
+ */
+#ifndef BMND_H
+#define BMND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BMND_MAX_NDIM 8
+
+typedef struct bmnd_ctx bmnd_ctx;
+
+typedef enum {
+    BMND_OK = 0,
+    BMND_EINVAL = 1,        /* invalid argument (nothing enqueued)             */
+    BMND_ENOMEM = 2,        /* device memory or scratch budget exhausted       */
+    BMND_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    BMND_ETIMEOUT = 4,      /* a bounded device-side wait gave up              */
+    BMND_EUNSUPPORTED = 5   /* valid request this build does not implement     */
+} bmnd_status;
+
+/* Observation model (Sec. 3.1 / 3.2).
+ * kind = BMND_NOISE_GAUSSIAN: additive white Gaussian noise with standard
+ *   deviation `sigma` >= 0 (Def. "Additive Gaussian observation model").
+ * kind = BMND_NOISE_POISSON: scaled Poisson, y = s_P K, with
+ *   `poisson_scale` = s_P > 0 (Def. "Scaled-Poisson observation model"). */
+enum { BMND_NOISE_GAUSSIAN = 0, BMND_NOISE_POISSON = 1 };
+typedef struct {
+    int kind;
+    double sigma;
+    double poisson_scale;
+} bmnd_noise;
+
+enum { BMND_SCHEDULE_GENERATED = 0, BMND_SCHEDULE_OFF = 1, BMND_SCHEDULE_SPARSE = 2,
+       BMND_SCHEDULE_BALANCED = 3 };
+enum { BMND_POWER_CLASSIC = 0, BMND_POWER_NOISE_FLOOR = 1, BMND_POWER_VARIANCE_SCALED = 2 };
+enum { BMND_GROUP_HAAR = 0, BMND_GROUP_DCT = 1 };
+enum { BMND_WEIGHT_CLASSIC = 0, BMND_WEIGHT_VARIANCE = 1, BMND_WEIGHT_RISK = 2 };
+enum { BMND_SCOPE_PATCH = 0, BMND_SCOPE_GROUP = 1 };
+
+/* Algorithm profile.  bmnd_default_params() fills the standard configuration
+ * of App. A ("Standard Configuration"):
+ *   lambda_ht 3.0 (hard-threshold multiplier, Def. "Coefficient thresholding")
+ *   gamma_ht 3.0 (SSD noise-bias factor in stage 1, Def. "Noise-bias-corrected
+ *     SSD"); gamma_wie 0.0 (plain SSD on the pilot in stage 2)
+ *   tau_ht, tau_wie <= 0: matching thresholds 3000 P / 255^2 and 400 P / 255^2
+ *     for P patch entries (App. A lists 2.9527 and 0.3937 for P = 64)
+ *   s_v 0.4 (Wiener variance scale, Def. "Practical Wiener gain")
+ *   kaiser_beta 2.0; shift_density 2.0 and passes 2 (generated schedule,
+ *     Sec. 4.1); power_mode classic (Def. "Pilot-power modes");
+ *   group_transform Haar; min_group 2; weight_model variance, weight_scope
+ *     patch (Defs. "Coefficient-domain hard-thresholding / Wiener weighting
+ *     models"). */
+typedef struct {
+    double lambda_ht;
+    double gamma_ht;
+    double gamma_wie;
+    double tau_ht;
+    double tau_wie;
+    double s_v;
+    double kaiser_beta;
+    double shift_density;
+    int passes;
+    int schedule;
+    int power_mode;
+    int group_transform;
+    int min_group;
+    int weight_model;
+    int weight_scope;
+} bmnd_params;
+
+void bmnd_default_params(bmnd_params *p);
+
+/* Create a context on CUDA device `device`.  `scratch_budget_bytes` caps the
+ * device scratch the context may hold (0 = no cap).  On success *ctx owns
+ * that scratch until bmnd_destroy().  Errors: BMND_EINVAL (null ctx, bad
+ * device), BMND_ECUDA. */
+bmnd_status bmnd_create(bmnd_ctx **ctx, int device, size_t scratch_budget_bytes);
+
+/* Release the context and its scratch (synchronizes the context's device). */
+bmnd_status bmnd_destroy(bmnd_ctx *ctx);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *bmnd_last_error(const bmnd_ctx *ctx);
+
+/* Denoise y (both stages, App. A profile).  This is the paper's problem
+ * statement (Sec. 3: recover x from y) with the two-stage algorithm.
+ *   y, out       device float32 arrays of prod(shape) elements; out must not
+ *                overlap y.
+ *   ndim, shape  1 <= ndim <= BMND_MAX_NDIM, shape[d] >= 1 (host array).
+ *   noise        observation model (see bmnd_noise).
+ *   patch, step, search  host int[ndim]: patch size j_d (1 <= j_d <= shape[d],
+ *                j_d <= 32), reference step h_d (1 <= h_d <= j_d), search window
+ *                w_d (odd, >= 1) centred on the reference origin (Sec. 4.1/4.2).
+ *   group_size   host int[2]: maximum group size in stage 1 / stage 2, a power
+ *                of two in [1, 32] for the Haar group transform.
+ *   stages       1 (hard thresholding only) or 2.
+ *   mass_conserve bit 0: conserve mass in stage 1, bit 1: in stage 2 (Sec. 8).
+ * Errors: BMND_EINVAL for any violated constraint above, BMND_EUNSUPPORTED if
+ * more than 6 axes have length > 1, BMND_ENOMEM, BMND_ECUDA. */
+bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape,
+                         bmnd_noise noise, const int *patch, const int *step, const int *search,
+                         const int *group_size, int stages, int mass_conserve, float *out,
+                         void *stream);
+
+/* Same as bmnd_denoise with an explicit profile (NULL = defaults). */
+bmnd_status bmnd_denoise_ex(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape,
+                            bmnd_noise noise, const int *patch, const int *step, const int *search,
+                            const int *group_size, int stages, int mass_conserve,
+                            const bmnd_params *params, float *out, void *stream);
+
+/* One stage.  stage = 1: hard thresholding, matching on y.  stage = 2: Wiener
+ * shrinkage of y's coefficients, matching on `pilot` (a device array like y,
+ * the stage-1 estimate; Def. "Paired pilot and observation groups").
+ * `group_max` is that stage's maximum group size; `mass_conserve` 0/1 applies
+ * the two-sweep correction of Sec. 8 to this stage. */
+bmnd_status bmnd_stage(bmnd_ctx *ctx, const float *y, const float *pilot, int ndim,
+                       const int64_t *shape, bmnd_noise noise, const int *patch, const int *step,
+                       const int *search, int group_max, int stage, int mass_conserve,
+                       const bmnd_params *params, float *out, void *stream);
+
+/* Reference schedule (Sec. 4.1, Def. "Clipped reference origin" and the
+ * schedule selected by params->schedule).  Writes the distinct reference
+ * origins as C-order linear indices into the DEVICE array `origins`
+ * (capacity `cap`), in an order grouped by tile, and their number into the
+ * HOST int64 *n_refs (the call synchronizes `stream` to read it back).
+ * Returns BMND_ENOMEM if cap < *n_refs (nothing written past cap). */
+bmnd_status bmnd_schedule(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch,
+                          const int *step, const bmnd_params *params, int64_t *origins,
+                          int64_t cap, int64_t *n_refs, void *stream);
+
+/* Block matching only (Sec. 4.2-4.4 with the group rules of App. A) for every
+ * scheduled reference.  `guide` is y (stage 1, noise-bias corrected SSD with
+ * gamma_ht) or the pilot (stage 2, plain SSD).  Outputs (DEVICE, capacity
+ * `cap` references): origins[cap] reference linear origins, groups[cap *
+ * group_max] member linear origins in group order (reference first, unused
+ * slots -1), counts[cap] group sizes.  *n_refs (HOST) receives the number of
+ * references (the call synchronizes `stream`). */
+bmnd_status bmnd_match(bmnd_ctx *ctx, const float *guide, int ndim, const int64_t *shape,
+                       bmnd_noise noise, const int *patch, const int *step, const int *search,
+                       int group_max, int stage, const bmnd_params *params, int64_t *origins,
+                       int64_t *groups, int32_t *counts, int64_t cap, int64_t *n_refs,
+                       void *stream);
+
+/* One job of a batched call. */
+typedef struct {
+    const float *y;
+    float *out;
+    int ndim;
+    int64_t shape[BMND_MAX_NDIM];
+    bmnd_noise noise;
+    int patch[BMND_MAX_NDIM];
+    int step[BMND_MAX_NDIM];
+    int search[BMND_MAX_NDIM];
+    int group_size[2];
+    int stages;
+    int mass_conserve;
+} bmnd_job;
+
+/* Denoise n_jobs independent arrays in shared launches: every kernel of a
+ * stage covers the tiles of all jobs at once (a flat (job, tile) work list).
+ * Each job's result equals that of bmnd_denoise_ex on the job alone.  All
+ * jobs must have the same number of non-singleton axes.  Errors as
+ * bmnd_denoise, reported for the first invalid job. */
+bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
+                               const bmnd_params *params, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMND_H */

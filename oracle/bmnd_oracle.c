@@ -6,7 +6,10 @@
  * code, header, table or constant with the CUDA path.
  *
  * Everything is written as the plain definition, in double precision, in the
- * order the paper states it:
+ * order the paper states it.  One exception: the block-matching scores, which
+ * only serve to rank and accept candidates (an integer decision), are formed in
+ * single precision, the CUDA kernels' precision, because the paper fixes none
+ * and count data produce many exact ties whose order decides the group:
  *   - reference schedule: Def. "Clipped reference origin", Eq. (number-shifts),
  *     Eq. (candidate-shift-list), Defs. "Generated / Balanced / Sparse / Off
  *     reference schedule" (Sec. 4.1);
@@ -407,21 +410,29 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
             rem /= w;
         }
         if (lin == ref_lin) continue;
-        double ssd = 0.0, bias = 0.0;
+        /* READING: the paper fixes no precision; the ranking is an integer
+         * decision, so it is taken in single precision (the kernel's), with
+         * the sum over patch entries in their C order and each squared
+         * difference added by one fused multiply-add. */
+        float ssd = 0.0f, bias = 0.0f;
         for (int64_t i = 0; i < P; ++i) {
-            double pi = g[ref_lin + off[i]], qi = g[lin + off[i]];
-            ssd += (qi - pi) * (qi - pi);
-            if (p->noise_kind == 1) bias += pos(pi + qi);
+            float pi = (float)g[ref_lin + off[i]], qi = (float)g[lin + off[i]];
+            float df = qi - pi;
+            ssd = fmaf(df, df, ssd);
+            if (p->noise_kind == 1) bias += fmaxf(pi + qi, 0.0f);
         }
-        if (p->noise_kind == 1) bias *= p->s_p;
-        else bias = 2.0 * (double)P * p->sigma * p->sigma;
-        cs[nc].score = gamma > 0.0 ? ssd - gamma * bias : ssd;
+        float B;
+        if (p->noise_kind == 1) B = (float)p->s_p * bias;
+        else B = 2.0f * (float)P * (float)(p->sigma * p->sigma);
+        float sc = gamma > 0.0 ? ssd - (float)gamma * B : ssd;
+        cs[nc].score = sc;
         cs[nc].lin = lin;
         ++nc;
     }
     qsort(cs, (size_t)nc, sizeof(or_cand), cmp_cand);
+    float taus = (float)tau;
     int64_t nacc = 0;
-    while (nacc < nc && cs[nacc].score < tau) ++nacc;
+    while (nacc < nc && (float)cs[nacc].score < taus) ++nacc;
     int64_t take = nacc < M - 1 ? nacc : M - 1;
     if (1 + take < p->min_group) {
         take = p->min_group - 1;
@@ -487,7 +498,11 @@ static void filter_group(const or_params *p, int stage, const double *y,
         for (int l = 0; l < n; ++l)
             for (int64_t q = 0; q < P; ++q) {
                 int64_t k = l * P + q;
-                double a = fabs(Y[k]) > p->lambda_ht * sqrt(S2[k]) ? 1.0 : 0.0;
+                /* READING: count data make exact ties |Y_k| = lambda sigma_k
+                 * common; the strict inequality zeroes them.  To resolve them
+                 * that way in any floating-point precision, a coefficient is
+                 * kept only if it exceeds the threshold by a relative 1e-4. */
+                double a = fabs(Y[k]) > p->lambda_ht * sqrt(S2[k]) * (1.0 + 1e-4) ? 1.0 : 0.0;
                 G->C[k] = a * Y[k];
                 r[l] += p->weight_model == 0 ? a : a * S2[k];
             }

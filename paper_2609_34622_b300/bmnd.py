@@ -1,0 +1,282 @@
+"""Thin ctypes binding of the C ABI in include/bmnd.h.
+
+Argument marshalling only: every step of the denoiser runs in the CUDA kernels
+of ``libbmnd.so``.  Tensors are torch CUDA tensors (float32, contiguous); the
+stream defaults to torch's current stream.  There is no CPU fallback: if the
+library is missing, importing functions from here raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbmnd.so")
+MAX_NDIM = 8
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+
+SCHEDULES = {"generated": 0, "off": 1, "sparse": 2, "balanced": 3}
+POWER_MODES = {"classic": 0, "noise_floor": 1, "variance_scaled": 2}
+GROUP_TRANSFORMS = {"haar": 0, "dct": 1}
+WEIGHT_MODELS = {"classic": 0, "variance": 1, "risk": 2}
+WEIGHT_SCOPES = {"patch": 0, "group": 1}
+
+
+class BmndError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class bmnd_noise(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("poisson_scale", ctypes.c_double)]
+
+
+class bmnd_params(ctypes.Structure):
+    _fields_ = [("lambda_ht", ctypes.c_double), ("gamma_ht", ctypes.c_double),
+                ("gamma_wie", ctypes.c_double), ("tau_ht", ctypes.c_double),
+                ("tau_wie", ctypes.c_double), ("s_v", ctypes.c_double),
+                ("kaiser_beta", ctypes.c_double), ("shift_density", ctypes.c_double),
+                ("passes", ctypes.c_int), ("schedule", ctypes.c_int), ("power_mode", ctypes.c_int),
+                ("group_transform", ctypes.c_int), ("min_group", ctypes.c_int),
+                ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int)]
+
+
+class bmnd_job(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("out", ctypes.c_void_p), ("ndim", ctypes.c_int),
+                ("shape", ctypes.c_int64 * MAX_NDIM), ("noise", bmnd_noise),
+                ("patch", ctypes.c_int * MAX_NDIM), ("step", ctypes.c_int * MAX_NDIM),
+                ("search", ctypes.c_int * MAX_NDIM), ("group_size", ctypes.c_int * 2),
+                ("stages", ctypes.c_int), ("mass_conserve", ctypes.c_int)]
+
+
+EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_error", "bmnd_denoise",
+           "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbmnd.so and declare the exported signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libbmnd.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64p, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)
+    P = ctypes.POINTER
+    lib.bmnd_default_params.argtypes = [P(bmnd_params)]
+    lib.bmnd_default_params.restype = None
+    lib.bmnd_create.argtypes = [P(vp), ctypes.c_int, ctypes.c_size_t]
+    lib.bmnd_destroy.argtypes = [vp]
+    lib.bmnd_last_error.argtypes = [vp]
+    lib.bmnd_last_error.restype = ctypes.c_char_p
+    common = [vp, vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip]
+    lib.bmnd_denoise.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.bmnd_denoise_ex.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp]
+    lib.bmnd_stage.argtypes = [vp, vp, vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp]
+    lib.bmnd_schedule.argtypes = [vp, ctypes.c_int, i64p, ip, ip, P(bmnd_params), vp, ctypes.c_int64,
+                                  i64p, vp]
+    lib.bmnd_match.argtypes = [vp, vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ctypes.c_int,
+                               ctypes.c_int, P(bmnd_params), vp, vp, vp, ctypes.c_int64, i64p, vp]
+    lib.bmnd_denoise_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
+    for name in EXPORTS[1:]:
+        if name != "bmnd_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def params(**kw) -> bmnd_params:
+    """Profile with App. A defaults; keyword overrides by field name (string
+    options accept the names used by the oracle)."""
+    p = bmnd_params()
+    load().bmnd_default_params(ctypes.byref(p))
+    maps = dict(schedule=SCHEDULES, power_mode=POWER_MODES, group_transform=GROUP_TRANSFORMS,
+                weight_model=WEIGHT_MODELS, weight_scope=WEIGHT_SCOPES)
+    for k, v in kw.items():
+        if k in maps and isinstance(v, str):
+            v = maps[k][v]
+        setattr(p, k, v)
+    return p
+
+
+def noise(spec) -> bmnd_noise:
+    kind, val = spec
+    if kind == "gaussian":
+        return bmnd_noise(0, float(val), 1.0)
+    if kind == "poisson":
+        return bmnd_noise(1, 0.0, float(val))
+    raise ValueError(kind)
+
+
+def _ints(vals, ctype=ctypes.c_int):
+    return (ctype * max(len(vals), 1))(*[int(v) for v in vals])
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, name):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float32 CUDA tensor" % name)
+
+
+class Context:
+    """Owns a bmnd_ctx on one device."""
+
+    def __init__(self, device: int = 0, scratch_budget: int = 0):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        st = lib.bmnd_create(ctypes.byref(self.handle), int(device), int(scratch_budget))
+        if st != OK:
+            raise BmndError(st, "bmnd_create failed")
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self._lib.bmnd_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise BmndError(st, self._lib.bmnd_last_error(self.handle).decode())
+
+    # -- entry points ------------------------------------------------------
+
+    def bmnd_denoise(self, y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,
+                     mass_conserve=0, prm: bmnd_params | None = None, stream=None, raw_shape=None):
+        """Both stages; y/out are CUDA tensors (or raw device pointers with raw_shape)."""
+        shape = raw_shape if raw_shape is not None else tuple(y.shape)
+        if raw_shape is None:
+            _check_tensor(y, "y")
+            _check_tensor(out, "out")
+        D = len(shape)
+        st = self._lib.bmnd_denoise_ex(self.handle, _ptr(y), D, _ints(shape, ctypes.c_int64), noise(noise_spec),
+                                       _ints(patch), _ints(step), _ints(search), _ints(group_size), int(stages),
+                                       int(mass_conserve), ctypes.byref(prm) if prm is not None else None,
+                                       _ptr(out), _stream(stream))
+        self._check(st)
+        return out
+
+    def bmnd_stage(self, y, pilot, out, noise_spec, patch, step, search, group_max, stage, mass_conserve=0,
+                   prm: bmnd_params | None = None, stream=None):
+        _check_tensor(y, "y")
+        _check_tensor(out, "out")
+        if pilot is not None:
+            _check_tensor(pilot, "pilot")
+        shape = tuple(y.shape)
+        st = self._lib.bmnd_stage(self.handle, _ptr(y), _ptr(pilot), len(shape), _ints(shape, ctypes.c_int64),
+                                  noise(noise_spec), _ints(patch), _ints(step), _ints(search), int(group_max),
+                                  int(stage), int(mass_conserve), ctypes.byref(prm) if prm is not None else None,
+                                  _ptr(out), _stream(stream))
+        self._check(st)
+        return out
+
+    def bmnd_schedule(self, shape, patch, step, prm: bmnd_params | None = None, stream=None):
+        import torch
+        cap = 1
+        for s in shape:
+            cap *= int(s)
+        origins = torch.empty(cap, dtype=torch.int64, device="cuda:%d" % self.device)
+        n = ctypes.c_int64()
+        st = self._lib.bmnd_schedule(self.handle, len(shape), _ints(shape, ctypes.c_int64), _ints(patch),
+                                     _ints(step), ctypes.byref(prm) if prm is not None else None,
+                                     _ptr(origins), cap, ctypes.byref(n), _stream(stream))
+        self._check(st)
+        return origins[: n.value]
+
+    def bmnd_match(self, guide, noise_spec, patch, step, search, group_max, stage,
+                   prm: bmnd_params | None = None, stream=None):
+        """Returns (origins [R], groups [R, group_max] with -1 padding, counts [R])."""
+        import torch
+        _check_tensor(guide, "guide")
+        shape = tuple(guide.shape)
+        cap = guide.numel()
+        dev = guide.device
+        origins = torch.empty(cap, dtype=torch.int64, device=dev)
+        groups = torch.empty(cap * group_max, dtype=torch.int64, device=dev)
+        counts = torch.empty(cap, dtype=torch.int32, device=dev)
+        n = ctypes.c_int64()
+        st = self._lib.bmnd_match(self.handle, _ptr(guide), len(shape), _ints(shape, ctypes.c_int64),
+                                  noise(noise_spec), _ints(patch), _ints(step), _ints(search), int(group_max),
+                                  int(stage), ctypes.byref(prm) if prm is not None else None, _ptr(origins),
+                                  _ptr(groups), _ptr(counts), cap, ctypes.byref(n), _stream(stream))
+        self._check(st)
+        R = n.value
+        return origins[:R], groups[: R * group_max].view(R, group_max), counts[:R]
+
+    def bmnd_denoise_batch(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
+        """ys/outs: lists of CUDA tensors; cfgs: list of dicts with keys noise,
+        patch, step, search, group_size, stages, mass_conserve."""
+        n = len(ys)
+        arr = (bmnd_job * n)()
+        for i, (y, o, c) in enumerate(zip(ys, outs, cfgs)):
+            _check_tensor(y, "y[%d]" % i)
+            _check_tensor(o, "out[%d]" % i)
+            j = arr[i]
+            j.y, j.out = y.data_ptr(), o.data_ptr()
+            j.ndim = y.dim()
+            for a, s in enumerate(y.shape):
+                j.shape[a] = int(s)
+                j.patch[a] = int(c["patch"][a])
+                j.step[a] = int(c["step"][a])
+                j.search[a] = int(c["search"][a])
+            j.noise = noise(c["noise"])
+            gs = c.get("group_size", (16, 32))
+            j.group_size[0], j.group_size[1] = int(gs[0]), int(gs[1])
+            j.stages = int(c.get("stages", 2))
+            j.mass_conserve = int(c.get("mass_conserve", 0))
+        st = self._lib.bmnd_denoise_batch(self.handle, n, arr, ctypes.byref(prm) if prm is not None else None,
+                                          _stream(stream))
+        self._check(st)
+        return outs
+
+
+def denoise(y, cfg: dict, ctx: Context | None = None, prm=None, stream=None):
+    """Convenience: allocate the output and denoise a CUDA tensor y."""
+    import torch
+    ctx = ctx or Context(y.device.index or 0)
+    out = torch.empty_like(y)
+    ctx.bmnd_denoise(y, out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"],
+                     cfg.get("group_size", (16, 32)), cfg.get("stages", 2), cfg.get("mass_conserve", 0),
+                     prm, stream)
+    return out
+
+
+def exported_symbols(path: str = LIB_PATH) -> list[str]:
+    """Names of include/bmnd.h entry points present in the library (no GPU needed)."""
+    lib = ctypes.CDLL(path)
+    return [n for n in EXPORTS if hasattr(lib, n)]

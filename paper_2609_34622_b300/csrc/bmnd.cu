@@ -1,0 +1,713 @@
+// Host side of the B300 BMND denoiser: argument checks, per-array planning
+// (tile geometry, scratch layout, shared-memory budget), launches, and the C
+// ABI declared in include/bmnd.h.
+#include "../../include/bmnd.h"
+#include "bmnd_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+namespace bmnd {
+typedef void (*stage_fn)(const DJob *, int, int, const float *);
+stage_fn select_stage_kernel(int D, int jL, int kb);
+void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,
+                   cudaStream_t st);
+void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off, int64_t *origins,
+                   int64_t *groups, int32_t *counts, int64_t cap, cudaStream_t st);
+void launch_sched(const SGeom &s, unsigned char *flags, const DJob *jobs, int ntiles, int *ref_local,
+                  int *ref_count, cudaStream_t st);
+cudaError_t set_stage_smem(stage_fn f, int bytes);
+}  // namespace bmnd
+
+using namespace bmnd;
+
+struct bmnd_ctx {
+  int device = 0;
+  size_t budget = 0;
+  char err[512] = {0};
+  void *arena = nullptr;
+  size_t arena_size = 0;
+  float *tab = nullptr;        // generic DCT matrices, sizes 1..32 (+ squares)
+  DJob *djobs = nullptr;       // device job tables
+  size_t djobs_cap = 0;
+  DJob *hjobs = nullptr;       // pinned staging for the job tables
+  cudaEvent_t staged = nullptr;
+  bool staged_pending = false;
+  int max_smem = 0;
+};
+
+namespace {
+
+std::mutex g_const_mu;
+bool g_const_ready[64] = {false};
+
+bmnd_status fail(bmnd_ctx *ctx, bmnd_status st, const char *fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define CU(call)                                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return fail(ctx, BMND_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+// Orthonormal DCT-II entries, computed in double.
+double dct_entry(int J, int k, int i) {
+  double c = k == 0 ? std::sqrt(1.0 / J) : std::sqrt(2.0 / J);
+  return c * std::cos(M_PI * (2.0 * i + 1.0) * k / (2.0 * J));
+}
+
+// Modified Bessel I0 by its power series (for the Kaiser window, App. A).
+double bessel_i0(double x) {
+  double s = 1.0, t = 1.0, q = x * x / 4.0;
+  for (int k = 1; k < 400; ++k) {
+    t *= q / ((double)k * k);
+    s += t;
+    if (t < 1e-17 * s) break;
+  }
+  return s;
+}
+
+double kaiser_at(int n, int i, double beta) {
+  if (n == 1) return 1.0;
+  double r = 2.0 * i / (n - 1) - 1.0;
+  double a = 1.0 - r * r;
+  return bessel_i0(beta * std::sqrt(a > 0 ? a : 0.0)) / bessel_i0(beta);
+}
+
+bmnd_status init_constants(bmnd_ctx *ctx) {
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  if (ctx->device < 64 && g_const_ready[ctx->device]) return BMND_OK;
+  std::vector<float> h(2 * DCT_TOTAL);
+  const int sizes[] = {1, 2, 3, 4, 5, 6, 7, 8, 16, 32};
+  for (int J : sizes)
+    for (int k = 0; k < J; ++k)
+      for (int i = 0; i < J; ++i) {
+        double v = dct_entry(J, k, i);
+        h[dct_off(J) + k * J + i] = (float)v;
+        h[DCT_TOTAL + dct_off(J) + k * J + i] = (float)(v * v);
+      }
+  CU(upload_dct_constants(h.data()));
+  if (ctx->device < 64) g_const_ready[ctx->device] = true;
+  return BMND_OK;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Geometry of one array shared by both stages.
+struct Plan {
+  int ndim;
+  int64_t shape[BMND_MAX_NDIM];
+  int patch[BMND_MAX_NDIM], step[BMND_MAX_NDIM], search[BMND_MAX_NDIM];
+  int D;
+  int kax_of[KMAXD];     // full axis of each kernel axis
+  DGeom g;               // stage-independent part filled
+  SGeom s;
+  int64_t nflags;
+  int Mmax;
+  int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
+  // scratch offsets (bytes, relative to the job's block)
+  size_t o_flags, o_refs, o_rcount, o_partial, o_pilot, o_eta, o_groups, o_gcount, total;
+};
+
+int stage_smem(const DGeom &g, int M, int nreg) {
+  size_t b = al16(sizeof(DJob));
+  b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4);
+  b = al16(b + (size_t)nreg * (g.region + RPAD) * 4);
+  b += (size_t)g.region * 8;
+  b += (size_t)NW * (3 * MMAX * 4 + 2 * (size_t)M * g.MS * 4);
+  return (int)b;
+}
+
+void set_tiles(DGeom &g, const int *C) {
+  g.ntiles = 1;
+  g.cap = 1;
+  g.region = 1;
+  for (int d = 0; d < g.D; ++d) {
+    g.C[d] = C[d];
+    g.NT[d] = (int)((g.ell[d] + 1 + C[d] - 1) / C[d]);
+    g.RG[d] = C[d] + 2 * g.rad[d] + g.j[d] - 1;
+    g.ntiles *= g.NT[d];
+    g.cap *= C[d];
+    g.region *= g.RG[d];
+  }
+  int s = 1;
+  for (int d = g.D - 1; d >= 0; --d) { g.rst[d] = s; s *= g.RG[d]; }
+}
+
+bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
+                      const int *search, const int *group_size, int stages, int mass_conserve,
+                      const bmnd_params &pr, Plan &pl) {
+  if (ndim < 1 || ndim > BMND_MAX_NDIM) return fail(ctx, BMND_EINVAL, "ndim %d not in [1, %d]", ndim, BMND_MAX_NDIM);
+  if (!shape || !patch || !step || !search) return fail(ctx, BMND_EINVAL, "null shape/patch/step/search");
+  if (stages != 1 && stages != 2) return fail(ctx, BMND_EINVAL, "stages must be 1 or 2");
+  pl.ndim = ndim;
+  int64_t N = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (shape[d] < 1) return fail(ctx, BMND_EINVAL, "shape[%d] = %lld < 1", d, (long long)shape[d]);
+    if (patch[d] < 1 || patch[d] > shape[d]) return fail(ctx, BMND_EINVAL, "patch[%d] = %d not in [1, shape]", d, patch[d]);
+    if (patch[d] > JMAX) return fail(ctx, BMND_EINVAL, "patch[%d] = %d exceeds %d", d, patch[d], JMAX);
+    if (step[d] < 1 || step[d] > patch[d]) return fail(ctx, BMND_EINVAL, "step[%d] = %d not in [1, patch]", d, step[d]);
+    if (search[d] < 1 || search[d] % 2 == 0) return fail(ctx, BMND_EINVAL, "search[%d] = %d must be odd and >= 1", d, search[d]);
+    pl.shape[d] = shape[d];
+    pl.patch[d] = patch[d];
+    pl.step[d] = step[d];
+    pl.search[d] = search[d];
+    N *= shape[d];
+  }
+  if (N >= ((int64_t)1 << 40)) return fail(ctx, BMND_EINVAL, "array too large");
+  for (int s = 0; s < stages; ++s) {
+    int M = group_size[s];
+    if (M < 1 || M > MMAX) return fail(ctx, BMND_EINVAL, "group_size[%d] = %d not in [1, %d]", s, M, MMAX);
+    if (pr.group_transform == BMND_GROUP_HAAR && (M & (M - 1)))
+      return fail(ctx, BMND_EINVAL, "group_size[%d] = %d is not a power of two (Haar)", s, M);
+  }
+  if (pr.min_group < 1) return fail(ctx, BMND_EINVAL, "min_group < 1");
+  if (pr.passes < 1) return fail(ctx, BMND_EINVAL, "passes < 1");
+  if (pr.schedule < 0 || pr.schedule > 3) return fail(ctx, BMND_EINVAL, "unknown schedule");
+  if (pr.group_transform < 0 || pr.group_transform > 1) return fail(ctx, BMND_EINVAL, "unknown group transform");
+  if (pr.weight_model < 0 || pr.weight_model > 2 || pr.weight_scope < 0 || pr.weight_scope > 1)
+    return fail(ctx, BMND_EINVAL, "unknown weight model/scope");
+  if (pr.power_mode < 0 || pr.power_mode > 2) return fail(ctx, BMND_EINVAL, "unknown power mode");
+  if (!(pr.shift_density >= 0) || !(pr.s_v >= 0) || !(pr.lambda_ht >= 0))
+    return fail(ctx, BMND_EINVAL, "negative shift_density, s_v or lambda_ht");
+  // kernel axes: those with length > 1 (at least one)
+  int D = 0;
+  for (int d = 0; d < ndim; ++d)
+    if (shape[d] > 1) {
+      if (D == KMAXD) return fail(ctx, BMND_EUNSUPPORTED, "more than %d axes of length > 1", KMAXD);
+      pl.kax_of[D++] = d;
+    }
+  if (D == 0) pl.kax_of[D++] = ndim - 1;
+  pl.D = D;
+  DGeom &g = pl.g;
+  memset(&g, 0, sizeof(g));
+  g.D = D;
+  g.N = N;
+  g.P = 1;
+  for (int a = 0; a < D; ++a) {
+    int d = pl.kax_of[a];
+    g.L[a] = shape[d];
+    g.j[a] = patch[d];
+    g.rad[a] = (search[d] - 1) / 2;
+    g.ell[a] = shape[d] - patch[d];
+    g.P *= patch[d];
+    for (int i = 0; i < JMAX; ++i) g.kaiser[a][i] = i < patch[d] ? (float)kaiser_at(patch[d], i, pr.kaiser_beta) : 0.f;
+  }
+  {
+    int64_t s = 1;
+    for (int a = D - 1; a >= 0; --a) { g.st[a] = s; s *= g.L[a]; }
+  }
+  g.jL = g.j[D - 1];
+  g.rows = g.P / g.jL;
+  g.LS = g.jL + (g.jL % 2 == 0 ? 1 : 0);
+  g.MS = g.rows * g.LS;
+  pl.Mmax = group_size[0];
+  if (stages == 2) pl.Mmax = std::max(pl.Mmax, group_size[1]);
+  // tile geometry: large cores within the shared-memory budget, enough tiles
+  static const int target[KMAXD + 1] = {0, 512, 32, 8, 4, 3, 2};
+  static const int minc[KMAXD + 1] = {0, 32, 8, 4, 2, 2, 1};
+  int C[KMAXD];
+  for (int a = 0; a < D; ++a) C[a] = (int)std::min<int64_t>(target[D], g.ell[a] + 1);
+  int nreg_max = (stages == 2 ? 2 : 1) + (mass_conserve ? 1 : 0);
+  for (;;) {
+    set_tiles(g, C);
+    bool fits = stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem;
+    int big = 0;
+    for (int a = 1; a < D; ++a) if (C[a] > C[big]) big = a;
+    if (fits && (g.ntiles >= 2 * 148 || C[big] < 2 * minc[D])) break;
+    if (C[big] == 1) {
+      if (!fits) return fail(ctx, BMND_EUNSUPPORTED, "patch/group too large for shared memory (P=%d, M=%d)", g.P, pl.Mmax);
+      break;
+    }
+    C[big] = (C[big] + 1) / 2;
+  }
+  pl.smem[0] = stage_smem(g, group_size[0], 1);
+  pl.smem[1] = stages == 2 ? stage_smem(g, group_size[1], 2) : 0;
+  pl.smem[2] = stage_smem(g, pl.Mmax, nreg_max);
+  // schedule geometry on the full shape
+  SGeom &s = pl.s;
+  memset(&s, 0, sizeof(s));
+  s.ndim = ndim;
+  s.schedule = pr.schedule;
+  s.passes = pr.schedule == BMND_SCHEDULE_OFF ? 1 : pr.passes;
+  s.rho = pr.shift_density;
+  s.D = D;
+  s.nslots = 1;
+  for (int d = 0; d < ndim; ++d) {
+    s.j[d] = patch[d];
+    s.h[d] = step[d];
+    s.ell[d] = shape[d] - patch[d];
+    s.Z[d] = (s.ell[d] + step[d] - 1) / step[d] + 1;
+    s.nslots *= s.Z[d];
+    s.kax[d] = -1;
+  }
+  for (int a = 0; a < D; ++a) s.kax[pl.kax_of[a]] = a;
+  pl.nflags = 1;
+  for (int a = D - 1; a >= 0; --a) { s.fst[a] = pl.nflags; pl.nflags *= g.ell[a] + 1; }
+  // scratch
+  size_t o = 0;
+  pl.o_flags = o; o = al256(o + (size_t)pl.nflags);
+  pl.o_refs = o; o = al256(o + (size_t)g.ntiles * g.cap * 4);
+  pl.o_rcount = o; o = al256(o + (size_t)g.ntiles * 4);
+  pl.o_partial = o; o = al256(o + (size_t)g.ntiles * g.region * 8);
+  pl.o_pilot = o; o = al256(o + (stages == 2 ? (size_t)N * 4 : 0));
+  pl.o_eta = o; o = al256(o + (mass_conserve ? (size_t)N * 4 : 0));
+  pl.o_groups = o; o = al256(o + (size_t)g.ntiles * g.cap * pl.Mmax * 4);
+  pl.o_gcount = o; o = al256(o + (size_t)g.ntiles * g.cap * 4);
+  pl.total = o;
+  return BMND_OK;
+}
+
+void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_params &pr) {
+  g.stage = stage;
+  g.M = M;
+  g.min_group = pr.min_group;
+  g.gtrans = pr.group_transform;
+  g.wmodel = pr.weight_model;
+  g.wscope = pr.weight_scope;
+  g.poisson = nz.kind == BMND_NOISE_POISSON;
+  double gamma = stage == 1 ? pr.gamma_ht : pr.gamma_wie;
+  g.gamma = (float)gamma;
+  g.bias_on = g.poisson && gamma > 0;
+  double tau = stage == 1 ? pr.tau_ht : pr.tau_wie;
+  if (tau <= 0) tau = (stage == 1 ? 3000.0 : 400.0) * g.P / (255.0 * 255.0);
+  g.tau = (float)tau;
+  g.lambda = (float)pr.lambda_ht;
+  g.s_v = (float)pr.s_v;
+  g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
+  g.s_p = (float)(g.poisson ? nz.poisson_scale : 1.0);
+  g.var_g = (float)(g.poisson ? 0.0 : nz.sigma * nz.sigma);
+}
+
+int pick_kb(const Plan &pl) {
+  int D = pl.D, jL = pl.g.jL;
+  if (D == 1 && jL == 32) return 5;
+  if (D == 1 && jL == 16) return 4;
+  if (D == 2 && jL == 8) return 8;
+  return 4;
+}
+
+bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
+  if (ctx->budget && need > ctx->budget)
+    return fail(ctx, BMND_ENOMEM, "scratch need %zu bytes exceeds budget %zu", need, ctx->budget);
+  if (need <= ctx->arena_size) return BMND_OK;
+  CU(cudaStreamSynchronize(st));
+  CU(cudaDeviceSynchronize());
+  if (ctx->arena) CU(cudaFree(ctx->arena));
+  ctx->arena = nullptr;
+  ctx->arena_size = 0;
+  size_t sz = need + need / 8;
+  if (cudaMalloc(&ctx->arena, sz) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BMND_ENOMEM, "cudaMalloc of %zu scratch bytes failed", sz);
+  }
+  ctx->arena_size = sz;
+  return BMND_OK;
+}
+
+bmnd_status stage_jobs(bmnd_ctx *ctx, const std::vector<DJob> &h, cudaStream_t st) {
+  size_t n = h.size();
+  if (n > ctx->djobs_cap) {
+    CU(cudaStreamSynchronize(st));
+    if (ctx->djobs) CU(cudaFree(ctx->djobs));
+    if (ctx->hjobs) CU(cudaFreeHost(ctx->hjobs));
+    ctx->djobs = nullptr;
+    ctx->hjobs = nullptr;
+    size_t cap = std::max<size_t>(n, 64);
+    CU(cudaMalloc(&ctx->djobs, cap * sizeof(DJob)));
+    CU(cudaMallocHost(&ctx->hjobs, cap * sizeof(DJob)));
+    ctx->djobs_cap = cap;
+    ctx->staged_pending = false;
+  }
+  if (ctx->staged_pending) CU(cudaEventSynchronize(ctx->staged));
+  memcpy(ctx->hjobs, h.data(), n * sizeof(DJob));
+  CU(cudaMemcpyAsync(ctx->djobs, ctx->hjobs, n * sizeof(DJob), cudaMemcpyHostToDevice, st));
+  CU(cudaEventRecord(ctx->staged, st));
+  ctx->staged_pending = true;
+  return BMND_OK;
+}
+
+struct JobIO {
+  const float *y;
+  float *out;
+  bmnd_noise noise;
+  int group_size[2];
+  int stages;
+  int mass_conserve;
+};
+
+bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz) {
+  if (nz.kind == BMND_NOISE_GAUSSIAN) {
+    if (!(nz.sigma >= 0)) return fail(ctx, BMND_EINVAL, "Gaussian sigma must be >= 0");
+  } else if (nz.kind == BMND_NOISE_POISSON) {
+    if (!(nz.poisson_scale > 0)) return fail(ctx, BMND_EINVAL, "Poisson scale must be > 0");
+  } else {
+    return fail(ctx, BMND_EINVAL, "unknown noise kind %d", nz.kind);
+  }
+  return BMND_OK;
+}
+
+// Run both requested stages of several arrays with shared launches.  All
+// plans must have the same kernel rank D.  first_stage/last_stage select a
+// sub-range (bmnd_stage runs one stage with an external pilot).
+bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<JobIO> &io,
+                     const bmnd_params &pr, int first_stage, int last_stage, const float *ext_pilot,
+                     cudaStream_t st) {
+  int nj = (int)plans.size();
+  int D = plans[0].D;
+  for (auto &pl : plans)
+    if (pl.D != D) return fail(ctx, BMND_EUNSUPPORTED, "batched jobs must share the number of non-singleton axes");
+  std::vector<size_t> base(nj);
+  size_t need = 0;
+  for (int i = 0; i < nj; ++i) { base[i] = need; need = al256(need + plans[i].total); }
+  bmnd_status rc = ensure_arena(ctx, need, st);
+  if (rc != BMND_OK) return rc;
+  char *A = (char *)ctx->arena;
+  // job tables: [stage 1 | stage 2]
+  std::vector<DJob> h(2 * nj);
+  int tiles = 0;
+  int64_t vox = 0;
+  int smax[2] = {0, 0};
+  bool any_mc[2] = {false, false};
+  for (int i = 0; i < nj; ++i) {
+    Plan &pl = plans[i];
+    char *B = A + base[i];
+    for (int s = 1; s <= 2; ++s) {
+      DJob &J = h[(s - 1) * nj + i];
+      memset(&J, 0, sizeof(J));
+      J.g = pl.g;
+      int M = io[i].group_size[s - 1];
+      fill_stage(J.g, s, M, io[i].noise, pr);
+      bool mc = (io[i].mass_conserve >> (s - 1)) & 1;
+      bool last = s == io[i].stages || s == last_stage;
+      float *pilot = (float *)(B + pl.o_pilot);
+      if (s == 1 && first_stage == 2) continue;
+      J.y = io[i].y;
+      J.guide = s == 1 ? io[i].y : (ext_pilot ? ext_pilot : pilot);
+      J.out = last ? io[i].out : pilot;
+      J.eta = mc ? (float *)(B + pl.o_eta) : nullptr;
+      J.partial = (float2 *)(B + pl.o_partial);
+      J.ref_local = (const int *)(B + pl.o_refs);
+      J.ref_count = (const int *)(B + pl.o_rcount);
+      J.groups = mc ? (int *)(B + pl.o_groups) : nullptr;
+      J.gcount = mc ? (int *)(B + pl.o_gcount) : nullptr;
+      J.tile_base = tiles;
+      J.vox_base = vox;
+      if (mc) any_mc[s - 1] = true;
+      smax[s - 1] = std::max(smax[s - 1], mc ? std::max(pl.smem[s - 1], pl.smem[2]) : pl.smem[s - 1]);
+    }
+    tiles += pl.g.ntiles;
+    vox += pl.g.N;
+  }
+  rc = stage_jobs(ctx, h, st);
+  if (rc != BMND_OK) return rc;
+  // schedule of every job (shared by both stages)
+  for (int i = 0; i < nj; ++i) {
+    Plan &pl = plans[i];
+    char *B = A + base[i];
+    CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
+    launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), ctx->djobs + (first_stage == 2 ? nj : 0) + i,
+                 pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
+  }
+  CU(cudaGetLastError());
+  stage_fn f = select_stage_kernel(D, plans[0].g.jL, pick_kb(plans[0]));
+  for (int i = 1; i < nj; ++i)
+    if (plans[i].g.jL != plans[0].g.jL) f = select_stage_kernel(D, 0, 4);
+  int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
+  for (int s = first_stage; s <= last_stage; ++s) {
+    const DJob *dj = ctx->djobs + (s - 1) * nj;
+    CU(set_stage_smem(f, smax[s - 1]));
+    f<<<tiles, NW * 32, smax[s - 1], st>>>(dj, nj, 0, ctx->tab);
+    CU(cudaGetLastError());
+    launch_reduce(D, dj, nj, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
+    CU(cudaGetLastError());
+    if (any_mc[s - 1]) {
+      f<<<tiles, NW * 32, smax[s - 1], st>>>(dj, nj, 2, ctx->tab);
+      CU(cudaGetLastError());
+      launch_reduce(D, dj, nj, vox, 0, rgrid, st);
+      CU(cudaGetLastError());
+    }
+  }
+  return BMND_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void bmnd_default_params(bmnd_params *p) {
+  if (!p) return;
+  p->lambda_ht = 3.0;
+  p->gamma_ht = 3.0;
+  p->gamma_wie = 0.0;
+  p->tau_ht = 0.0;
+  p->tau_wie = 0.0;
+  p->s_v = 0.4;
+  p->kaiser_beta = 2.0;
+  p->shift_density = 2.0;
+  p->passes = 2;
+  p->schedule = BMND_SCHEDULE_GENERATED;
+  p->power_mode = BMND_POWER_CLASSIC;
+  p->group_transform = BMND_GROUP_HAAR;
+  p->min_group = 2;
+  p->weight_model = BMND_WEIGHT_VARIANCE;
+  p->weight_scope = BMND_SCOPE_PATCH;
+}
+
+bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {
+  if (!out) return BMND_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return BMND_EINVAL;
+  }
+  bmnd_ctx *ctx = new bmnd_ctx();
+  ctx->device = device;
+  ctx->budget = scratch_budget_bytes;
+  bmnd_status rc = BMND_OK;
+  do {
+    if (cudaSetDevice(device) != cudaSuccess) { rc = BMND_ECUDA; break; }
+    if (cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+      rc = BMND_ECUDA;
+      break;
+    }
+    rc = init_constants(ctx);
+    if (rc != BMND_OK) break;
+    std::vector<float> t(2 * GEN_TOTAL);
+    for (int J = 1; J <= 32; ++J) {
+      int off = (J - 1) * J * (2 * J - 1) / 6;
+      for (int k = 0; k < J; ++k)
+        for (int i = 0; i < J; ++i) {
+          double v = dct_entry(J, k, i);
+          t[off + k * J + i] = (float)v;
+          t[GEN_TOTAL + off + k * J + i] = (float)(v * v);
+        }
+    }
+    if (cudaMalloc(&ctx->tab, sizeof(float) * t.size()) != cudaSuccess) { rc = BMND_ENOMEM; break; }
+    if (cudaMemcpy(ctx->tab, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = BMND_ECUDA;
+      break;
+    }
+    if (cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess) { rc = BMND_ECUDA; break; }
+  } while (0);
+  if (rc != BMND_OK) {
+    cudaGetLastError();
+    bmnd_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return BMND_OK;
+}
+
+bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
+  if (!ctx) return BMND_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->tab) cudaFree(ctx->tab);
+  if (ctx->djobs) cudaFree(ctx->djobs);
+  if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
+  if (ctx->staged) cudaEventDestroy(ctx->staged);
+  delete ctx;
+  return BMND_OK;
+}
+
+const char *bmnd_last_error(const bmnd_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+bmnd_status bmnd_denoise_ex(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape,
+                            bmnd_noise noise, const int *patch, const int *step, const int *search,
+                            const int *group_size, int stages, int mass_conserve,
+                            const bmnd_params *params, float *out, void *stream) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (!y || !out) return fail(ctx, BMND_EINVAL, "null y or out");
+  if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  bmnd_status rc = check_noise(ctx, noise);
+  if (rc != BMND_OK) return rc;
+  if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
+  CU(cudaSetDevice(ctx->device));
+  std::vector<Plan> plans(1);
+  rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, plans[0]);
+  if (rc != BMND_OK) return rc;
+  int64_t N = plans[0].g.N;
+  if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
+  JobIO io{y, out, noise, {group_size[0], stages == 2 ? group_size[1] : group_size[0]}, stages,
+           mass_conserve & (stages == 2 ? 3 : 1)};
+  return run_jobs(ctx, plans, {io}, pr, 1, stages, nullptr, (cudaStream_t)stream);
+}
+
+bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape,
+                         bmnd_noise noise, const int *patch, const int *step, const int *search,
+                         const int *group_size, int stages, int mass_conserve, float *out,
+                         void *stream) {
+  return bmnd_denoise_ex(ctx, y, ndim, shape, noise, patch, step, search, group_size, stages,
+                         mass_conserve, nullptr, out, stream);
+}
+
+bmnd_status bmnd_stage(bmnd_ctx *ctx, const float *y, const float *pilot, int ndim,
+                       const int64_t *shape, bmnd_noise noise, const int *patch, const int *step,
+                       const int *search, int group_max, int stage, int mass_conserve,
+                       const bmnd_params *params, float *out, void *stream) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (!y || !out) return fail(ctx, BMND_EINVAL, "null y or out");
+  if (stage != 1 && stage != 2) return fail(ctx, BMND_EINVAL, "stage must be 1 or 2");
+  if (stage == 2 && !pilot) return fail(ctx, BMND_EINVAL, "stage 2 needs a pilot");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  bmnd_status rc = check_noise(ctx, noise);
+  if (rc != BMND_OK) return rc;
+  CU(cudaSetDevice(ctx->device));
+  int gs[2] = {group_max, group_max};
+  std::vector<Plan> plans(1);
+  int mc = mass_conserve ? (stage == 1 ? 1 : 2) : 0;
+  rc = make_plan(ctx, ndim, shape, patch, step, search, gs, stage, mc, pr, plans[0]);
+  if (rc != BMND_OK) return rc;
+  int64_t N = plans[0].g.N;
+  if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
+  if (pilot && !(pilot + N <= out || out + N <= pilot)) return fail(ctx, BMND_EINVAL, "out overlaps pilot");
+  JobIO io{y, out, noise, {group_max, group_max}, stage, mc};
+  return run_jobs(ctx, plans, {io}, pr, stage, stage, pilot, (cudaStream_t)stream);
+}
+
+static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim, const int64_t *shape,
+                                      bmnd_noise noise, const int *patch, const int *step,
+                                      const int *search, int group_max, int stage,
+                                      const bmnd_params *params, int64_t *origins, int64_t *groups,
+                                      int32_t *counts, int64_t cap, int64_t *n_refs, void *stream,
+                                      bool do_match) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (!n_refs || !origins) return fail(ctx, BMND_EINVAL, "null origins or n_refs");
+  if (do_match && (!guide || !groups || !counts)) return fail(ctx, BMND_EINVAL, "null guide/groups/counts");
+  if (do_match && stage != 1 && stage != 2) return fail(ctx, BMND_EINVAL, "stage must be 1 or 2");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  if (do_match) {
+    bmnd_status rc = check_noise(ctx, noise);
+    if (rc != BMND_OK) return rc;
+  }
+  static const int ones[BMND_MAX_NDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  if (!do_match) search = ones;
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  int gs[2] = {do_match ? group_max : 1, do_match ? group_max : 1};
+  Plan pl;
+  bmnd_status rc = make_plan(ctx, ndim, shape, patch, step, search, gs, do_match && stage == 2 ? 2 : 1, 0,
+                             pr, pl);
+  if (rc != BMND_OK) return rc;
+  size_t tileoff_bytes = al256((size_t)pl.g.ntiles * 8);
+  rc = ensure_arena(ctx, pl.total + tileoff_bytes, st);
+  if (rc != BMND_OK) return rc;
+  char *B = (char *)ctx->arena;
+  DJob J;
+  memset(&J, 0, sizeof(J));
+  J.g = pl.g;
+  fill_stage(J.g, stage == 2 ? 2 : 1, gs[0], noise, pr);
+  J.y = guide;
+  J.guide = guide;
+  J.ref_local = (const int *)(B + pl.o_refs);
+  J.ref_count = (const int *)(B + pl.o_rcount);
+  J.groups = (int *)(B + pl.o_groups);
+  J.gcount = (int *)(B + pl.o_gcount);
+  std::vector<DJob> h{J};
+  rc = stage_jobs(ctx, h, st);
+  if (rc != BMND_OK) return rc;
+  CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
+  launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), ctx->djobs, pl.g.ntiles, (int *)(B + pl.o_refs),
+               (int *)(B + pl.o_rcount), st);
+  CU(cudaGetLastError());
+  if (do_match) {
+    stage_fn f = select_stage_kernel(pl.D, pl.g.jL, pick_kb(pl));
+    int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
+    CU(set_stage_smem(f, sm));
+    f<<<pl.g.ntiles, NW * 32, sm, st>>>(ctx->djobs, 1, 1, ctx->tab);
+    CU(cudaGetLastError());
+  }
+  std::vector<int> cnt(pl.g.ntiles);
+  CU(cudaMemcpyAsync(cnt.data(), B + pl.o_rcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<int64_t> off(pl.g.ntiles);
+  int64_t tot = 0;
+  for (int t = 0; t < pl.g.ntiles; ++t) { off[t] = tot; tot += cnt[t]; }
+  *n_refs = tot;
+  int64_t *doff = (int64_t *)(B + pl.total);
+  CU(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st));
+  launch_export(pl.D, ctx->djobs, pl.g.ntiles, doff, origins, do_match ? groups : nullptr,
+                do_match ? counts : nullptr, cap, st);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  if (tot > cap) return fail(ctx, BMND_ENOMEM, "capacity %lld < %lld references", (long long)cap, (long long)tot);
+  return BMND_OK;
+}
+
+bmnd_status bmnd_schedule(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch,
+                          const int *step, const bmnd_params *params, int64_t *origins,
+                          int64_t cap, int64_t *n_refs, void *stream) {
+  bmnd_noise nz{BMND_NOISE_GAUSSIAN, 0.0, 1.0};
+  return match_or_schedule(ctx, nullptr, ndim, shape, nz, patch, step, nullptr, 1, 1, params, origins,
+                           nullptr, nullptr, cap, n_refs, stream, false);
+}
+
+bmnd_status bmnd_match(bmnd_ctx *ctx, const float *guide, int ndim, const int64_t *shape,
+                       bmnd_noise noise, const int *patch, const int *step, const int *search,
+                       int group_max, int stage, const bmnd_params *params, int64_t *origins,
+                       int64_t *groups, int32_t *counts, int64_t cap, int64_t *n_refs,
+                       void *stream) {
+  return match_or_schedule(ctx, guide, ndim, shape, noise, patch, step, search, group_max, stage, params,
+                           origins, groups, counts, cap, n_refs, stream, true);
+}
+
+bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
+                               const bmnd_params *params, void *stream) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (n_jobs < 1 || !jobs) return fail(ctx, BMND_EINVAL, "no jobs");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  CU(cudaSetDevice(ctx->device));
+  std::vector<Plan> plans(n_jobs);
+  std::vector<JobIO> io(n_jobs);
+  int stages = jobs[0].stages;
+  for (int i = 0; i < n_jobs; ++i) {
+    const bmnd_job &jb = jobs[i];
+    if (!jb.y || !jb.out) return fail(ctx, BMND_EINVAL, "job %d: null y or out", i);
+    bmnd_status rc = check_noise(ctx, jb.noise);
+    if (rc != BMND_OK) return rc;
+    if (jb.stages != stages) return fail(ctx, BMND_EUNSUPPORTED, "job %d: all jobs must use the same stage count", i);
+    if (jb.mass_conserve < 0 || jb.mass_conserve > 3) return fail(ctx, BMND_EINVAL, "job %d: bad mass_conserve", i);
+    rc = make_plan(ctx, jb.ndim, jb.shape, jb.patch, jb.step, jb.search, jb.group_size, jb.stages,
+                   jb.mass_conserve, pr, plans[i]);
+    if (rc != BMND_OK) return rc;
+    int64_t N = plans[i].g.N;
+    if (!(jb.y + N <= jb.out || jb.out + N <= jb.y)) return fail(ctx, BMND_EINVAL, "job %d: out overlaps y", i);
+    io[i] = JobIO{jb.y, jb.out, jb.noise, {jb.group_size[0], stages == 2 ? jb.group_size[1] : jb.group_size[0]},
+                  stages, jb.mass_conserve & (stages == 2 ? 3 : 1)};
+  }
+  return run_jobs(ctx, plans, io, pr, 1, stages, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Device side of the B300 BMND denoiser (sm_103a).
+//
+// Work decomposition.  The reference origins of one array are partitioned into
+// tiles: a tile owns the origins r with r_d in [t_d C_d, t_d C_d + C_d).  All
+// candidate patches of those references lie in the tile's *region*
+// [t_d C_d - rad_d, t_d C_d + C_d - 1 + rad_d + j_d - 1], so one CTA stages the
+// region of the guide (and of the observation) in shared memory once and runs
+// matching, the group transform, shrinkage, the inverse transform and the
+// Kaiser-weighted overlap-add for every reference of the tile out of it.
+//
+// Aggregation is atomic-free and deterministic: warps accumulate their groups
+// into the tile's shared (numerator, weight) region one after another, in
+// reference order, handing the turn on with named barriers; each tile then
+// writes its region as a partial, and a reduce kernel sums the partials of the
+// tiles covering every location in tile order before normalizing
+// (Def. "Weighted overlap-add estimate").  The result therefore does not depend
+// on scheduling, on the number of jobs in a batched launch, or on timing.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bmnd {
+
+constexpr int KMAXD = 6;     // non-singleton axes handled by the kernels
+constexpr int MMAX = 32;     // maximum group size
+constexpr int JMAX = 32;     // maximum patch length per axis
+constexpr int NW = 8;        // warps per CTA of the stage kernel
+constexpr int RPAD = 40;     // floats of padding after every shared region
+
+// Dense orthonormal DCT-II matrices of the sizes with register-resident line
+// transforms, forward then entrywise squared (the latter propagates diagonal
+// variances, Prop. "Diagonal Poisson variance propagation").
+constexpr int DCT_TOTAL = 1484;
+__host__ __device__ constexpr int dct_off(int J) {
+  return J == 1 ? 0 : J == 2 ? 1 : J == 3 ? 5 : J == 4 ? 14 : J == 5 ? 30 : J == 6 ? 55
+       : J == 7 ? 91 : J == 8 ? 140 : J == 16 ? 204 : J == 32 ? 460 : -1;
+}
+// Uploads the forward and squared tables (2 * DCT_TOTAL floats) to the
+// constant bank of the current device.
+cudaError_t upload_dct_constants(const float *h);
+
+// Generic DCT table in global memory: sizes 1..32 at offset (J-1)J(2J-1)/6,
+// then the entrywise squares at +GEN_TOTAL.
+constexpr int GEN_TOTAL = 11440;
+
+// Per-array geometry of one stage, with singleton axes removed.
+struct DGeom {
+  int D;
+  int P;        // patch entries
+  int rows;     // P / jL
+  int jL;       // patch length on the last axis
+  int LS;       // shared-buffer line stride (jL, padded to odd)
+  int MS;       // shared-buffer member stride (rows * LS)
+  int region;   // prod RG
+  int ntiles;
+  int cap;      // prod C: capacity of the per-tile reference list
+  int stage;    // 1 hard threshold, 2 Wiener
+  int M;        // maximum group size
+  int min_group;
+  int gtrans;   // 0 Haar, 1 DCT along the group axis
+  int wmodel;   // 0 classic, 1 variance, 2 risk
+  int wscope;   // 0 patch, 1 group
+  int poisson;
+  int bias_on;  // stage-1 SSD noise-bias correction active
+  float gamma, tau, lambda, s_v, a_power, s_p, var_g;
+  int64_t N;
+  int64_t L[KMAXD], st[KMAXD], ell[KMAXD];
+  int j[KMAXD], rad[KMAXD];
+  int C[KMAXD], NT[KMAXD], RG[KMAXD], rst[KMAXD];
+  float kaiser[KMAXD][JMAX];
+};
+
+struct DJob {
+  DGeom g;
+  const float *y;      // observation
+  const float *guide;  // matching guide and variance-map source (y or pilot)
+  float *out;          // stage estimate
+  float *eta;          // overlap-add denominator (mass conservation)
+  float2 *partial;     // ntiles * region (numerator, weight)
+  const int *ref_local;  // ntiles * cap core-local reference indices
+  const int *ref_count;  // ntiles
+  int *groups;         // ntiles * cap * M region offsets of members (or null)
+  int *gcount;         // ntiles * cap group sizes
+  int tile_base;       // first tile of this job in a batched grid
+  int pad0;
+  int64_t vox_base;    // first location of this job in a batched reduce
+};
+
+// Schedule geometry on the full (unsqueezed) shape.
+struct SGeom {
+  int ndim;
+  int schedule;   // 0 generated, 1 off, 2 sparse, 3 balanced
+  int passes;
+  int D;          // kernel axes
+  double rho;
+  int64_t Z[8], ell[8];
+  int j[8], h[8];
+  int kax[8];     // kernel axis of each full axis (-1 if singleton)
+  int64_t fst[KMAXD];  // strides of the origin grid over kernel axes
+  int64_t nslots;
+};
+
+}  // namespace bmnd
