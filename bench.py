@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 BMND denoiser: denoised voxels/s, both stages.
+
+One step = one pass of both stages over one synthetic batch resident in HBM.
+Default workload: the 1-D ECG-like signal of 262144 samples (Poisson, peak 50,
+patch 32, step 4, search 129, groups 16/32).  Other workloads: --workload c1
+(2-D 64x64), c3 (32 images of 512x512 in one batched call), c4 (3-D 128^3
+with mass conservation).
+
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on
+the launching stream; L2 is flushed (256 MiB write) before every timed step,
+outside the events.  N > 1 (torchrun): independent replicas, one per GPU,
+each on its own seeded instance of the workload; value = all ranks' voxels /
+max-over-ranks time.  --impl reference times the FP64 CPU oracle on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_34622_b300 import synth  # noqa: E402
+
+METRIC = "denoised voxels/s (both stages)"
+UNIT = "voxels/s"
+SMS = 148
+FP32_LANES = 128
+
+
+def workload(name: str, item: int):
+    if name == "c1":
+        j = synth.config1(item)
+        return [j], "2-D 64x64 discs/rectangles, Poisson peak 10, patch 8x8, step 3, search 19x19, groups 16/32"
+    if name == "c2":
+        j = synth.config2(item)
+        return [j], ("1-D ECG-like signal, 262144 samples, Poisson peak 50, patch 32, step 4, search 129, "
+                     "groups 16/32, both stages")
+    if name == "c3":
+        jobs = synth.config3()
+        return jobs, ("2-D batch: 16 images 512x512 Poisson (peaks 1,2,5,10,30) + the same 16 with Gaussian "
+                      "sigma 25/255, patch 8x8, step 3, search 39x39, groups 16/32, one batched call")
+    if name == "c4":
+        j = synth.config4(item)
+        return [j], ("3-D 128^3 ellipsoid phantom, Poisson 0.5-5 counts, patch 4x4x4, step 2, search 11^3, "
+                     "groups 16/32, mass conservation in both stages")
+    raise SystemExit("unknown workload %s" % name)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return res
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return res
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 2032)] or sm
+        res.update(sm_mhz=statistics.median(busy) if busy else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return res
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the stage kernel
+# ---------------------------------------------------------------------------
+
+def window_counts(origins: np.ndarray, shape, patch, search) -> np.ndarray:
+    """Candidates per reference (clipped window, reference included)."""
+    coords = np.stack(np.unravel_index(origins, shape), axis=1)
+    n = np.ones(len(origins), np.int64)
+    for d, (L, j, w) in enumerate(zip(shape, patch, search)):
+        rad = (w - 1) // 2
+        lo = np.maximum(coords[:, d] - rad, 0)
+        hi = np.minimum(coords[:, d] + rad, L - j)
+        n *= hi - lo + 1
+    return n
+
+
+def stage_flops(ncand: np.ndarray, counts: np.ndarray, patch, stage: int, poisson: bool) -> float:
+    """Algorithmic FP32 operations of one stage-kernel launch.
+
+    matching: per candidate and patch entry, sub + fma (3), plus add + max +
+    add (3) for the Poisson noise bias of stage 1;
+    per group of n members and P entries: each dense DCT line of length j costs
+    2 j^2 (2 n P j per axis); the Haar along the group costs 4 n P; the
+    transforms run: variance (Poisson only, squared matrices), guide forward,
+    observation forward (stage 2), inverse; gather/shrink/weights ~10 n P;
+    weighted accumulation 4 n P."""
+    P = int(np.prod(patch))
+    per_entry = 6.0 if (stage == 1 and poisson) else 3.0
+    match = float(np.sum(ncand - 1)) * P * per_entry
+    n = counts.astype(np.float64)
+    one_xform = 2.0 * n * P * float(np.sum(patch)) + 4.0 * n * P
+    nx = 2 + (1 if poisson else 0) + (1 if stage == 2 else 0)
+    filt = float(np.sum(nx * one_xform + 14.0 * n * P))
+    return match + filt
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(name: str, jobs):
+    """A bounded sample of the workload for the CPU oracle."""
+    if name in ("c1", "c2"):
+        return jobs[:1], "the full workload (%d voxels)" % jobs[0].y.size
+    if name == "c3":
+        j = jobs[0]
+        y = np.ascontiguousarray(j.y[:96, :96])
+        return [synth.Job(y, j.x[:96, :96], j.noise, j.patch, j.step, j.search)], \
+            "a 96x96 crop of image 0 of the batch"
+    j = jobs[0]
+    y = np.ascontiguousarray(j.y[:32, :32, :32])
+    return [synth.Job(y, j.x[:32, :32, :32], j.noise, j.patch, j.step, j.search, j.group_size, 2, 3)], \
+        "a 32^3 crop of the volume"
+
+
+def time_oracle(jobs, min_seconds: float, max_reps: int = 1000):
+    import oracle
+    oracle.build()
+    vox, t0, reps = 0, time.perf_counter(), 0
+    while True:
+        for j in jobs:
+            p = oracle.params(j.y.shape, j.patch, j.step, j.search, j.noise, j.group_size, j.stages,
+                              j.mass_conserve)
+            oracle.denoise(p, j.y)
+            vox += j.y.size
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            return vox / el, el, reps, oracle.num_threads()
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        jobs, desc = workload(args.workload, 0)
+        sample, sdesc = oracle_sample(args.workload, jobs)
+        vox = sum(j.y.size for j in sample)
+        for _ in range(args.warmup):
+            time_oracle(sample, 0.0, 1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            time_oracle(sample, 0.0, 1)
+        el = time.perf_counter() - t0
+        import oracle
+        val = vox * args.steps / el
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": desc, "sample": sdesc},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": sdesc},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_2609_34622_b300.bmnd as bm
+    from paper_2609_34622_b300 import build as B
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+
+    jobs, desc = workload(args.workload, rank)
+    ctx = bm.Context(local)
+    stream = torch.cuda.current_stream()
+    ys = [torch.from_numpy(j.y).to(dev) for j in jobs]
+    outs = [torch.empty_like(y) for y in ys]
+    cfgs = [j.cfg for j in jobs]
+    vox_step = sum(j.y.size for j in jobs)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def step(yy, oo):
+        if len(jobs) == 1:
+            c = cfgs[0]
+            ctx.bmnd_denoise(yy[0], oo[0], c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
+                             c["stages"], c["mass_conserve"], stream=stream)
+        else:
+            ctx.bmnd_denoise_batch(yy, oo, cfgs, stream=stream)
+
+    # algorithmic work per stage launch (outside any timing)
+    flops = {1: 0.0, 2: 0.0}
+    for j, y in zip(jobs, ys):
+        c = j.cfg
+        o, _, cnt1 = ctx.bmnd_match(y, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1)
+        pilot = torch.empty_like(y)
+        ctx.bmnd_stage(y, None, pilot, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1,
+                       c["mass_conserve"] & 1)
+        _, _, cnt2 = ctx.bmnd_match(pilot, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][1], 2)
+        ncand = window_counts(o.cpu().numpy(), j.y.shape, c["patch"], c["search"])
+        pois = c["noise"][0] == "poisson"
+        flops[1] += stage_flops(ncand, cnt1.cpu().numpy(), c["patch"], 1, pois)
+        flops[2] += stage_flops(ncand, cnt2.cpu().numpy(), c["patch"], 2, pois)
+        if c["mass_conserve"]:
+            # the second sweep repeats the filtering (not the matching)
+            pass
+
+    for _ in range(args.warmup):
+        step(ys, outs)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing ----
+    ctx.bmnd_set_profiling(True)
+    ctx.bmnd_kernel_stats(reset=True)
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(ys, outs)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kstats = ctx.bmnd_kernel_stats(reset=True)
+    ctx.bmnd_set_profiling(False)
+
+    # ---- end to end: pinned host input -> device -> both stages -> host ----
+    hy = [torch.from_numpy(j.y).pin_memory() for j in jobs]
+    ho = [torch.empty(j.y.shape, dtype=torch.float32).pin_memory() for j in jobs]
+    dy = [torch.empty_like(y) for y in ys]
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev2[k][0].record(stream)
+        for h, d in zip(hy, dy):
+            d.copy_(h, non_blocking=True)
+        step(dy, outs)
+        for h, o in zip(ho, outs):
+            h.copy_(o, non_blocking=True)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+
+    if dist:
+        t = torch.tensor([dev_ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, e2e_ms = float(t[0]), float(t[1])
+
+    total_vox = vox_step * args.steps * world
+    value = total_vox / (dev_ms / 1e3)
+    e2e_val = total_vox / (e2e_ms / 1e3)
+
+    # roofline of the dominant kernel (the stage kernel, both stages)
+    n1, ms1 = kstats["stage1"]
+    n2, ms2 = kstats["stage2"]
+    stage_ms = ms1 + ms2
+    stage_flop = flops[1] * n1 + flops[2] * n2
+    achieved = stage_flop / (stage_ms / 1e3) / 1e12 if stage_ms > 0 else None
+    mhz = clk["sm_mhz"] or 2032.0
+    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    launches = sum(v[0] for v in kstats.values()) + kstats["schedule"][0]  # schedule = mark + compact
+    step_ms_total = sum(v[1] for v in kstats.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "voxels_per_step_per_gpu": vox_step, "l2": "flushed (256 MiB) before each step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                   "samples": clk["samples"]},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * vox_step, "d2h_bytes_per_step": 4 * vox_step},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None,
+                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median sampled SM clock)" % mhz,
+                     "stage_kernel_ms_per_step": stage_ms / args.steps,
+                     "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
+                     "share_of_step": stage_ms / step_ms_total if step_ms_total else None},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, sdesc = oracle_sample(args.workload, jobs)
+        v, el, reps, cores = time_oracle(sample, 10.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%s, both stages, %d repetition(s), %.1f s" % (sdesc, reps, el)}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,19 @@ typedef struct {
 bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
                                const bmnd_params *params, void *stream);
 
+/* Per-kernel timing, for measurement only (the paper has no counterpart).
+ * With profiling enabled, every kernel launched by the context is bracketed by
+ * CUDA events recorded on the launch stream.  bmnd_kernel_stats() synchronizes
+ * the context's device, folds the recorded pairs into per-kind totals and
+ * returns, for one kind, the number of launches and their summed duration in
+ * milliseconds since the last reset (reset != 0 clears all totals after
+ * reading).  Kinds: */
+enum { BMND_KERNEL_SCHEDULE = 0, BMND_KERNEL_STAGE1 = 1, BMND_KERNEL_STAGE2 = 2,
+       BMND_KERNEL_REDUCE = 3, BMND_KERNEL_MC_SWEEP = 4, BMND_KERNEL_KINDS = 5 };
+bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable);
+bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches,
+                              double *total_ms);
+
 #ifdef __cplusplus
 }
 #endif

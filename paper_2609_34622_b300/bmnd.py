@@ -55,7 +55,9 @@ class bmnd_job(ctypes.Structure):
 
 
 EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_error", "bmnd_denoise",
-           "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch"]
+           "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
+           "bmnd_set_profiling", "bmnd_kernel_stats"]
+KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4}
 
 _lib = None
 
@@ -86,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.bmnd_match.argtypes = [vp, vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ctypes.c_int,
                                ctypes.c_int, P(bmnd_params), vp, vp, vp, ctypes.c_int64, i64p, vp]
     lib.bmnd_denoise_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
+    lib.bmnd_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.bmnd_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -263,6 +267,23 @@ class Context:
                                           _stream(stream))
         self._check(st)
         return outs
+
+
+    def bmnd_set_profiling(self, enable: bool):
+        self._check(self._lib.bmnd_set_profiling(self.handle, int(bool(enable))))
+
+    def bmnd_kernel_stats(self, reset: bool = False) -> dict:
+        """{kind: (launches, total_ms)} for every kernel kind; reset clears after reading."""
+        res = {}
+        kinds = list(KERNEL_KINDS.items())
+        for i, (name, k) in enumerate(kinds):
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            last = i == len(kinds) - 1
+            self._check(self._lib.bmnd_kernel_stats(self.handle, k, int(reset and last), ctypes.byref(n),
+                                                    ctypes.byref(ms)))
+            res[name] = (n.value, ms.value)
+        return res
 
 
 def denoise(y, cfg: dict, ctx: Context | None = None, prm=None, stream=None):

@@ -15,7 +15,7 @@
 #include <vector>
 
 namespace bmnd {
-typedef void (*stage_fn)(const DJob *, int, int, const float *);
+typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 stage_fn select_stage_kernel(int D, int jL, int kb);
 void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,
                    cudaStream_t st);
@@ -41,12 +41,18 @@ struct bmnd_ctx {
   cudaEvent_t staged = nullptr;
   bool staged_pending = false;
   int max_smem = 0;
+  int num_sms = 0;
+  int *counters = nullptr;     // persistent-kernel tile counters
+  // per-kernel timing (bmnd_set_profiling)
+  bool profiling = false;
+  struct Mark { int kind; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t k_launches[BMND_KERNEL_KINDS] = {0};
+  double k_ms[BMND_KERNEL_KINDS] = {0};
 };
 
 namespace {
-
-std::mutex g_const_mu;
-bool g_const_ready[64] = {false};
 
 bmnd_status fail(bmnd_ctx *ctx, bmnd_status st, const char *fmt, ...) {
   if (ctx) {
@@ -89,22 +95,54 @@ double kaiser_at(int n, int i, double beta) {
   return bessel_i0(beta * std::sqrt(a > 0 ? a : 0.0)) / bessel_i0(beta);
 }
 
+std::mutex g_const_mu;
+bool g_const_ready[64] = {false};
+
+// Constants of the butterfly DCT (once per device).
 bmnd_status init_constants(bmnd_ctx *ctx) {
   std::lock_guard<std::mutex> lk(g_const_mu);
   if (ctx->device < 64 && g_const_ready[ctx->device]) return BMND_OK;
-  std::vector<float> h(2 * DCT_TOTAL);
-  const int sizes[] = {1, 2, 3, 4, 5, 6, 7, 8, 16, 32};
-  for (int J : sizes)
-    for (int k = 0; k < J; ++k)
-      for (int i = 0; i < J; ++i) {
-        double v = dct_entry(J, k, i);
-        h[dct_off(J) + k * J + i] = (float)v;
-        h[DCT_TOTAL + dct_off(J) + k * J + i] = (float)(v * v);
-      }
-  CU(upload_dct_constants(h.data()));
+  float sec[31], scale[12];
+  for (int N = 2; N <= 32; N *= 2)
+    for (int n = 0; n < N / 2; ++n) sec[N / 2 - 1 + n] = (float)(1.0 / (2.0 * std::cos(M_PI * (2.0 * n + 1.0) / (2.0 * N))));
+  for (int l = 0; l <= 5; ++l) {
+    double N = (double)(1 << l);
+    scale[2 * l] = (float)std::sqrt(1.0 / N);
+    scale[2 * l + 1] = (float)std::sqrt(2.0 / N);
+  }
+  CU(upload_fast_dct_constants(sec, scale));
   if (ctx->device < 64) g_const_ready[ctx->device] = true;
   return BMND_OK;
 }
+
+cudaEvent_t pool_event(bmnd_ctx *ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+  bmnd_ctx *ctx;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(bmnd_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), st(s) {
+    if (ctx->profiling && (a = pool_event(ctx))) cudaEventRecord(a, st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(ctx);
+    if (!b) { ctx->event_pool.push_back(a); return; }
+    cudaEventRecord(b, st);
+    ctx->marks.push_back({kind, a, b});
+  }
+};
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -120,6 +158,7 @@ struct Plan {
   SGeom s;
   int64_t nflags;
   int Mmax;
+  int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
   size_t o_flags, o_refs, o_rcount, o_partial, o_pilot, o_eta, o_groups, o_gcount, total;
@@ -127,10 +166,14 @@ struct Plan {
 
 int stage_smem(const DGeom &g, int M, int nreg) {
   size_t b = al16(sizeof(DJob));
-  b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4);
+  b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4 + KMAXD * 4 + (g.fp ? (size_t)g.P * 4 : 0) +
+           (size_t)g.fp * 4);
+  size_t mats = 0;
+  for (int a = 0; a < g.D; ++a) mats += (size_t)mat_block(g.j[a]) * 4;
+  b = al16(b + mats);
   b = al16(b + (size_t)nreg * (g.region + RPAD) * 4);
   b += (size_t)g.region * 8;
-  b += (size_t)NW * (3 * MMAX * 4 + 2 * (size_t)M * g.MS * 4);
+  b += (size_t)NW * warp_bytes(M, g.MS, g.fp);
   return (int)b;
 }
 
@@ -217,6 +260,17 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   g.rows = g.P / g.jL;
   g.LS = g.jL + (g.jL % 2 == 0 ? 1 : 0);
   g.MS = g.rows * g.LS;
+  if (g.MS % 2 == 0) g.MS += 1;  // odd member stride: per-member rows in distinct banks
+  // private group footprint for the accumulation when it is small
+  {
+    int64_t fp = 1;
+    for (int a = 0; a < D; ++a) {
+      g.FW[a] = 2 * g.rad[a] + g.j[a];
+      fp *= g.FW[a];
+    }
+    g.fp = 0;
+    pl.fp_candidate = fp <= 1024 ? (int)fp : 0;
+  }
   pl.Mmax = group_size[0];
   if (stages == 2) pl.Mmax = std::max(pl.Mmax, group_size[1]);
   // tile geometry: large cores within the shared-memory budget, enough tiles
@@ -236,6 +290,15 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
       break;
     }
     C[big] = (C[big] + 1) / 2;
+  }
+  // enable the private footprint if it costs no resident CTA per SM
+  if (pl.fp_candidate) {
+    const int per_sm = 233472;  // shared memory per SM
+    int without = stage_smem(g, pl.Mmax, nreg_max);
+    g.fp = pl.fp_candidate;
+    int with = stage_smem(g, pl.Mmax, nreg_max);
+    int b0 = std::min(2, per_sm / std::max(without, 1)), b1 = std::min(2, per_sm / std::max(with, 1));
+    if (with > ctx->max_smem || b1 < b0) g.fp = 0;
   }
   pl.smem[0] = stage_smem(g, group_size[0], 1);
   pl.smem[1] = stages == 2 ? stage_smem(g, group_size[1], 2) : 0;
@@ -318,6 +381,21 @@ bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
     return fail(ctx, BMND_ENOMEM, "cudaMalloc of %zu scratch bytes failed", sz);
   }
   ctx->arena_size = sz;
+  return BMND_OK;
+}
+
+// Launch the persistent stage kernel: one CTA per resident slot, tiles handed
+// out by an atomic counter that is cleared first.
+bmnd_status launch_stage(bmnd_ctx *ctx, stage_fn f, const DJob *dj, int nj, int tiles, int mode, int smem,
+                         cudaStream_t st) {
+  CU(set_stage_smem(f, smem));
+  int per_sm = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)f, NW * 32, smem));
+  if (per_sm < 1) return fail(ctx, BMND_EUNSUPPORTED, "stage kernel does not fit on an SM (%d bytes)", smem);
+  int grid = std::min(tiles, per_sm * ctx->num_sms);
+  CU(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
+  f<<<grid, NW * 32, smem, st>>>(dj, nj, tiles, mode, ctx->tab, ctx->counters);
+  CU(cudaGetLastError());
   return BMND_OK;
 }
 
@@ -422,6 +500,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     Plan &pl = plans[i];
     char *B = A + base[i];
     CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
+    ProfScope ps(ctx, BMND_KERNEL_SCHEDULE, st);
     launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), ctx->djobs + (first_stage == 2 ? nj : 0) + i,
                  pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
   }
@@ -432,15 +511,26 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
   int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = first_stage; s <= last_stage; ++s) {
     const DJob *dj = ctx->djobs + (s - 1) * nj;
-    CU(set_stage_smem(f, smax[s - 1]));
-    f<<<tiles, NW * 32, smax[s - 1], st>>>(dj, nj, 0, ctx->tab);
-    CU(cudaGetLastError());
-    launch_reduce(D, dj, nj, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
+    {
+      ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
+      rc = launch_stage(ctx, f, dj, nj, tiles, 0, smax[s - 1], st);
+    }
+    if (rc != BMND_OK) return rc;
+    {
+      ProfScope ps(ctx, BMND_KERNEL_REDUCE, st);
+      launch_reduce(D, dj, nj, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
+    }
     CU(cudaGetLastError());
     if (any_mc[s - 1]) {
-      f<<<tiles, NW * 32, smax[s - 1], st>>>(dj, nj, 2, ctx->tab);
-      CU(cudaGetLastError());
-      launch_reduce(D, dj, nj, vox, 0, rgrid, st);
+      {
+        ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
+        rc = launch_stage(ctx, f, dj, nj, tiles, 2, smax[s - 1], st);
+      }
+      if (rc != BMND_OK) return rc;
+      {
+        ProfScope ps(ctx, BMND_KERNEL_REDUCE, st);
+        launch_reduce(D, dj, nj, vox, 0, rgrid, st);
+      }
       CU(cudaGetLastError());
     }
   }
@@ -488,12 +578,16 @@ bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes)
   bmnd_status rc = BMND_OK;
   do {
     if (cudaSetDevice(device) != cudaSuccess) { rc = BMND_ECUDA; break; }
-    if (cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
       rc = BMND_ECUDA;
       break;
     }
     rc = init_constants(ctx);
     if (rc != BMND_OK) break;
+    // the static tile counter of the persistent kernel shares the CTA's shared memory
+    ctx->max_smem -= 64;
+    if (cudaMalloc(&ctx->counters, 64 * sizeof(int)) != cudaSuccess) { rc = BMND_ENOMEM; break; }
     std::vector<float> t(2 * GEN_TOTAL);
     for (int J = 1; J <= 32; ++J) {
       int off = (J - 1) * J * (2 * J - 1) / 6;
@@ -520,12 +614,43 @@ bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes)
   return BMND_OK;
 }
 
+bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->profiling = enable != 0;
+  return BMND_OK;
+}
+
+bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches, double *total_ms) {
+  if (!ctx) return BMND_EINVAL;
+  if (kind < 0 || kind >= BMND_KERNEL_KINDS) return fail(ctx, BMND_EINVAL, "unknown kernel kind %d", kind);
+  CU(cudaSetDevice(ctx->device));
+  CU(cudaDeviceSynchronize());
+  for (auto &m : ctx->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      ctx->k_ms[m.kind] += ms;
+      ctx->k_launches[m.kind] += 1;
+    }
+    ctx->event_pool.push_back(m.a);
+    ctx->event_pool.push_back(m.b);
+  }
+  ctx->marks.clear();
+  if (launches) *launches = ctx->k_launches[kind];
+  if (total_ms) *total_ms = ctx->k_ms[kind];
+  if (reset)
+    for (int k = 0; k < BMND_KERNEL_KINDS; ++k) { ctx->k_launches[k] = 0; ctx->k_ms[k] = 0; }
+  return BMND_OK;
+}
+
 bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   if (!ctx) return BMND_EINVAL;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (auto &m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->tab) cudaFree(ctx->tab);
+  if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->djobs) cudaFree(ctx->djobs);
   if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
   if (ctx->staged) cudaEventDestroy(ctx->staged);
@@ -643,9 +768,8 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   if (do_match) {
     stage_fn f = select_stage_kernel(pl.D, pl.g.jL, pick_kb(pl));
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
-    CU(set_stage_smem(f, sm));
-    f<<<pl.g.ntiles, NW * 32, sm, st>>>(ctx->djobs, 1, 1, ctx->tab);
-    CU(cudaGetLastError());
+    rc = launch_stage(ctx, f, ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
+    if (rc != BMND_OK) return rc;
   }
   std::vector<int> cnt(pl.g.ntiles);
   CU(cudaMemcpyAsync(cnt.data(), B + pl.o_rcount, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st));

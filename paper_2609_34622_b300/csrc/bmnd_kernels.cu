@@ -5,13 +5,12 @@
 #include <float.h>
 #include <limits.h>
 
+#ifndef BMND_MIN_BLOCKS
+#define BMND_MIN_BLOCKS 2
+#endif
+
 namespace bmnd {
 
-__constant__ float c_dct[2 * DCT_TOTAL];
-
-cudaError_t upload_dct_constants(const float *h) {
-  return cudaMemcpyToSymbol(c_dct, h, sizeof(float) * 2 * DCT_TOTAL);
-}
 
 // ---------------------------------------------------------------------------
 // reference schedule (Sec. 4.1)
@@ -170,6 +169,11 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 __device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -187,34 +191,14 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
 // 1-D transforms on shared-memory lines
 // ---------------------------------------------------------------------------
 
-// Orthonormal DCT-II of a line of length J held in registers.  MODE 0: C x,
-// 1: C^T x (inverse), 2: (C.^2) x.
-template <int J, int MODE>
-__device__ __forceinline__ void dct_line(float *__restrict__ buf, int base, int stride) {
-  float x[J];
-#pragma unroll
-  for (int i = 0; i < J; ++i) x[i] = buf[base + i * stride];
-#pragma unroll
-  for (int k = 0; k < J; ++k) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < J; ++i) {
-      float c = MODE == 0 ? c_dct[dct_off(J) + k * J + i]
-              : MODE == 1 ? c_dct[dct_off(J) + i * J + k]
-                          : c_dct[DCT_TOTAL + dct_off(J) + k * J + i];
-      s = fmaf(c, x[i], s);
-    }
-    buf[base + k * stride] = s;
-  }
-}
-
-// Any length J <= 32, matrices from global memory (generic fallback).
+// Any length J <= 32 with the matrix read from global memory (used for the
+// optional DCT along the group axis, whose length varies per group).
 // tab: forward matrices of all sizes 1..32 at offset (J-1)J(2J-1)/6, then the
-// entrywise squares at +GEN_TOTAL.
+// entrywise squares at +GEN_TOTAL.  mode 0: M x, 1: M^T x, 2: (M.^2) x.
 __device__ __forceinline__ int gen_off(int J) { return (J - 1) * J * (2 * J - 1) / 6; }
 
 __device__ __noinline__ void dct_line_generic(float *__restrict__ buf, int base, int stride, int J, int mode,
-                                 const float *__restrict__ tab) {
+                                              const float *__restrict__ tab) {
   float x[JMAX];
   for (int i = 0; i < J; ++i) x[i] = buf[base + i * stride];
   const float *Mt = tab + (mode == 2 ? GEN_TOTAL : 0) + gen_off(J);
@@ -222,6 +206,53 @@ __device__ __noinline__ void dct_line_generic(float *__restrict__ buf, int base,
     float s = 0.f;
     for (int i = 0; i < J; ++i) s = fmaf(mode == 1 ? __ldg(Mt + i * J + k) : __ldg(Mt + k * J + i), x[i], s);
     buf[base + k * stride] = s;
+  }
+}
+
+// Dense transform of nlines lines of length J held in a warp's shared group
+// buffer: line l starts at base_of(l) with element stride st.  M is a J x J
+// row-major matrix in shared memory (forward, transposed-for-inverse or
+// squared).  When there are fewer lines than lanes, L lanes share a line and
+// split its outputs; every lane first loads its line into registers, then the
+// warp synchronizes, then outputs are written in place.
+template <int J, typename BaseOf>
+__device__ __forceinline__ void xform_lines(float *__restrict__ buf, int nlines, BaseOf base_of, int st,
+                                            const float *__restrict__ M, int lane) {
+  int L = 1;
+  while (L * 2 * nlines <= 32 && L * 2 <= J) L *= 2;
+  const int items = nlines * L;
+  for (int i0 = 0; i0 < items; i0 += 32) {
+    const int item = i0 + lane;
+    const bool act = item < items;
+    const int l = act ? item / L : 0, sub = act ? item - (item / L) * L : 0;
+    const int base = act ? base_of(l) : 0;
+    float x[J];
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
+    }
+    __syncwarp();
+    if (act) {
+      for (int k = sub; k < J; k += L) {
+        const float *row = M + k * J;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if constexpr (J % 4 == 0) {
+#pragma unroll
+          for (int i = 0; i < J / 4; ++i) {
+            float4 c = reinterpret_cast<const float4 *>(row)[i];
+            s0 = fmaf(c.x, x[4 * i], s0);
+            s1 = fmaf(c.y, x[4 * i + 1], s1);
+            s2 = fmaf(c.z, x[4 * i + 2], s2);
+            s3 = fmaf(c.w, x[4 * i + 3], s3);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < J; ++i) s0 = fmaf(row[i], x[i], s0);
+        }
+        buf[base + k * st] = (s0 + s1) + (s2 + s3);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -263,83 +294,197 @@ __device__ __forceinline__ void haar_line(float *__restrict__ buf, int base, int
   for (int i = 0; i < N; ++i) buf[base + i * stride] = x[i];
 }
 
-__device__ __noinline__ void spatial_line(float *buf, int base, int stride, int J, int mode,
-                                          const float *tab) {
-#define BMND_DCT_CASE(JJ)                                                  \
-  case JJ:                                                                 \
-    if (mode == 0) dct_line<JJ, 0>(buf, base, stride);                     \
-    else if (mode == 1) dct_line<JJ, 1>(buf, base, stride);                \
-    else dct_line<JJ, 2>(buf, base, stride);                               \
-    break;
-  switch (J) {
-    BMND_DCT_CASE(1) BMND_DCT_CASE(2) BMND_DCT_CASE(3) BMND_DCT_CASE(4) BMND_DCT_CASE(5)
-    BMND_DCT_CASE(6) BMND_DCT_CASE(7) BMND_DCT_CASE(8) BMND_DCT_CASE(16) BMND_DCT_CASE(32)
-    default: dct_line_generic(buf, base, stride, J, mode, tab);
-  }
-#undef BMND_DCT_CASE
+template <int N>
+__device__ __forceinline__ void haar_line_mode(float *buf, int base, int stride, int mode) {
+  if (mode == 0) haar_line<N, 0>(buf, base, stride);
+  else if (mode == 1) haar_line<N, 1>(buf, base, stride);
+  else haar_line<N, 2>(buf, base, stride);
 }
 
-__device__ __noinline__ void member_line(float *buf, int base, int stride, int n, int mode, int gtrans,
-                                         const float *tab) {
-  if (gtrans == 1) { dct_line_generic(buf, base, stride, n, mode, tab); return; }
-#define BMND_HAAR_CASE(NN)                                                 \
-  case NN:                                                                 \
-    if (mode == 0) haar_line<NN, 0>(buf, base, stride);                    \
-    else if (mode == 1) haar_line<NN, 1>(buf, base, stride);               \
-    else haar_line<NN, 2>(buf, base, stride);                              \
-    break;
-  switch (n) {
-    BMND_HAAR_CASE(1) BMND_HAAR_CASE(2) BMND_HAAR_CASE(4) BMND_HAAR_CASE(8) BMND_HAAR_CASE(16)
-    BMND_HAAR_CASE(32)
-    default: break;
+// Fast DCT of power-of-two length in registers (B. G. Lee, "A new algorithm
+// to compute the discrete cosine transform", IEEE Trans. ASSP 32(6), 1984):
+// the even outputs of a length-N DCT-II are a length-N/2 DCT-II of
+// x_n + x_{N-1-n}; the odd outputs are X_{2k+1} = Y_k + Y_{k+1}, where Y is a
+// length-N/2 DCT-II of (x_n - x_{N-1-n}) / (2 cos(pi (2n+1) / (2N))), because
+// cos((2k+1) t) = (cos(2k t) + cos(2(k+1) t)) / (2 cos t).  The DCT-III
+// (transpose) follows from the same identity read backwards.
+// c_sec holds 1 / (2 cos(pi (2n+1) / (2N))) for N = 2, 4, 8, 16, 32 at offset
+// N/2 - 1 + n; c_scale holds sqrt(1/N) and sqrt(2/N) at 2 log2(N) (+1).
+__constant__ float c_sec[32];
+__constant__ float c_scale[12];
+
+cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12) {
+  cudaError_t e = cudaMemcpyToSymbol(c_sec, sec31, sizeof(float) * 31);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_scale, scale12, sizeof(float) * 12);
+}
+
+template <int N>
+struct Lee {
+  // unnormalized DCT-II, in place: X_k = sum_n x_n cos(pi (2n+1) k / (2N))
+  static __device__ __forceinline__ void fwd(float (&x)[N]) {
+    float a[N / 2], b[N / 2];
+#pragma unroll
+    for (int n = 0; n < N / 2; ++n) {
+      a[n] = x[n] + x[N - 1 - n];
+      b[n] = (x[n] - x[N - 1 - n]) * c_sec[N / 2 - 1 + n];
+    }
+    Lee<N / 2>::fwd(a);
+    Lee<N / 2>::fwd(b);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) x[2 * k] = a[k];
+#pragma unroll
+    for (int k = 0; k < N / 2 - 1; ++k) x[2 * k + 1] = b[k] + b[k + 1];
+    x[N - 1] = b[N / 2 - 1];
   }
-#undef BMND_HAAR_CASE
+  // unnormalized DCT-III, in place: x_n = sum_k X_k cos(pi (2n+1) k / (2N))
+  static __device__ __forceinline__ void inv(float (&X)[N]) {
+    float e[N / 2], p[N / 2];
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) e[k] = X[2 * k];
+    p[0] = X[1];
+#pragma unroll
+    for (int m = 1; m < N / 2; ++m) p[m] = X[2 * m + 1] + X[2 * m - 1];
+    Lee<N / 2>::inv(e);
+    Lee<N / 2>::inv(p);
+#pragma unroll
+    for (int n = 0; n < N / 2; ++n) {
+      float B = p[n] * c_sec[N / 2 - 1 + n];
+      X[n] = e[n] + B;
+      X[N - 1 - n] = e[n] - B;
+    }
+  }
+};
+template <>
+struct Lee<1> {
+  static __device__ __forceinline__ void fwd(float (&)[1]) {}
+  static __device__ __forceinline__ void inv(float (&)[1]) {}
+};
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// Orthonormal DCT of one line (length J, power of two) with stride st.
+// mode 0: C x; 1: C^T x; 2: (C.^2) x, using
+// C_ki^2 = c_k^2 (1 + cos(pi (2i+1) 2k / (2J))) / 2: the squared transform is
+// (sum_i m_i + s_k V_r) / J with V a length-J/2 DCT-II of m_i + m_{J-1-i}
+// (r = k for 0 < k < J/2 with s_k = +1, r = J - k for k > J/2 with s_k = -1,
+// and no V term for k = 0 and k = J/2).
+template <int J>
+__device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base, int st, int mode) {
+  float x[J];
+#pragma unroll
+  for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
+  const float s0 = c_scale[2 * ilog2c(J)], s1 = c_scale[2 * ilog2c(J) + 1];
+  if (mode == 0) {
+    Lee<J>::fwd(x);
+    x[0] *= s0;
+#pragma unroll
+    for (int k = 1; k < J; ++k) x[k] *= s1;
+  } else if (mode == 1) {
+    x[0] *= s0;
+#pragma unroll
+    for (int k = 1; k < J; ++k) x[k] *= s1;
+    Lee<J>::inv(x);
+  } else {
+    float S = 0.f;
+#pragma unroll
+    for (int i = 0; i < J; ++i) S += x[i];
+    const float invJ = 1.f / (float)J;
+    if constexpr (J >= 2) {
+      float a[J / 2];
+#pragma unroll
+      for (int i = 0; i < J / 2; ++i) a[i] = x[i] + x[J - 1 - i];
+      Lee<J / 2>::fwd(a);
+      x[0] = S * invJ;
+#pragma unroll
+      for (int k = 1; k < J / 2; ++k) x[k] = (S + a[k]) * invJ;
+      x[J / 2] = S * invJ;
+#pragma unroll
+      for (int k = J / 2 + 1; k < J; ++k) x[k] = (S - a[J - k]) * invJ;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < J; ++i) buf[base + i * st] = x[i];
+}
+
+// Shared-memory matrices of one patch axis: [forward | transposed | squared].
+__device__ __forceinline__ const float *axis_matrix(const float *mats, const int *moff, int a, int J, int mode) {
+  return mats + moff[a] + (mode == 0 ? 0 : (mode == 1 ? J * J : 2 * J * J));
 }
 
 // Separable group transform T = (group axis) (x) DCT_j0 (x) ... on a warp's
 // shared group buffer of n members.  mode 0: T, 1: T^T = T^{-1}, 2: T.^2.
 template <int D>
-__device__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
-                            const float *tab) {
-  // spatial axes
+__device__ __noinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
+                            const float *mats, const int *moff, const float *tab) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    int ja = g.j[a];
+    const int ja = g.j[a];
     if (ja == 1) continue;
-    int per = g.P / ja;  // lines per member along axis a
-    int bst_a;           // buffer stride of axis a
+    const int per = g.P / ja;  // lines per member along axis a
+    int bs[D];
     {
       int s = 1;
-      if (a < D - 1) {
-        s = g.LS;
-        for (int e = a + 1; e < D - 1; ++e) s *= g.j[e];
+#pragma unroll
+      for (int e = D - 1; e >= 0; --e) {
+        if (e == D - 1) { bs[e] = 1; s = g.LS; }
+        else { bs[e] = s; s *= g.j[e]; }
       }
-      bst_a = s;
     }
-    for (int l = lane; l < n * per; l += 32) {
+    auto base_of = [&](int l) {
       int m = l / per, li = l - m * per;
-      // li enumerates the coordinates of all axes except a, C order
-      int base = m * g.MS;
-      int rem = li;
+      int base = m * g.MS, rem = li;
 #pragma unroll
       for (int e = D - 1; e >= 0; --e) {
         if (e == a) continue;
         int c = rem % g.j[e];
         rem /= g.j[e];
-        int s = 1;
-        if (e < D - 1) {
-          s = g.LS;
-          for (int f = e + 1; f < D - 1; ++f) s *= g.j[f];
-        }
-        base += c * s;
+        base += c * bs[e];
       }
-      spatial_line(buf, base, bst_a, ja, mode, tab);
+      return base;
+    };
+    const float *M = axis_matrix(mats, moff, a, ja, mode);
+    const int nl = n * per, st = bs[a];
+    if ((ja & (ja - 1)) == 0) {
+      // power-of-two length: register butterflies, one lane per line
+      for (int l = lane; l < nl; l += 32) {
+        const int base = base_of(l);
+        switch (ja) {
+          case 2: fast_dct_line<2>(buf, base, st, mode); break;
+          case 4: fast_dct_line<4>(buf, base, st, mode); break;
+          case 8: fast_dct_line<8>(buf, base, st, mode); break;
+          case 16: fast_dct_line<16>(buf, base, st, mode); break;
+          default: fast_dct_line<32>(buf, base, st, mode); break;
+        }
+      }
+      __syncwarp();
+      continue;
     }
-    __syncwarp();
+    switch (ja) {
+      case 3: xform_lines<3>(buf, nl, base_of, st, M, lane); break;
+      case 5: xform_lines<5>(buf, nl, base_of, st, M, lane); break;
+      case 6: xform_lines<6>(buf, nl, base_of, st, M, lane); break;
+      case 7: xform_lines<7>(buf, nl, base_of, st, M, lane); break;
+      case 12: xform_lines<12>(buf, nl, base_of, st, M, lane); break;
+      default:
+        for (int l = lane; l < nl; l += 32) dct_line_generic(buf, base_of(l), st, ja, mode, tab);
+        __syncwarp();
+    }
   }
   // group axis
   if (n > 1) {
-    for (int v = lane; v < g.P; v += 32) member_line(buf, vbuf[v], g.MS, n, mode, g.gtrans, tab);
+    for (int v = lane; v < g.P; v += 32) {
+      const int base = vbuf[v];
+      if (g.gtrans == 1) { dct_line_generic(buf, base, g.MS, n, mode, tab); continue; }
+      switch (n) {
+        case 2: haar_line_mode<2>(buf, base, g.MS, mode); break;
+        case 4: haar_line_mode<4>(buf, base, g.MS, mode); break;
+        case 8: haar_line_mode<8>(buf, base, g.MS, mode); break;
+        case 16: haar_line_mode<16>(buf, base, g.MS, mode); break;
+        case 32: haar_line_mode<32>(buf, base, g.MS, mode); break;
+        default: break;
+      }
+    }
     __syncwarp();
   }
 }
@@ -349,7 +494,7 @@ __device__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lan
 // ---------------------------------------------------------------------------
 
 template <int D, int JL, int KB>
-__device__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
+__device__ __noinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
                           const int *org, const int *rowoff, int lane, int *mem) {
   int lo[D], W[D];
   int64_t ncand = 1;
@@ -414,29 +559,31 @@ __device__ int warp_match(const DGeom &g, const float *__restrict__ S, const int
         const float *prow = S + rbase + rowoff[r];
         const float *qrow = S + cbase + rowoff[r];
         if (JL > 0) {
+          // sliding window over the candidate row: q[b] = qrow[i + b]
           constexpr int JJ = JL > 0 ? JL : 1;
-          float p[JJ], q[KB + JJ - 1];
+          float q[KB];
 #pragma unroll
-          for (int i = 0; i < JJ; ++i) p[i] = prow[i];
+          for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
 #pragma unroll
-          for (int i = 0; i < KB + JJ - 1; ++i) q[i] = qrow[i];
-          if (g.bias_on) {
-#pragma unroll
-            for (int i = 0; i < JJ; ++i)
-#pragma unroll
-              for (int b = 0; b < KB; ++b) {
-                float df = __fsub_rn(q[b + i], p[i]);
-                acc[b] = fmaf(df, df, acc[b]);
-                bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(p[i], q[b + i]), 0.f));
-              }
-          } else {
-#pragma unroll
-            for (int i = 0; i < JJ; ++i)
+          for (int i = 0; i < JJ; ++i) {
+            q[KB - 1] = qrow[i + KB - 1];
+            const float pv = prow[i];
+            if (g.bias_on) {
 #pragma unroll
               for (int b = 0; b < KB; ++b) {
-                float df = __fsub_rn(q[b + i], p[i]);
+                float df = __fsub_rn(q[b], pv);
+                acc[b] = fmaf(df, df, acc[b]);
+                bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, q[b]), 0.f));
+              }
+            } else {
+#pragma unroll
+              for (int b = 0; b < KB; ++b) {
+                float df = __fsub_rn(q[b], pv);
                 acc[b] = fmaf(df, df, acc[b]);
               }
+            }
+#pragma unroll
+            for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
           }
         } else {
           for (int i = 0; i < jl; ++i) {
@@ -504,279 +651,477 @@ __device__ int warp_match(const DGeom &g, const float *__restrict__ S, const int
   return count;
 }
 
+
+// ---------------------------------------------------------------------------
+// collaborative filtering of one group (Secs. 5-7)
+// ---------------------------------------------------------------------------
+
+// Entries (m, v) of a group, m < n members, v < P patch entries, visited with
+// a lane stride of 32 and no integer division.
+#define BMND_FOR_ENTRIES(body)                         \
+  {                                                    \
+    int m = lane / P, v = lane - (lane / P) * P;       \
+    while (m < n) {                                    \
+      body;                                            \
+      v += 32;                                         \
+      while (v >= P) { v -= P; ++m; }                  \
+    }                                                  \
+  }
+
+// Filters the group whose member origins (region offsets) are in mem[0..n).
+// Stage 1: hard thresholding of T y_g against sigma_k from the variance map;
+// stage 2: Wiener shrinkage of T y_g with gains from the pilot group.  Leaves
+// the synthesized patches in bufB (returns 0) or bufA (returns 1), the patch
+// weights in wts, and for the second mass-conservation sweep the correction
+// alpha = d_g / (zeta^T 1) of Def. "Aggregation-aware constant-synthesis
+// correction" in *alpha_out.
+template <int D>
+__device__ __noinline__ int filter_group(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
+                                         const int *__restrict__ vreg, const int *__restrict__ vbuf,
+                                         const float *__restrict__ omega, const float *__restrict__ Sg,
+                                         const float *__restrict__ Sy, const float *__restrict__ Se,
+                                         float *__restrict__ bufA, float *__restrict__ bufB, float *__restrict__ wts,
+                                         float *__restrict__ rr_s, const float *mats, const int *moff,
+                                         const float *tab, float *alpha_out) {
+  const int P = g.P, MS = g.MS;
+  const bool stage2 = g.stage == 2;
+  // ---- gather the guide group (y in stage 1, pilot in stage 2) and, for
+  // Poisson data, its variance map m_v = s_P [guide]_+ ----
+  BMND_FOR_ENTRIES({
+    const float gv = Sg[mem[m] + vreg[v]];
+    const int a = m * MS + vbuf[v];
+    bufB[a] = gv;
+    if (g.poisson) bufA[a] = g.s_p * fmaxf(gv, 0.f);
+  });
+  __syncwarp();
+  // sigma_k^2 = sum_i T_ki^2 m_v(u_i); Gaussian: sigma^2 (orthonormal T)
+  if (g.poisson) group_xform<D>(bufA, g, n, 2, lane, vbuf, mats, moff, tab);
+  group_xform<D>(bufB, g, n, 0, lane, vbuf, mats, moff, tab);
+  // ---- shrinkage; per-coefficient weight terms into bufA ----
+  const float lam = g.lambda * 1.0001f, lam2 = lam * lam;
+  BMND_FOR_ENTRIES({
+    const int a = m * MS + vbuf[v];
+    const float s2 = g.poisson ? bufA[a] : g.var_g;
+    const float X = bufB[a];
+    float wterm;
+    if (!stage2) {
+      // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
+      // with count data, are zeroed whatever the rounding), as X^2 > ...
+      const bool keep = X * X > lam2 * s2;
+      bufB[a] = keep ? X : 0.f;
+      wterm = keep ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
+    } else {
+      const float S = fmaxf(X * X - g.a_power * s2, 0.f);
+      const float den = S + g.s_v * s2;
+      const float G = den > 0.f ? __fdividef(S, den) : 0.f;
+      bufB[a] = G;
+      wterm = g.wmodel == 0 ? G * G
+                            : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
+    }
+    bufA[a] = wterm;
+  });
+  __syncwarp();
+  // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums its row;
+  // the member stride is odd, so the rows fall in distinct banks) ----
+  if (lane < n) {
+    float r = 0.f;
+    const float *row = bufA + lane * MS;
+    for (int v = 0; v < P; ++v) r += row[vbuf[v]];
+    rr_s[lane] = r;
+  }
+  __syncwarp();
+  // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
+  if (lane < n) {
+    float R = 0.f;
+    if (g.wscope == 1) {
+      for (int l = 0; l < n; ++l) R += rr_s[l];
+    } else if (g.gtrans == 0) {
+      R = rr_s[0] / (float)n;
+      for (int b = n; b >= 2; b >>= 1) R += rr_s[n / b + lane / b] / (float)b;
+    } else {
+      const float *Mt = tab + gen_off(n);
+      for (int l = 0; l < n; ++l) {
+        const float c = __ldg(Mt + l * n + lane);
+        R += c * c * rr_s[l];
+      }
+    }
+    wts[lane] = R > 0.f ? 1.f / R : 1.f;
+  }
+  __syncwarp();
+  float *syn = bufB;
+  if (stage2) {
+    // Wiener: transform the observation group and apply the gains
+    BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
+    __syncwarp();
+    group_xform<D>(bufA, g, n, 0, lane, vbuf, mats, moff, tab);
+    BMND_FOR_ENTRIES({
+      const int a = m * MS + vbuf[v];
+      bufA[a] *= bufB[a];
+    });
+    __syncwarp();
+    syn = bufA;
+  }
+  // ---- inverse transform: synthesized patches ----
+  group_xform<D>(syn, g, n, 1, lane, vbuf, mats, moff, tab);
+  float alpha = 0.f;
+  if (mc2) {
+    // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
+    // alpha = d_g / zeta^T 1 to every synthesized entry
+    float dg = 0.f, z1 = 0.f;
+    BMND_FOR_ENTRIES({
+      const int u = mem[m] + vreg[v];
+      const float et = Se[u];
+      const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+      dg = fmaf(z, Sy[u] - syn[m * MS + vbuf[v]], dg);
+      z1 += z;
+    });
+    dg = warp_sum(dg);
+    z1 = warp_sum(z1);
+    alpha = z1 > 0.f ? dg / z1 : 0.f;
+  }
+  *alpha_out = alpha;
+  return stage2 ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // the stage kernel
 // ---------------------------------------------------------------------------
 
+// Shared-memory layout of one job (the host computes the same sizes).
+struct SmemLayout {
+  int *vreg, *vbuf, *rowoff, *moff, *fvoff, *fpreg;
+  float *omega, *mats, *Sg, *Sy, *Se;
+  float2 *acc;
+  unsigned char *warps;
+  int wbytes;
+};
+
+__device__ __forceinline__ unsigned char *al16p(unsigned char *p) {
+  return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
+__device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stage2, bool mc2) {
+  SmemLayout s;
+  unsigned char *p = smem + ((sizeof(DJob) + 15) & ~(size_t)15);
+  s.vreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.P;
+  s.vbuf = reinterpret_cast<int *>(p); p += sizeof(int) * g.P;
+  s.omega = reinterpret_cast<float *>(p); p += sizeof(float) * g.P;
+  s.rowoff = reinterpret_cast<int *>(p); p += sizeof(int) * g.rows;
+  s.moff = reinterpret_cast<int *>(p); p += sizeof(int) * KMAXD;
+  s.fvoff = reinterpret_cast<int *>(p); p += sizeof(int) * (g.fp ? g.P : 0);
+  s.fpreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.fp;
+  p = al16p(p);
+  s.mats = reinterpret_cast<float *>(p);
+  for (int a = 0; a < g.D; ++a) p += sizeof(float) * mat_block(g.j[a]);
+  p = al16p(p);
+  const int RS = g.region + RPAD;
+  s.Sg = reinterpret_cast<float *>(p); p += sizeof(float) * RS;
+  s.Sy = s.Sg;
+  if (stage2) { s.Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  s.Se = nullptr;
+  if (mc2) { s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  p = al16p(p);
+  s.acc = reinterpret_cast<float2 *>(p); p += sizeof(float2) * g.region;
+  s.warps = p;
+  s.wbytes = warp_bytes(g.M, g.MS, g.fp);
+  return s;
+}
+
 // mode 0: match + filter + aggregate (group tables written if job.groups);
 // mode 1: match only, group tables written; mode 2: mass-conservation sweep 2
 // (groups read back, corrected patches aggregated with the sweep-1 weights).
+// Persistent: each CTA takes tiles from *counter until all are done.
 template <int D, int JL, int KB>
-__global__ void __launch_bounds__(NW * 32, 1)
-k_stage(const DJob *__restrict__ jobs, int njobs, int mode, const float *__restrict__ tab) {
+__global__ void __launch_bounds__(NW * 32, BMND_MIN_BLOCKS)
+k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, const float *__restrict__ tab,
+        int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // locate the job of this tile
-  int jb = 0;
-  {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].tile_base <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    jb = lo;
-  }
   DJob *sj = reinterpret_cast<DJob *>(smem);
-  {
-    const int *src = reinterpret_cast<const int *>(&jobs[jb]);
-    int *dst = reinterpret_cast<int *>(sj);
-    for (int i = threadIdx.x; i < (int)(sizeof(DJob) / 4); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  // sweep 2 only concerns jobs with mass conservation; the others keep the
-  // partials of sweep 1, which the second reduce turns into the same output
-  if (mode == 2 && sj->groups == nullptr) return;
-  const DGeom &g = sj->g;
-  const int tile = blockIdx.x - sj->tile_base;
-  const bool stage2 = g.stage == 2;
-  const bool mc2 = mode == 2;
-  // shared layout
-  unsigned char *p = smem + ((sizeof(DJob) + 15) & ~(size_t)15);
-  int *vreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.P;
-  int *vbuf = reinterpret_cast<int *>(p); p += sizeof(int) * g.P;
-  float *omega = reinterpret_cast<float *>(p); p += sizeof(float) * g.P;
-  int *rowoff = reinterpret_cast<int *>(p); p += sizeof(int) * g.rows;
-  p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
-  const int RS = g.region + RPAD;
-  float *Sg = reinterpret_cast<float *>(p); p += sizeof(float) * RS;           // guide
-  float *Sy = Sg;
-  if (stage2) { Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }  // observation
-  float *Se = nullptr;
-  if (mc2) { Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }     // eta
-  p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
-  float2 *acc = reinterpret_cast<float2 *>(p); p += sizeof(float2) * g.region;
-  int wbytes = (3 * MMAX) * 4 + 2 * g.M * g.MS * 4;
-  unsigned char *wp = p + (size_t)warp * wbytes;
-  int *mem = reinterpret_cast<int *>(wp);
-  float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
-  float *rr_s = reinterpret_cast<float *>(wp + 2 * MMAX * 4);
-  float *bufA = reinterpret_cast<float *>(wp + 3 * MMAX * 4);
-  float *bufB = bufA + g.M * g.MS;
-
-  int tc[D], org[D];
-  {
-    int rem = tile;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) { tc[d] = rem % g.NT[d]; rem /= g.NT[d]; }
-#pragma unroll
-    for (int d = 0; d < D; ++d) org[d] = tc[d] * g.C[d] - g.rad[d];
-  }
-  // tables: region offset, buffer offset and window of every patch entry
-  for (int v = threadIdx.x; v < g.P; v += blockDim.x) {
-    int rem = v, ro = 0;
-    float w = 1.f;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
-      int c = rem % g.j[d];
-      rem /= g.j[d];
-      ro += c * g.rst[d];
-      w *= g.kaiser[d][c];
-    }
-    vreg[v] = ro;
-    vbuf[v] = (v / g.jL) * g.LS + (v % g.jL);
-    omega[v] = w;
-    if (v % g.jL == 0) rowoff[v / g.jL] = ro;
-  }
-  // stage the region(s); locations outside the array are never read as
-  // patch entries (candidates are clipped) and are set to zero
-  const float *gsrc = sj->guide, *ysrc = sj->y, *esrc = sj->eta;
-  for (int e = threadIdx.x; e < RS; e += blockDim.x) {
-    float vg = 0.f, vy = 0.f, ve = 0.f;
-    if (e < g.region) {
-      int rem = e;
-      int64_t gi = 0;
-      bool in = true;
-#pragma unroll
-      for (int d = D - 1; d >= 0; --d) {
-        int c = rem % g.RG[d];
-        rem /= g.RG[d];
-        int64_t x = (int64_t)org[d] + c;
-        if (x < 0 || x >= g.L[d]) in = false;
-        gi += x * g.st[d];
+  int cur_job = -1;
+  SmemLayout L;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int gt = s_tile;
+    if (gt >= total_tiles) break;
+    int jb;
+    {
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
       }
-      if (in) {
-        vg = __ldg(gsrc + gi);
-        if (stage2) vy = __ldg(ysrc + gi);
-        if (mc2) ve = __ldg(esrc + gi);
-      }
-      acc[e] = make_float2(0.f, 0.f);
+      jb = lo;
     }
-    Sg[e] = vg;
-    if (stage2) Sy[e] = vy;
-    if (mc2) Se[e] = ve;
-  }
-  __syncthreads();
-
-  const int nref = sj->ref_count[tile];
-  const int rounds = (nref + NW - 1) / NW;
-  const int64_t tslot = (int64_t)tile * g.cap;
-  for (int rd = 0; rd < rounds; ++rd) {
-    const int ri = rd * NW + warp;
-    const bool has = ri < nref;
-    int n = 0;
-    float alpha = 0.f;
-    float *syn = bufB;
-    if (has) {
-      int rr[D];
+    if (jb != cur_job) {
+      // new job: its descriptor, per-entry tables and transform matrices
+      const int *src = reinterpret_cast<const int *>(&jobs[jb]);
+      int *dst = reinterpret_cast<int *>(sj);
+      for (int i = threadIdx.x; i < (int)(sizeof(DJob) / 4); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      const DGeom &g = sj->g;
+      L = smem_layout(smem, g, g.stage == 2, mode == 2);
+      for (int v = threadIdx.x; v < g.P; v += blockDim.x) {
+        int rem = v, ro = 0;
+        float w = 1.f;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+          int c = rem % g.j[d];
+          rem /= g.j[d];
+          ro += c * g.rst[d];
+          w *= g.kaiser[d][c];
+        }
+        L.vreg[v] = ro;
+        L.vbuf[v] = (v / g.jL) * g.LS + (v % g.jL);
+        L.omega[v] = w;
+        if (v % g.jL == 0) L.rowoff[v / g.jL] = ro;
+        if (g.fp) {
+          int r2 = v, fo = 0, fs = 1;
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) {
+            fo += (r2 % g.j[d]) * fs;
+            r2 /= g.j[d];
+            fs *= g.FW[d];
+          }
+          L.fvoff[v] = fo;
+        }
+      }
+      for (int f = threadIdx.x; f < g.fp; f += blockDim.x) {
+        int r2 = f, ro = 0;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+          ro += (r2 % g.FW[d]) * g.rst[d];
+          r2 /= g.FW[d];
+        }
+        L.fpreg[f] = ro;
+      }
+      if (threadIdx.x == 0) {
+        int o = 0;
+        for (int a = 0; a < D; ++a) { L.moff[a] = o; o += mat_block(g.j[a]); }
+      }
       {
-        int rem = sj->ref_local[tslot + ri];
+        int o = 0;
+        for (int a = 0; a < D; ++a) {
+          const int J = g.j[a];
+          const float *F = tab + gen_off(J), *Q = tab + GEN_TOTAL + gen_off(J);
+          for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
+            int k = e / J, i = e - k * J;
+            L.mats[o + e] = __ldg(F + e);
+            L.mats[o + J * J + e] = __ldg(F + i * J + k);
+            L.mats[o + 2 * J * J + e] = __ldg(Q + e);
+          }
+          o += mat_block(J);
+        }
+      }
+      cur_job = jb;
+    }
+    // sweep 2 only concerns jobs with mass conservation; the others keep the
+    // partials of sweep 1, which the second reduce turns into the same output
+    if (mode == 2 && sj->groups == nullptr) continue;
+    const DGeom &g = sj->g;
+    const int tile = gt - sj->tile_base;
+    const bool stage2 = g.stage == 2;
+    const bool mc2 = mode == 2;
+    unsigned char *wp = L.warps + (size_t)warp * L.wbytes;
+    int *mem = reinterpret_cast<int *>(wp);
+    float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
+    float *rr_s = reinterpret_cast<float *>(wp + 2 * MMAX * 4);
+    int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
+    int *lst = reinterpret_cast<int *>(wp + 4 * MMAX * 4);
+    float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
+    float *bufB = bufA + g.M * g.MS;
+    float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * g.MS);
+    float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
+    float2 *acc = L.acc;
+    const int *vreg = L.vreg, *vbuf = L.vbuf, *rowoff = L.rowoff;
+    const float *omega = L.omega;
+
+    int tc[D], org[D];
+    {
+      int rem = tile;
 #pragma unroll
-        for (int d = D - 1; d >= 0; --d) { rr[d] = rem % g.C[d] + g.rad[d]; rem /= g.C[d]; }
-      }
-      if (!mc2) {
-        n = warp_match<D, JL, KB>(g, Sg, rr, org, rowoff, lane, mem);
-        if (sj->groups) {
-          for (int m = lane; m < g.M; m += 32)
-            sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
-          if (lane == 0) sj->gcount[tslot + ri] = n;
+      for (int d = D - 1; d >= 0; --d) { tc[d] = rem % g.NT[d]; rem /= g.NT[d]; }
+#pragma unroll
+      for (int d = 0; d < D; ++d) org[d] = tc[d] * g.C[d] - g.rad[d];
+    }
+    // stage the region(s); locations outside the array are never read as
+    // patch entries (candidates are clipped) and are set to zero
+    const float *gsrc = sj->guide, *ysrc = sj->y, *esrc = sj->eta;
+    const int RS = g.region + RPAD;
+    for (int e = threadIdx.x; e < RS; e += blockDim.x) {
+      float vg = 0.f, vy = 0.f, ve = 0.f;
+      if (e < g.region) {
+        int rem = e;
+        int64_t gi = 0;
+        bool in = true;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+          int c = rem % g.RG[d];
+          rem /= g.RG[d];
+          int64_t x = (int64_t)org[d] + c;
+          if (x < 0 || x >= g.L[d]) in = false;
+          gi += x * g.st[d];
         }
-      } else {
-        n = sj->gcount[tslot + ri];
-        for (int m = lane; m < n; m += 32) mem[m] = sj->groups[(tslot + ri) * g.M + m];
-        __syncwarp();
+        if (in) {
+          vg = __ldg(gsrc + gi);
+          if (stage2) vy = __ldg(ysrc + gi);
+          if (mc2) ve = __ldg(esrc + gi);
+        }
+        acc[e] = make_float2(0.f, 0.f);
       }
-      if (mode != 1) {
-        const int nP = n * g.P;
-        // ---- coefficient variances: sigma_k^2 = sum_i T_ki^2 m_v(u_i) ----
-        if (g.poisson) {
-          for (int e = lane; e < nP; e += 32) {
-            int m = e / g.P, v = e - m * g.P;
-            bufA[m * g.MS + vbuf[v]] = g.s_p * fmaxf(Sg[mem[m] + vreg[v]], 0.f);
+      Sg[e] = vg;
+      if (stage2) Sy[e] = vy;
+      if (mc2) Se[e] = ve;
+    }
+    __syncthreads();
+
+    const int nref = sj->ref_count[tile];
+    const int rounds = (nref + NW - 1) / NW;
+    const int64_t tslot = (int64_t)tile * g.cap;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int ri = rd * NW + warp;
+      const bool has = ri < nref;
+      int n = 0;
+      float alpha = 0.f;
+      float *syn = bufB;
+      if (has) {
+        int rr[D];
+        {
+          int rem = sj->ref_local[tslot + ri];
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) { rr[d] = rem % g.C[d] + g.rad[d]; rem /= g.C[d]; }
+        }
+        if (!mc2) {
+          n = warp_match<D, JL, KB>(g, Sg, rr, org, rowoff, lane, mem);
+          if (sj->groups) {
+            for (int m = lane; m < g.M; m += 32)
+              sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
+            if (lane == 0) sj->gcount[tslot + ri] = n;
           }
+        } else {
+          n = sj->gcount[tslot + ri];
+          for (int m = lane; m < n; m += 32) mem[m] = sj->groups[(tslot + ri) * g.M + m];
           __syncwarp();
-          group_xform<D>(bufA, g, n, 2, lane, vbuf, tab);
         }
-        // ---- forward transform of the guide group (y in stage 1, pilot in stage 2)
-        for (int e = lane; e < nP; e += 32) {
-          int m = e / g.P, v = e - m * g.P;
-          bufB[m * g.MS + vbuf[v]] = Sg[mem[m] + vreg[v]];
+        if (mode != 1) {
+          const int which = filter_group<D>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
+                                            rr_s, L.mats, L.moff, tab, &alpha);
+          syn = which ? bufA : bufB;
         }
-        __syncwarp();
-        group_xform<D>(bufB, g, n, 0, lane, vbuf, tab);
-        // ---- shrinkage; per-coefficient weight terms into bufA ----
-        for (int e = lane; e < nP; e += 32) {
-          int m = e / g.P, v = e - m * g.P;
-          int a = m * g.MS + vbuf[v];
-          float s2 = g.poisson ? bufA[a] : g.var_g;
-          float X = bufB[a];
-          float wterm;
-          if (!stage2) {
-            // strict inequality with a relative guard of 1e-4: exact ties
-            // (common with count data) are zeroed whatever the rounding
-            bool keep = fabsf(X) > g.lambda * sqrtf(s2) * 1.0001f;
-            bufB[a] = keep ? X : 0.f;
-            wterm = keep ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
-          } else {
-            float S = fmaxf(X * X - g.a_power * s2, 0.f);
-            float den = S + g.s_v * s2;
-            float G = den > 0.f ? S / den : 0.f;
-            bufB[a] = G;
-            wterm = g.wmodel == 0 ? G * G : (g.wmodel == 1 ? G * G * s2
-                                              : G * G * s2 + (1.f - G) * (1.f - G) * S);
+      }
+      if (mode == 1) continue;
+      // ---- overlap levels of the group's members: level(m) = 1 + the
+      // highest level of an earlier member whose patch overlaps m's.  Members
+      // of one level cover disjoint locations, so adding them level by level
+      // keeps, at every location, the members' order.
+      int mylev = 0, maxlev = 0, boxbase = 0;
+      if (has) {
+        int cm[D];
+        {
+          int rem = lane < n ? mem[lane] : 0;
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) { cm[d] = rem % g.RG[d]; rem /= g.RG[d]; }
+        }
+        for (int m = 1; m < n; ++m) {
+          bool ov = lane < m;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            int o = __shfl_sync(0xffffffffu, cm[d], m);
+            ov = ov && abs(cm[d] - o) < g.j[d];
           }
-          bufA[a] = wterm;
+          int l = warp_max_i(ov ? mylev + 1 : 0);
+          if (lane == m) mylev = l;
         }
-        __syncwarp();
-        // ---- r_l = sum_q (term), per group-axis plane l ----
-        for (int m = 0; m < n; ++m) {
-          float s = 0.f;
-          for (int v = lane; v < g.P; v += 32) s += bufA[m * g.MS + vbuf[v]];
-          s = warp_sum(s);
-          if (lane == 0) rr_s[m] = s;
-        }
-        __syncwarp();
-        // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
-        if (lane < n) {
-          float R = 0.f;
-          if (g.wscope == 1) {
-            for (int l = 0; l < n; ++l) R += rr_s[l];
-          } else if (g.gtrans == 0) {
-            R = rr_s[0] / (float)n;
-            for (int b = n; b >= 2; b >>= 1) R += rr_s[n / b + lane / b] / (float)b;
-          } else {
-            const float *Mt = tab + gen_off(n);
-            for (int l = 0; l < n; ++l) {
-              float c = __ldg(Mt + l * n + lane);
-              R += c * c * rr_s[l];
+        maxlev = warp_max_i(lane < n ? mylev : 0);
+        if (g.fp) {
+          // private footprint: the box [core, core + 2 rad + j - 1] of the
+          // reference holds every member patch
+          int fo = 0, bb = 0;
+          {
+            int rem = sj->ref_local[tslot + ri], fs = 1;
+            int c[D];
+#pragma unroll
+            for (int d = D - 1; d >= 0; --d) { c[d] = rem % g.C[d]; rem /= g.C[d]; }
+#pragma unroll
+            for (int d = D - 1; d >= 0; --d) {
+              bb += c[d] * g.rst[d];
+              fo += (cm[d] - c[d]) * fs;
+              fs *= g.FW[d];
             }
           }
-          wts[lane] = R > 0.f ? 1.f / R : 1.f;
-        }
-        __syncwarp();
-        if (stage2) {
-          // Wiener: transform the observation group and apply the gains
-          for (int e = lane; e < nP; e += 32) {
-            int m = e / g.P, v = e - m * g.P;
-            bufA[m * g.MS + vbuf[v]] = Sy[mem[m] + vreg[v]];
-          }
+          boxbase = bb;
+          if (lane < n) lvl[lane] = fo;  // footprint offset of member `lane`
+          for (int f = lane; f < g.fp; f += 32) fpb[f] = make_float2(0.f, 0.f);
           __syncwarp();
-          group_xform<D>(bufA, g, n, 0, lane, vbuf, tab);
-          for (int e = lane; e < nP; e += 32) {
-            int m = e / g.P, v = e - m * g.P;
-            int a = m * g.MS + vbuf[v];
-            bufA[a] *= bufB[a];
+          for (int Lv = 0; Lv <= maxlev; ++Lv) {
+            const bool mine = lane < n && mylev == Lv;
+            unsigned mask = __ballot_sync(0xffffffffu, mine);
+            if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
+            __syncwarp();
+            int items = __popc(mask) * g.P;
+            for (int it = lane; it < items; it += 32) {
+              int r = it / g.P, v = it - r * g.P;
+              int m = lst[r];
+              int a = lvl[m] + L.fvoff[v];
+              float wo = wts[m] * omega[v];
+              float2 t = fpb[a];
+              t.x = fmaf(wo, syn[m * g.MS + vbuf[v]] + alpha, t.x);
+              t.y += wo;
+              fpb[a] = t;
+            }
+            __syncwarp();
           }
-          __syncwarp();
-          syn = bufA;
         }
-        // ---- inverse transform: synthesized patches ----
-        group_xform<D>(syn, g, n, 1, lane, vbuf, tab);
-        if (mc2) {
-          // Def. aggregation-aware constant-synthesis correction: the
-          // correction adds alpha = d_g / (zeta^T 1) to every synthesized entry
-          float dg = 0.f, z1 = 0.f;
-          for (int e = lane; e < nP; e += 32) {
-            int m = e / g.P, v = e - m * g.P;
-            int u = mem[m] + vreg[v];
-            float et = Se[u];
-            float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-            dg = fmaf(z, Sy[u] - syn[m * g.MS + vbuf[v]], dg);
-            z1 += z;
+      }
+      // ---- ordered, atomic-free accumulation into the tile region ----
+      if (!(warp == 0 && rd == 0)) named_sync(1 + warp, 64);
+      if (has) {
+        if (g.fp) {
+          for (int f = lane; f < g.fp; f += 32) {
+            float2 t = fpb[f];
+            if (t.y != 0.f) {
+              int a = boxbase + L.fpreg[f];
+              float2 u = acc[a];
+              u.x += t.x;
+              u.y += t.y;
+              acc[a] = u;
+            }
           }
-          dg = warp_sum(dg);
-          z1 = warp_sum(z1);
-          alpha = z1 > 0.f ? dg / z1 : 0.f;
+        } else {
+          for (int Lv = 0; Lv <= maxlev; ++Lv) {
+            const bool mine = lane < n && mylev == Lv;
+            unsigned mask = __ballot_sync(0xffffffffu, mine);
+            if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
+            __syncwarp();
+            int items = __popc(mask) * g.P;
+            for (int it = lane; it < items; it += 32) {
+              int r = it / g.P, v = it - r * g.P;
+              int m = lst[r];
+              int a = mem[m] + vreg[v];
+              float wo = wts[m] * omega[v];
+              float2 t = acc[a];
+              t.x = fmaf(wo, syn[m * g.MS + vbuf[v]] + alpha, t.x);
+              t.y += wo;
+              acc[a] = t;
+            }
+            __syncwarp();
+          }
         }
+      }
+      __threadfence_block();
+      {
+        int nxt = warp + 1 == NW ? 0 : warp + 1;
+        if (!(nxt == 0 && rd == rounds - 1)) named_arrive(1 + nxt, 64);
       }
     }
     if (mode == 1) continue;
-    // ---- ordered, atomic-free accumulation into the tile region ----
-    if (!(warp == 0 && rd == 0)) named_sync(1 + warp, 64);
-    if (has) {
-      for (int m = 0; m < n; ++m) {
-        const float wm = wts[m];
-        const int base = mem[m];
-        for (int v = lane; v < g.P; v += 32) {
-          int a = base + vreg[v];
-          float wo = wm * omega[v];
-          float2 t = acc[a];
-          t.x = fmaf(wo, syn[m * g.MS + vbuf[v]] + alpha, t.x);
-          t.y += wo;
-          acc[a] = t;
-        }
-        __syncwarp();
-      }
-    }
-    __threadfence_block();
-    {
-      int nxt = warp + 1 == NW ? 0 : warp + 1;
-      if (!(nxt == 0 && rd == rounds - 1)) named_arrive(1 + nxt, 64);
-    }
+    __syncthreads();
+    float2 *dst = sj->partial + (int64_t)tile * g.region;
+    for (int e = threadIdx.x; e < g.region; e += blockDim.x) dst[e] = acc[e];
   }
-  if (mode == 1) return;
-  __syncthreads();
-  float2 *dst = sj->partial + (int64_t)tile * g.region;
-  for (int e = threadIdx.x; e < g.region; e += blockDim.x) dst[e] = acc[e];
 }
 
 // Sum the partials of the tiles covering every location in tile order and
@@ -892,7 +1237,7 @@ __global__ void k_export_groups(const DJob *__restrict__ jobs, const int64_t *__
 // explicit instantiations and launch helpers
 // ---------------------------------------------------------------------------
 
-typedef void (*stage_fn)(const DJob *, int, int, const float *);
+typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 
 template <int D, int JL, int KB>
 stage_fn stage_ptr() { return &k_stage<D, JL, KB>; }

@@ -27,21 +27,28 @@ constexpr int JMAX = 32;     // maximum patch length per axis
 constexpr int NW = 8;        // warps per CTA of the stage kernel
 constexpr int RPAD = 40;     // floats of padding after every shared region
 
-// Dense orthonormal DCT-II matrices of the sizes with register-resident line
-// transforms, forward then entrywise squared (the latter propagates diagonal
-// variances, Prop. "Diagonal Poisson variance propagation").
-constexpr int DCT_TOTAL = 1484;
-__host__ __device__ constexpr int dct_off(int J) {
-  return J == 1 ? 0 : J == 2 ? 1 : J == 3 ? 5 : J == 4 ? 14 : J == 5 ? 30 : J == 6 ? 55
-       : J == 7 ? 91 : J == 8 ? 140 : J == 16 ? 204 : J == 32 ? 460 : -1;
-}
-// Uploads the forward and squared tables (2 * DCT_TOTAL floats) to the
-// constant bank of the current device.
-cudaError_t upload_dct_constants(const float *h);
-
-// Generic DCT table in global memory: sizes 1..32 at offset (J-1)J(2J-1)/6,
-// then the entrywise squares at +GEN_TOTAL.
+// DCT table in global memory: orthonormal DCT-II matrices of sizes 1..32 at
+// offset (J-1)J(2J-1)/6, then their entrywise squares at +GEN_TOTAL.  Each CTA
+// copies the matrices of its patch axes (forward, transposed, squared) into
+// shared memory.
 constexpr int GEN_TOTAL = 11440;
+
+// Uploads the fast-DCT constants to the constant bank of the current device:
+// sec31[N/2 - 1 + n] = 1 / (2 cos(pi (2n+1) / (2N))) for N = 2, 4, ..., 32 and
+// scale12[2 log2 N] = sqrt(1/N), scale12[2 log2 N + 1] = sqrt(2/N), N = 1..32.
+cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
+
+// Bytes of one warp's shared block: member list, weights, plane sums and two
+// level lists (5 x MMAX words), two group buffers of M x MS floats, and the
+// private footprint (fp float2), rounded up to 16 bytes.
+__host__ __device__ constexpr int warp_bytes(int M, int MS, int fp) {
+  return (5 * MMAX * 4 + 2 * M * MS * 4 + fp * 8 + 15) & ~15;
+}
+
+// Floats reserved in shared memory for the three J x J matrices of one patch
+// axis, rounded up to 4 so that every block starts on a 16-byte boundary (the
+// line transforms read rows of sizes divisible by 4 as float4).
+__host__ __device__ constexpr int mat_block(int J) { return (3 * J * J + 3) & ~3; }
 
 // Per-array geometry of one stage, with singleton axes removed.
 struct DGeom {
@@ -68,6 +75,10 @@ struct DGeom {
   int j[KMAXD], rad[KMAXD];
   int C[KMAXD], NT[KMAXD], RG[KMAXD], rst[KMAXD];
   float kaiser[KMAXD][JMAX];
+  // private group footprint (2 rad_d + j_d per axis) used to accumulate a
+  // group before merging it into the tile region; fp = 0 disables it
+  int fp;
+  int FW[KMAXD];
 };
 
 struct DJob {
