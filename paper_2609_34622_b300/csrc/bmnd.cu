@@ -16,7 +16,7 @@
 
 namespace bmnd {
 typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
-stage_fn select_stage_kernel(int D, int jL, int kb);
+stage_fn select_stage_kernel(int D, int jL, int kb, int minb);
 void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,
                    cudaStream_t st);
 void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off, int64_t *origins,
@@ -260,7 +260,6 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   g.rows = g.P / g.jL;
   g.LS = g.jL + (g.jL % 2 == 0 ? 1 : 0);
   g.MS = g.rows * g.LS;
-  if (g.MS % 2 == 0) g.MS += 1;  // odd member stride: per-member rows in distinct banks
   // private group footprint for the accumulation when it is small
   {
     int64_t fp = 1;
@@ -386,8 +385,11 @@ bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
 
 // Launch the persistent stage kernel: one CTA per resident slot, tiles handed
 // out by an atomic counter that is cleared first.
-bmnd_status launch_stage(bmnd_ctx *ctx, stage_fn f, const DJob *dj, int nj, int tiles, int mode, int smem,
-                         cudaStream_t st) {
+bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, const DJob *dj, int nj, int tiles, int mode,
+                         int smem, cudaStream_t st) {
+  // two CTAs per SM when their shared memory fits, else the full register file
+  const int minb = 2 * (smem + 1024) <= 233472 ? 2 : 1;
+  stage_fn f = select_stage_kernel(D, jL, kb, minb);
   CU(set_stage_smem(f, smem));
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)f, NW * 32, smem));
@@ -505,15 +507,15 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
                  pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
   }
   CU(cudaGetLastError());
-  stage_fn f = select_stage_kernel(D, plans[0].g.jL, pick_kb(plans[0]));
+  int kjL = plans[0].g.jL, kkb = pick_kb(plans[0]);
   for (int i = 1; i < nj; ++i)
-    if (plans[i].g.jL != plans[0].g.jL) f = select_stage_kernel(D, 0, 4);
+    if (plans[i].g.jL != plans[0].g.jL) { kjL = 0; kkb = 4; }
   int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = first_stage; s <= last_stage; ++s) {
     const DJob *dj = ctx->djobs + (s - 1) * nj;
     {
       ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
-      rc = launch_stage(ctx, f, dj, nj, tiles, 0, smax[s - 1], st);
+      rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 0, smax[s - 1], st);
     }
     if (rc != BMND_OK) return rc;
     {
@@ -524,7 +526,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     if (any_mc[s - 1]) {
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
-        rc = launch_stage(ctx, f, dj, nj, tiles, 2, smax[s - 1], st);
+        rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 2, smax[s - 1], st);
       }
       if (rc != BMND_OK) return rc;
       {
@@ -766,9 +768,8 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
                (int *)(B + pl.o_rcount), st);
   CU(cudaGetLastError());
   if (do_match) {
-    stage_fn f = select_stage_kernel(pl.D, pl.g.jL, pick_kb(pl));
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
-    rc = launch_stage(ctx, f, ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
+    rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
     if (rc != BMND_OK) return rc;
   }
   std::vector<int> cnt(pl.g.ntiles);

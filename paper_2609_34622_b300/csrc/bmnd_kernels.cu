@@ -5,10 +5,6 @@
 #include <float.h>
 #include <limits.h>
 
-#ifndef BMND_MIN_BLOCKS
-#define BMND_MIN_BLOCKS 2
-#endif
-
 namespace bmnd {
 
 
@@ -559,31 +555,48 @@ __device__ __noinline__ int warp_match(const DGeom &g, const float *__restrict__
         const float *prow = S + rbase + rowoff[r];
         const float *qrow = S + cbase + rowoff[r];
         if (JL > 0) {
-          // sliding window over the candidate row: q[b] = qrow[i + b]
+          // sliding window over the candidate row, q[b] = qrow[i + b],
+          // unrolled in blocks of IB entries
           constexpr int JJ = JL > 0 ? JL : 1;
+          constexpr int IB = JJ < 8 ? JJ : 8;
           float q[KB];
 #pragma unroll
           for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
+          if (g.bias_on) {
+#pragma unroll 1
+            for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
-          for (int i = 0; i < JJ; ++i) {
-            q[KB - 1] = qrow[i + KB - 1];
-            const float pv = prow[i];
-            if (g.bias_on) {
+              for (int ii = 0; ii < IB; ++ii) {
+                const int i = i0 + ii;
+                q[KB - 1] = qrow[i + KB - 1];
+                const float pv = prow[i];
 #pragma unroll
-              for (int b = 0; b < KB; ++b) {
-                float df = __fsub_rn(q[b], pv);
-                acc[b] = fmaf(df, df, acc[b]);
-                bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, q[b]), 0.f));
-              }
-            } else {
+                for (int b = 0; b < KB; ++b) {
+                  float df = __fsub_rn(q[b], pv);
+                  acc[b] = fmaf(df, df, acc[b]);
+                  bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, q[b]), 0.f));
+                }
 #pragma unroll
-              for (int b = 0; b < KB; ++b) {
-                float df = __fsub_rn(q[b], pv);
-                acc[b] = fmaf(df, df, acc[b]);
+                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
               }
             }
+          } else {
+#pragma unroll 1
+            for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
-            for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
+              for (int ii = 0; ii < IB; ++ii) {
+                const int i = i0 + ii;
+                q[KB - 1] = qrow[i + KB - 1];
+                const float pv = prow[i];
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                  float df = __fsub_rn(q[b], pv);
+                  acc[b] = fmaf(df, df, acc[b]);
+                }
+#pragma unroll
+                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
+              }
+            }
           }
         } else {
           for (int i = 0; i < jl; ++i) {
@@ -611,18 +624,21 @@ __device__ __noinline__ int warp_match(const DGeom &g, const float *__restrict__
         }
       }
     }
-    // merge this round's candidates into the running best list
-#pragma unroll
+    // merge this round's candidates into the running best list (one copy of
+    // the merge code: the candidates rotate through key[0] / idx[0])
+#pragma unroll 1
     for (int b = 0; b < KB; ++b) {
-      bool offer = kv_less(key[b], idx[b], thr, thri);
+      bool offer = kv_less(key[0], idx[0], thr, thri);
       if (__any_sync(0xffffffffu, offer)) {
-        float ok = offer ? key[b] : FLT_MAX;
-        int oi = offer ? idx[b] : INT_MAX;
+        float ok = offer ? key[0] : FLT_MAX;
+        int oi = offer ? idx[0] : INT_MAX;
         warp_sort(ok, oi, lane);
         warp_merge(lk, li, ok, oi, lane);
         thr = __shfl_sync(0xffffffffu, lk, g.M - 2 >= 0 ? g.M - 2 : 0);
         thri = __shfl_sync(0xffffffffu, li, g.M - 2 >= 0 ? g.M - 2 : 0);
       }
+#pragma unroll
+      for (int t = 0; t < KB - 1; ++t) { key[t] = key[t + 1]; idx[t] = idx[t + 1]; }
     }
   }
   nacc = warp_sum_i(nacc);
@@ -721,12 +737,17 @@ __device__ __noinline__ int filter_group(const DGeom &g, int n, bool mc2, int la
     bufA[a] = wterm;
   });
   __syncwarp();
-  // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums its row;
-  // the member stride is odd, so the rows fall in distinct banks) ----
+  // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums its row) ----
   if (lane < n) {
+    // each lane starts at its own entry so that the rows' reads spread over
+    // the banks; the sum is taken in a fixed order per row
     float r = 0.f;
     const float *row = bufA + lane * MS;
-    for (int v = 0; v < P; ++v) r += row[vbuf[v]];
+    int v = lane % P;
+    for (int t = 0; t < P; ++t) {
+      r += row[vbuf[v]];
+      if (++v == P) v = 0;
+    }
     rr_s[lane] = r;
   }
   __syncwarp();
@@ -831,8 +852,8 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
 // mode 1: match only, group tables written; mode 2: mass-conservation sweep 2
 // (groups read back, corrected patches aggregated with the sweep-1 weights).
 // Persistent: each CTA takes tiles from *counter until all are done.
-template <int D, int JL, int KB>
-__global__ void __launch_bounds__(NW * 32, BMND_MIN_BLOCKS)
+template <int D, int JL, int KB, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
 k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, const float *__restrict__ tab,
         int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1240,24 +1261,28 @@ __global__ void k_export_groups(const DJob *__restrict__ jobs, const int64_t *__
 typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 
 template <int D, int JL, int KB>
-stage_fn stage_ptr() { return &k_stage<D, JL, KB>; }
+stage_fn stage_ptr(int minb) { return minb >= 2 ? &k_stage<D, JL, KB, 2> : &k_stage<D, JL, KB, 1>; }
 
-stage_fn select_stage_kernel(int D, int jL, int kb) {
+// Stage kernel for a geometry: D kernel axes, last-axis patch length jL,
+// candidates per lane kb, and the register budget: minb = 2 limits registers
+// so that two CTAs share an SM (used when their shared memory fits), minb = 1
+// gives the kernel the whole register file.
+stage_fn select_stage_kernel(int D, int jL, int kb, int minb) {
   switch (D) {
     case 1:
-      if (jL == 32 && kb == 5) return stage_ptr<1, 32, 5>();
-      if (jL == 16 && kb == 4) return stage_ptr<1, 16, 4>();
-      return stage_ptr<1, 0, 4>();
+      if (jL == 32 && kb == 5) return stage_ptr<1, 32, 5>(minb);
+      if (jL == 16 && kb == 4) return stage_ptr<1, 16, 4>(minb);
+      return stage_ptr<1, 0, 4>(minb);
     case 2:
-      if (jL == 8 && kb == 8) return stage_ptr<2, 8, 8>();
-      if (jL == 4 && kb == 4) return stage_ptr<2, 4, 4>();
-      return stage_ptr<2, 0, 4>();
+      if (jL == 8 && kb == 8) return stage_ptr<2, 8, 8>(minb);
+      if (jL == 4 && kb == 4) return stage_ptr<2, 4, 4>(minb);
+      return stage_ptr<2, 0, 4>(minb);
     case 3:
-      if (jL == 4 && kb == 4) return stage_ptr<3, 4, 4>();
-      return stage_ptr<3, 0, 4>();
-    case 4: return stage_ptr<4, 0, 4>();
-    case 5: return stage_ptr<5, 0, 4>();
-    case 6: return stage_ptr<6, 0, 4>();
+      if (jL == 4 && kb == 4) return stage_ptr<3, 4, 4>(minb);
+      return stage_ptr<3, 0, 4>(minb);
+    case 4: return stage_ptr<4, 0, 4>(minb);
+    case 5: return stage_ptr<5, 0, 4>(minb);
+    case 6: return stage_ptr<6, 0, 4>(minb);
   }
   return nullptr;
 }
