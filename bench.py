@@ -181,6 +181,27 @@ def time_oracle(jobs, min_seconds: float, max_reps: int = 1000):
 
 # ---------------------------------------------------------------------------
 
+def captured_traffic(workload: str):
+    """DRAM bytes per stage-kernel launch from the committed ncu summary, if
+    the kernel source is unchanged since the capture (else None)."""
+    if workload != "c2":
+        return None
+    import hashlib
+    import re
+    summ = os.path.join(ROOT, "profiles", "k_stage_1d_262144.md")
+    src = os.path.join(ROOT, "paper_2609_34622_b300", "csrc", "bmnd_kernels.cu")
+    try:
+        text = open(summ).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m1 = re.search(r"kernel_source_sha: ([0-9a-f]{16})", text)
+    m2 = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not (m1 and m2) or m1.group(1) != sha:
+        return None
+    return int(m2.group(1))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,7 +367,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None,
+                     "traffic": captured_traffic(args.workload),
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median sampled SM clock)" % mhz,
                      "stage_kernel_ms_per_step": stage_ms / args.steps,
                      "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
