@@ -206,6 +206,35 @@ bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable);
 bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches,
                               double *total_ms);
 
+/* Allocation-free denoising (the paper has no counterpart: this is a
+ * deployment convenience).  Same computation and arguments as bmnd_denoise
+ * with the App. A profile, but no context and no allocation: it calls no
+ * cudaMalloc, cudaFree, pinned-host or other allocating routine.  It is meant
+ * for callers that cannot allocate device memory: code running while another
+ * component owns the device allocator, services working inside a memory
+ * budget that is already committed, or environments where cudaMalloc is
+ * unavailable or would synchronize the device at the wrong moment.
+ *
+ * Scratch: one file-scope device array of 64 MiB, held by every GPU that
+ * loads the library until the process exits.  Arrays whose plan needs more
+ * scratch are rejected with BMND_ENOMEM before any work is enqueued (a 1-D
+ * signal of 262144 samples and a 2-D 512x512 image fit; a 2048x2048 image
+ * does not).
+ *   - The first call on a device (the current device) performs a one-time,
+ *     synchronous set-up: it resolves the array's device address, loads the
+ *     transform tables and constants and reads the device limits.  Make that
+ *     first call before any stream capture.
+ *   - Every call shares the array, which keeps the previous call's contents;
+ *     the call clears what must start at zero.  Calls whose work overlaps on
+ *     the GPU (different streams, or host threads on one device) race on the
+ *     array and give wrong results: serialize them.
+ *   - errbuf/errlen (may be NULL/0) receive a one-line message on error.
+ * Errors: as bmnd_denoise, plus BMND_ENOMEM when the array is too small. */
+bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                                 const int *patch, const int *step, const int *search,
+                                 const int *group_size, int stages, int mass_conserve, float *out,
+                                 void *stream, char *errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

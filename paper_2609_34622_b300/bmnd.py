@@ -56,7 +56,7 @@ class bmnd_job(ctypes.Structure):
 
 EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_error", "bmnd_denoise",
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
-           "bmnd_set_profiling", "bmnd_kernel_stats"]
+           "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4}
 
 _lib = None
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
                                ctypes.c_int, P(bmnd_params), vp, vp, vp, ctypes.c_int64, i64p, vp]
     lib.bmnd_denoise_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
     lib.bmnd_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.bmnd_denoise_noalloc.argtypes = [vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ip, ctypes.c_int,
+                                         ctypes.c_int, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bmnd_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
@@ -284,6 +286,22 @@ class Context:
                                                     ctypes.byref(ms)))
             res[name] = (n.value, ms.value)
         return res
+
+
+def bmnd_denoise_noalloc(y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,
+                         mass_conserve=0, stream=None):
+    """Allocation-free denoising on the current device (no context): the
+    library's scratch is a fixed 64 MiB device array; see include/bmnd.h."""
+    _check_tensor(y, "y")
+    _check_tensor(out, "out")
+    shape = tuple(y.shape)
+    err = ctypes.create_string_buffer(256)
+    st = load().bmnd_denoise_noalloc(_ptr(y), len(shape), _ints(shape, ctypes.c_int64), noise(noise_spec),
+                                     _ints(patch), _ints(step), _ints(search), _ints(group_size), int(stages),
+                                     int(mass_conserve), _ptr(out), _stream(stream), err, len(err))
+    if st != OK:
+        raise BmndError(st, err.value.decode())
+    return out
 
 
 def denoise(y, cfg: dict, ctx: Context | None = None, prm=None, stream=None):

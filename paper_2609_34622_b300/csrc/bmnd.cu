@@ -836,3 +836,190 @@ bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free denoising
+//
+// For callers that must not allocate device memory: code that runs while
+// another component owns the device allocator, inside a memory budget that is
+// already spoken for, or in an environment where cudaMalloc is unavailable or
+// would synchronize the device at the wrong moment.  The scratch of this entry
+// point is one file-scope device array of fixed size, held by every GPU that
+// loads the library until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoallocBytes = (size_t)64 << 20;  // 64 MiB of scratch per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Layout of the array: [tile counter | job table (2 DJob) | DCT table | work].
+constexpr size_t kNoallocCounter = 0;
+constexpr size_t kNoallocJobs = 256;
+constexpr size_t kNoallocTab = (kNoallocJobs + 2 * sizeof(DJob) + 255) & ~(size_t)255;
+constexpr size_t kNoallocWork = (kNoallocTab + 2 * GEN_TOTAL * sizeof(float) + 255) & ~(size_t)255;
+
+struct NoallocDevice {
+  bool ready;
+  unsigned char *base;  // device address of g_noalloc_scratch on this device
+  int max_smem;
+  int num_sms;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc[64];
+float g_noalloc_tab_host[2 * GEN_TOTAL];
+
+// One-time set-up on the current device: resolve the array's device address,
+// load the DCT tables and constants, read the SM count and shared-memory
+// limit.  Synchronous; the first call on a device must precede any stream
+// capture.
+bmnd_status noalloc_setup(int device, NoallocDevice *&out, char *err, size_t errlen) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (device < 0 || device >= 64) {
+    snprintf(err, errlen, "device %d out of range", device);
+    return BMND_EINVAL;
+  }
+  NoallocDevice &d = g_noalloc[device];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      snprintf(err, errlen, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      cudaGetLastError();
+      return BMND_ECUDA;
+    }
+    for (int J = 1; J <= 32; ++J) {
+      int off = (J - 1) * J * (2 * J - 1) / 6;
+      for (int k = 0; k < J; ++k)
+        for (int i = 0; i < J; ++i) {
+          double v = dct_entry(J, k, i);
+          g_noalloc_tab_host[off + k * J + i] = (float)v;
+          g_noalloc_tab_host[GEN_TOTAL + off + k * J + i] = (float)(v * v);
+        }
+    }
+    e = cudaMemcpy((unsigned char *)ptr + kNoallocTab, g_noalloc_tab_host, sizeof(g_noalloc_tab_host),
+                   cudaMemcpyHostToDevice);
+    int max_smem = 0, num_sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+      snprintf(err, errlen, "set-up: %s", cudaGetErrorString(e));
+      cudaGetLastError();
+      return BMND_ECUDA;
+    }
+    d.base = (unsigned char *)ptr;
+    d.max_smem = max_smem - 64;
+    d.num_sms = num_sms;
+    d.ready = true;
+  }
+  out = &d;
+  return BMND_OK;
+}
+
+// The allocation-free path on a stack context `c` whose scratch pointers lie
+// in the static array (nothing in it allocates).
+bmnd_status noalloc_run(bmnd_ctx *ctx, NoallocDevice *dev, const float *y, int ndim, const int64_t *shape,
+                        bmnd_noise noise, const int *patch, const int *step, const int *search,
+                        const int *group_size, int stages, int mass_conserve, float *out, cudaStream_t st) {
+  if (!y || !out || !group_size) return fail(ctx, BMND_EINVAL, "null y, out or group_size");
+  bmnd_status rc = check_noise(ctx, noise);
+  if (rc != BMND_OK) return rc;
+  if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
+  bmnd_params pr;
+  bmnd_default_params(&pr);
+  Plan pl;
+  rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, pl);
+  if (rc != BMND_OK) return rc;
+  const int64_t N = pl.g.N;
+  if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
+  // the group tables (last in the plan's layout) are only used by mass
+  // conservation
+  const size_t need = kNoallocWork + (mass_conserve ? pl.total : pl.o_groups);
+  if (need > kNoallocBytes)
+    return fail(ctx, BMND_ENOMEM, "this array needs %zu bytes of scratch; the allocation-free entry point has %zu",
+                need, kNoallocBytes);
+  unsigned char *B = dev->base + kNoallocWork;
+  const int gs1 = stages == 2 ? group_size[1] : group_size[0];
+  const int mc = mass_conserve & (stages == 2 ? 3 : 1);
+  DJob h[2];
+  bool any_mc[2] = {false, false};
+  int smax[2] = {0, 0};
+  for (int s = 1; s <= 2; ++s) {
+    DJob &J = h[s - 1];
+    memset(&J, 0, sizeof(J));
+    J.g = pl.g;
+    fill_stage(J.g, s, s == 1 ? group_size[0] : gs1, noise, pr);
+    const bool m = (mc >> (s - 1)) & 1;
+    float *pilot = (float *)(B + pl.o_pilot);
+    J.y = y;
+    J.guide = s == 1 ? y : pilot;
+    J.out = s == stages ? out : pilot;
+    J.eta = m ? (float *)(B + pl.o_eta) : nullptr;
+    J.partial = (float2 *)(B + pl.o_partial);
+    J.ref_local = (const int *)(B + pl.o_refs);
+    J.ref_count = (const int *)(B + pl.o_rcount);
+    J.groups = m ? (int *)(B + pl.o_groups) : nullptr;
+    J.gcount = m ? (int *)(B + pl.o_gcount) : nullptr;
+    any_mc[s - 1] = m;
+    smax[s - 1] = m ? std::max(pl.smem[s - 1], pl.smem[2]) : pl.smem[s - 1];
+  }
+  // from pageable host memory: the copy is staged before the call returns
+  CU(cudaMemcpyAsync(ctx->djobs, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  // the schedule flags must start at zero; everything else the kernels read
+  // (reference lists, partials, pilot, eta, group tables) is written first
+  CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
+  launch_sched(pl.s, B + pl.o_flags, ctx->djobs, pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
+  CU(cudaGetLastError());
+  const int64_t vox = pl.g.N;
+  const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
+  for (int s = 1; s <= stages; ++s) {
+    const DJob *dj = ctx->djobs + (s - 1);
+    rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
+    if (rc != BMND_OK) return rc;
+    launch_reduce(pl.D, dj, 1, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
+    CU(cudaGetLastError());
+    if (any_mc[s - 1]) {
+      rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
+      if (rc != BMND_OK) return rc;
+      launch_reduce(pl.D, dj, 1, vox, 0, rgrid, st);
+      CU(cudaGetLastError());
+    }
+  }
+  return BMND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                                 const int *patch, const int *step, const int *search,
+                                 const int *group_size, int stages, int mass_conserve, float *out,
+                                 void *stream, char *errbuf, size_t errlen) {
+  char err[256] = {0};
+  bmnd_status rc = BMND_OK;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(err, sizeof(err), "no current CUDA device");
+    rc = BMND_ECUDA;
+  }
+  NoallocDevice *dev = nullptr;
+  if (rc == BMND_OK) rc = noalloc_setup(device, dev, err, sizeof(err));
+  if (rc == BMND_OK) {
+    bmnd_ctx c;  // pointers into the static array; nothing is allocated or freed
+    c.device = device;
+    c.max_smem = dev->max_smem;
+    c.num_sms = dev->num_sms;
+    c.counters = (int *)(dev->base + kNoallocCounter);
+    c.djobs = (DJob *)(dev->base + kNoallocJobs);
+    c.tab = (float *)(dev->base + kNoallocTab);
+    rc = noalloc_run(&c, dev, y, ndim, shape, noise, patch, step, search, group_size, stages, mass_conserve, out,
+                     (cudaStream_t)stream);
+    if (rc != BMND_OK) snprintf(err, sizeof(err), "%s", c.err);
+  }
+  if (errbuf && errlen) snprintf(errbuf, errlen, "%s", rc == BMND_OK ? "" : err);
+  return rc;
+}
+
+}  // extern "C"
