@@ -217,6 +217,7 @@ __device__ __forceinline__ void xform_lines(float *__restrict__ buf, int nlines,
   int L = 1;
   while (L * 2 * nlines <= 32 && L * 2 <= J) L *= 2;
   const int items = nlines * L;
+#pragma unroll 1
   for (int i0 = 0; i0 < items; i0 += 32) {
     const int item = i0 + lane;
     const bool act = item < items;
@@ -254,38 +255,50 @@ __device__ __forceinline__ void xform_lines(float *__restrict__ buf, int nlines,
 
 // Full-depth orthonormal Haar of length N (power of two) in registers.
 // Forward output order: [scaling, coarsest detail, ..., finest details].
+// Levels are unrolled by template recursion so that every index is a
+// compile-time constant and the line stays in registers.
+template <int N, int LEN, bool SQ>
+__device__ __forceinline__ void haar_fwd_levels(float (&x)[N]) {
+  if constexpr (LEN >= 2) {
+    const float R = 0.70710678118654752f;
+    float t[LEN];
+#pragma unroll
+    for (int i = 0; i < LEN / 2; ++i) {
+      const float a = x[2 * i], b = x[2 * i + 1];
+      if (SQ) { t[i] = 0.5f * (a + b); t[LEN / 2 + i] = 0.5f * (a + b); }
+      else { t[i] = R * (a + b); t[LEN / 2 + i] = R * (a - b); }
+    }
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) x[i] = t[i];
+    haar_fwd_levels<N, LEN / 2, SQ>(x);
+  }
+}
+
+template <int N, int LEN>
+__device__ __forceinline__ void haar_inv_levels(float (&x)[N]) {
+  if constexpr (LEN <= N) {
+    const float R = 0.70710678118654752f;
+    float t[LEN];
+#pragma unroll
+    for (int i = 0; i < LEN / 2; ++i) {
+      const float a = x[i], d = x[LEN / 2 + i];
+      t[2 * i] = R * (a + d);
+      t[2 * i + 1] = R * (a - d);
+    }
+#pragma unroll
+    for (int i = 0; i < LEN; ++i) x[i] = t[i];
+    haar_inv_levels<N, LEN * 2>(x);
+  }
+}
+
 // MODE 0 forward, 1 inverse, 2 forward with squared coefficients.
 template <int N, int MODE>
 __device__ __forceinline__ void haar_line(float *__restrict__ buf, int base, int stride) {
-  float x[N], t[N];
+  float x[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) x[i] = buf[base + i * stride];
-  const float R = 0.70710678118654752f;
-  if (MODE != 1) {
-#pragma unroll
-    for (int len = N; len >= 2; len >>= 1) {
-#pragma unroll
-      for (int i = 0; i < len / 2; ++i) {
-        float a = x[2 * i], b = x[2 * i + 1];
-        if (MODE == 2) { t[i] = 0.5f * (a + b); t[len / 2 + i] = 0.5f * (a + b); }
-        else { t[i] = R * (a + b); t[len / 2 + i] = R * (a - b); }
-      }
-#pragma unroll
-      for (int i = 0; i < len; ++i) x[i] = t[i];
-    }
-  } else {
-#pragma unroll
-    for (int len = 2; len <= N; len <<= 1) {
-#pragma unroll
-      for (int i = 0; i < len / 2; ++i) {
-        float a = x[i], d = x[len / 2 + i];
-        t[2 * i] = R * (a + d);
-        t[2 * i + 1] = R * (a - d);
-      }
-#pragma unroll
-      for (int i = 0; i < len; ++i) x[i] = t[i];
-    }
-  }
+  if (MODE == 1) haar_inv_levels<N, 2>(x);
+  else haar_fwd_levels<N, N, MODE == 2>(x);
 #pragma unroll
   for (int i = 0; i < N; ++i) buf[base + i * stride] = x[i];
 }
@@ -411,7 +424,7 @@ __device__ __forceinline__ const float *axis_matrix(const float *mats, const int
 // Separable group transform T = (group axis) (x) DCT_j0 (x) ... on a warp's
 // shared group buffer of n members.  mode 0: T, 1: T^T = T^{-1}, 2: T.^2.
 template <int D>
-__device__ __noinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
+__device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
                             const float *mats, const int *moff, const float *tab) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -443,6 +456,7 @@ __device__ __noinline__ void group_xform(float *buf, const DGeom &g, int n, int 
     const int nl = n * per, st = bs[a];
     if ((ja & (ja - 1)) == 0) {
       // power-of-two length: register butterflies, one lane per line
+#pragma unroll 1
       for (int l = lane; l < nl; l += 32) {
         const int base = base_of(l);
         switch (ja) {
@@ -469,6 +483,7 @@ __device__ __noinline__ void group_xform(float *buf, const DGeom &g, int n, int 
   }
   // group axis
   if (n > 1) {
+#pragma unroll 1
     for (int v = lane; v < g.P; v += 32) {
       const int base = vbuf[v];
       if (g.gtrans == 1) { dct_line_generic(buf, base, g.MS, n, mode, tab); continue; }
@@ -490,7 +505,7 @@ __device__ __noinline__ void group_xform(float *buf, const DGeom &g, int n, int 
 // ---------------------------------------------------------------------------
 
 template <int D, int JL, int KB>
-__device__ __noinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
+__device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
                           const int *org, const int *rowoff, int lane, int *mem) {
   int lo[D], W[D];
   int64_t ncand = 1;
@@ -692,7 +707,7 @@ __device__ __noinline__ int warp_match(const DGeom &g, const float *__restrict__
 // alpha = d_g / (zeta^T 1) of Def. "Aggregation-aware constant-synthesis
 // correction" in *alpha_out.
 template <int D>
-__device__ __noinline__ int filter_group(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
+__device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
                                          const int *__restrict__ vreg, const int *__restrict__ vbuf,
                                          const float *__restrict__ omega, const float *__restrict__ Sg,
                                          const float *__restrict__ Sy, const float *__restrict__ Se,
@@ -701,89 +716,120 @@ __device__ __noinline__ int filter_group(const DGeom &g, int n, bool mc2, int la
                                          const float *tab, float *alpha_out) {
   const int P = g.P, MS = g.MS;
   const bool stage2 = g.stage == 2;
-  // ---- gather the guide group (y in stage 1, pilot in stage 2) and, for
-  // Poisson data, its variance map m_v = s_P [guide]_+ ----
-  BMND_FOR_ENTRIES({
-    const float gv = Sg[mem[m] + vreg[v]];
-    const int a = m * MS + vbuf[v];
-    bufB[a] = gv;
-    if (g.poisson) bufA[a] = g.s_p * fmaxf(gv, 0.f);
-  });
-  __syncwarp();
-  // sigma_k^2 = sum_i T_ki^2 m_v(u_i); Gaussian: sigma^2 (orthonormal T)
-  if (g.poisson) group_xform<D>(bufA, g, n, 2, lane, vbuf, mats, moff, tab);
-  group_xform<D>(bufB, g, n, 0, lane, vbuf, mats, moff, tab);
-  // ---- shrinkage; per-coefficient weight terms into bufA ----
+  // The transforms run as one loop over a short phase list so that the
+  // transform code is inlined once: before each transform, the phase's own
+  // gather / shrink / gain step.
+  //   stage 1: T^2 m_v (Poisson) | T y_g | shrink, weights | T^T C
+  //   stage 2: T^2 m_v (Poisson) | T gamma_g | gains, weights | T y_g | G Y, T^T C
   const float lam = g.lambda * 1.0001f, lam2 = lam * lam;
-  BMND_FOR_ENTRIES({
-    const int a = m * MS + vbuf[v];
-    const float s2 = g.poisson ? bufA[a] : g.var_g;
-    const float X = bufB[a];
-    float wterm;
-    if (!stage2) {
-      // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
-      // with count data, are zeroed whatever the rounding), as X^2 > ...
-      const bool keep = X * X > lam2 * s2;
-      bufB[a] = keep ? X : 0.f;
-      wterm = keep ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
-    } else {
-      const float S = fmaxf(X * X - g.a_power * s2, 0.f);
-      const float den = S + g.s_v * s2;
-      const float G = den > 0.f ? __fdividef(S, den) : 0.f;
-      bufB[a] = G;
-      wterm = g.wmodel == 0 ? G * G
-                            : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
-    }
-    bufA[a] = wterm;
-  });
-  __syncwarp();
-  // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums its row) ----
-  if (lane < n) {
-    // each lane starts at its own entry so that the rows' reads spread over
-    // the banks; the sum is taken in a fixed order per row
-    float r = 0.f;
-    const float *row = bufA + lane * MS;
-    int v = lane % P;
-    for (int t = 0; t < P; ++t) {
-      r += row[vbuf[v]];
-      if (++v == P) v = 0;
-    }
-    rr_s[lane] = r;
-  }
-  __syncwarp();
-  // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
-  if (lane < n) {
-    float R = 0.f;
-    if (g.wscope == 1) {
-      for (int l = 0; l < n; ++l) R += rr_s[l];
-    } else if (g.gtrans == 0) {
-      R = rr_s[0] / (float)n;
-      for (int b = n; b >= 2; b >>= 1) R += rr_s[n / b + lane / b] / (float)b;
-    } else {
-      const float *Mt = tab + gen_off(n);
-      for (int l = 0; l < n; ++l) {
-        const float c = __ldg(Mt + l * n + lane);
-        R += c * c * rr_s[l];
+  float *syn = stage2 ? bufA : bufB;
+  const int first = g.poisson ? 0 : 1;
+  const int last = stage2 ? 4 : 3;
+  for (int ph = first; ph <= last; ++ph) {
+    float *tb;
+    int tmode;
+    if (ph == 0) {
+      // gather the guide group (y in stage 1, pilot in stage 2) and, for
+      // Poisson data, its variance map m_v = s_P [guide]_+; then
+      // sigma_k^2 = sum_i T_ki^2 m_v(u_i)
+      BMND_FOR_ENTRIES({
+        const float gv = Sg[mem[m] + vreg[v]];
+        const int a = m * MS + vbuf[v];
+        bufB[a] = gv;
+        bufA[a] = g.s_p * fmaxf(gv, 0.f);
+      });
+      __syncwarp();
+      tb = bufA;
+      tmode = 2;
+    } else if (ph == 1) {
+      if (!g.poisson) {
+        BMND_FOR_ENTRIES({ bufB[m * MS + vbuf[v]] = Sg[mem[m] + vreg[v]]; });
+        __syncwarp();
       }
+      tb = bufB;
+      tmode = 0;
+    } else if (ph == 2) {
+      // ---- shrinkage; per-coefficient weight terms into bufA ----
+      BMND_FOR_ENTRIES({
+        const int a = m * MS + vbuf[v];
+        const float s2 = g.poisson ? bufA[a] : g.var_g;
+        const float X = bufB[a];
+        float wterm;
+        if (!stage2) {
+          // |X| > lambda sigma with a relative guard of 1e-4 (exact ties,
+          // common with count data, are zeroed whatever the rounding)
+          const bool keep = X * X > lam2 * s2;
+          bufB[a] = keep ? X : 0.f;
+          wterm = keep ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
+        } else {
+          const float S = fmaxf(X * X - g.a_power * s2, 0.f);
+          const float den = S + g.s_v * s2;
+          const float G = den > 0.f ? __fdividef(S, den) : 0.f;
+          bufB[a] = G;
+          wterm = g.wmodel == 0 ? G * G
+                                : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
+        }
+        bufA[a] = wterm;
+      });
+      __syncwarp();
+      // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums
+      // its row, starting at its own entry so the reads spread over banks) ----
+      if (lane < n) {
+        float r = 0.f;
+        const float *row = bufA + lane * MS;
+        int v = lane % P;
+        for (int t = 0; t < P; ++t) {
+          r += row[vbuf[v]];
+          if (++v == P) v = 0;
+        }
+        rr_s[lane] = r;
+      }
+      __syncwarp();
+      // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
+      if (lane < n) {
+        float R = 0.f;
+        if (g.wscope == 1) {
+          for (int l = 0; l < n; ++l) R += rr_s[l];
+        } else if (g.gtrans == 0) {
+          R = rr_s[0] / (float)n;
+          for (int bb = n; bb >= 2; bb >>= 1) R += rr_s[n / bb + lane / bb] / (float)bb;
+        } else {
+          const float *Mt = tab + gen_off(n);
+          for (int l = 0; l < n; ++l) {
+            const float c = __ldg(Mt + l * n + lane);
+            R += c * c * rr_s[l];
+          }
+        }
+        wts[lane] = R > 0.f ? 1.f / R : 1.f;
+      }
+      __syncwarp();
+      if (stage2) {
+        // Wiener: the observation group, to be transformed next
+        BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
+        __syncwarp();
+        tb = bufA;
+        tmode = 0;
+      } else {
+        tb = bufB;
+        tmode = 1;
+      }
+    } else if (ph == 3) {
+      if (stage2) {
+        BMND_FOR_ENTRIES({
+          const int a = m * MS + vbuf[v];
+          bufA[a] *= bufB[a];
+        });
+        __syncwarp();
+        tb = bufA;
+        tmode = 1;
+      } else {
+        break;
+      }
+    } else {
+      break;
     }
-    wts[lane] = R > 0.f ? 1.f / R : 1.f;
+    group_xform<D>(tb, g, n, tmode, lane, vbuf, mats, moff, tab);
   }
-  __syncwarp();
-  float *syn = bufB;
-  if (stage2) {
-    // Wiener: transform the observation group and apply the gains
-    BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
-    __syncwarp();
-    group_xform<D>(bufA, g, n, 0, lane, vbuf, mats, moff, tab);
-    BMND_FOR_ENTRIES({
-      const int a = m * MS + vbuf[v];
-      bufA[a] *= bufB[a];
-    });
-    __syncwarp();
-    syn = bufA;
-  }
-  // ---- inverse transform: synthesized patches ----
-  group_xform<D>(syn, g, n, 1, lane, vbuf, mats, moff, tab);
   float alpha = 0.f;
   if (mc2) {
     // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
