@@ -206,6 +206,47 @@ bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable);
 bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches,
                               double *total_ms);
 
+/* ---- Serving loop --------------------------------------------------------
+ * A request server (the paper has no counterpart; it serves the data-parallel
+ * path to many concurrent requests).  A worker thread admits submitted jobs in
+ * arrival order while the device-memory budget and the slot count allow,
+ * copies each admitted job's input to the device and builds its reference
+ * schedule, then runs steps: in every step each active job runs its next
+ * stage, and jobs of the same kernel class share one launch of each kernel
+ * (continuous batching: jobs that arrive while a step runs join the next one;
+ * a job's stage-1 estimate and buffers stay on the device between its
+ * stages).  When a job's last stage is done its output is copied to the host
+ * and its memory is released.  Each job owns its tiles and partial sums, so
+ * its result is bitwise the same as bmnd_denoise on the job alone.
+ * Jobs use the App. A profile. */
+typedef struct bmnd_server bmnd_server;
+typedef struct {
+    size_t mem_budget_bytes;  /* device memory for admitted jobs (0: 8 GiB)   */
+    int max_slots;            /* jobs admitted at the same time (0: 256)      */
+} bmnd_server_config;
+typedef struct {
+    int64_t submitted, completed, failed;
+    double p50_ms, p99_ms, mean_ms;  /* latency: submission to result on the host */
+    double voxels_per_s;             /* completed voxels / (last completion - first submission) */
+    int64_t steps;                   /* server steps (shared launches)            */
+    double mean_jobs_per_step;
+} bmnd_server_stats;
+
+/* Create a server on `device` (allocates the budget up front).  Errors:
+ * BMND_EINVAL, BMND_ENOMEM, BMND_ECUDA. */
+bmnd_status bmnd_server_create(bmnd_server **srv, int device, const bmnd_server_config *cfg);
+/* Submit a job; job->y and job->out are HOST arrays that must stay valid
+ * until bmnd_server_wait returns for the ticket.  Invalid jobs (as for
+ * bmnd_denoise) and jobs larger than the budget are rejected here. */
+bmnd_status bmnd_server_submit(bmnd_server *srv, const bmnd_job *job, int64_t *ticket);
+/* Wait for a ticket (timeout_ms < 0: no limit; BMND_ETIMEOUT if it runs out);
+ * returns the job's status and its latency in *latency_ms (may be NULL).  A
+ * ticket can be waited for once. */
+bmnd_status bmnd_server_wait(bmnd_server *srv, int64_t ticket, int timeout_ms, double *latency_ms);
+bmnd_status bmnd_server_get_stats(bmnd_server *srv, bmnd_server_stats *stats);
+/* Finish all submitted jobs, stop the worker and release everything. */
+bmnd_status bmnd_server_destroy(bmnd_server *srv);
+
 /* Allocation-free denoising (the paper has no counterpart: this is a
  * deployment convenience).  Same computation and arguments as bmnd_denoise
  * with the App. A profile, but no context and no allocation: it calls no

@@ -54,9 +54,21 @@ class bmnd_job(ctypes.Structure):
                 ("stages", ctypes.c_int), ("mass_conserve", ctypes.c_int)]
 
 
+class bmnd_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int)]
+
+
+class bmnd_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("voxels_per_s", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("mean_jobs_per_step", ctypes.c_double)]
+
+
 EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_error", "bmnd_denoise",
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
-           "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc"]
+           "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
+           "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4}
 
 _lib = None
@@ -89,6 +101,11 @@ def load(path: str = LIB_PATH):
                                ctypes.c_int, P(bmnd_params), vp, vp, vp, ctypes.c_int64, i64p, vp]
     lib.bmnd_denoise_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
     lib.bmnd_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.bmnd_server_create.argtypes = [P(vp), ctypes.c_int, P(bmnd_server_config)]
+    lib.bmnd_server_submit.argtypes = [vp, P(bmnd_job), i64p]
+    lib.bmnd_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_int, P(ctypes.c_double)]
+    lib.bmnd_server_get_stats.argtypes = [vp, P(bmnd_server_stats)]
+    lib.bmnd_server_destroy.argtypes = [vp]
     lib.bmnd_denoise_noalloc.argtypes = [vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ip, ctypes.c_int,
                                          ctypes.c_int, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bmnd_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double)]
@@ -286,6 +303,77 @@ class Context:
                                                     ctypes.byref(ms)))
             res[name] = (n.value, ms.value)
         return res
+
+
+def _fill_job(j, y_ptr, out_ptr, shape, c):
+    j.y, j.out = y_ptr, out_ptr
+    j.ndim = len(shape)
+    for a, sz in enumerate(shape):
+        j.shape[a] = int(sz)
+        j.patch[a] = int(c["patch"][a])
+        j.step[a] = int(c["step"][a])
+        j.search[a] = int(c["search"][a])
+    j.noise = noise(c["noise"])
+    gs = c.get("group_size", (16, 32))
+    j.group_size[0], j.group_size[1] = int(gs[0]), int(gs[1])
+    j.stages = int(c.get("stages", 2))
+    j.mass_conserve = int(c.get("mass_conserve", 0))
+
+
+class Server:
+    """Request server of the C ABI (bmnd_server_*): host numpy arrays in,
+    host numpy arrays out; admission by device-memory budget and continuous
+    batching happen in the library's worker thread."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0, max_slots: int = 0):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        cfg = bmnd_server_config(int(mem_budget), int(max_slots))
+        st = lib.bmnd_server_create(ctypes.byref(self.handle), int(device), ctypes.byref(cfg))
+        if st != OK:
+            raise BmndError(st, "bmnd_server_create failed")
+        self._keep = {}
+
+    def bmnd_server_submit(self, y: np.ndarray, cfg: dict, out: np.ndarray | None = None) -> int:
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        if out is None:
+            out = np.empty_like(y)
+        j = bmnd_job()
+        _fill_job(j, y.ctypes.data, out.ctypes.data, y.shape, cfg)
+        t = ctypes.c_int64()
+        st = self._lib.bmnd_server_submit(self.handle, ctypes.byref(j), ctypes.byref(t))
+        if st != OK:
+            raise BmndError(st, "submit rejected")
+        self._keep[t.value] = (y, out)
+        return t.value
+
+    def bmnd_server_wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (output array, latency in ms)."""
+        lat = ctypes.c_double()
+        st = self._lib.bmnd_server_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(lat))
+        y, out = self._keep.pop(ticket)
+        if st != OK:
+            raise BmndError(st, "job failed")
+        return out, lat.value
+
+    def bmnd_server_get_stats(self) -> dict:
+        s = bmnd_server_stats()
+        st = self._lib.bmnd_server_get_stats(self.handle, ctypes.byref(s))
+        if st != OK:
+            raise BmndError(st, "stats")
+        return {f: getattr(s, f) for f, _ in bmnd_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            self._lib.bmnd_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bmnd_denoise_noalloc(y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,

@@ -1023,3 +1023,426 @@ bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving loop: memory-budgeted admission and continuous batching
+// ---------------------------------------------------------------------------
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over the server's device arena (host bookkeeping).
+struct ArenaAlloc {
+  std::map<size_t, size_t> free_;  // offset -> size
+  void init(size_t size) {
+    free_.clear();
+    free_[0] = size;
+  }
+  bool alloc(size_t bytes, size_t &off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        off = it->first;
+        size_t rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+enum { SJ_PENDING = 0, SJ_STAGE1 = 1, SJ_STAGE2 = 2, SJ_DONE = 3, SJ_FAILED = 4 };
+
+struct SrvJob {
+  int64_t ticket = 0;
+  bmnd_job spec;  // y / out are HOST pointers
+  Plan plan;
+  size_t off = 0, bytes = 0;
+  int state = SJ_PENDING;
+  bmnd_status status = BMND_OK;
+  Clock::time_point t_submit, t_done;
+  float *dy = nullptr, *dout = nullptr;
+  DJob *djob = nullptr;        // this job's own descriptor (schedule kernels)
+  unsigned char *scratch = nullptr;
+};
+
+}  // namespace
+
+struct bmnd_server {
+  bmnd_ctx *ctx = nullptr;
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 0;
+  unsigned char *arena = nullptr;
+  ArenaAlloc alloc;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SrvJob *> pending;
+  std::vector<SrvJob *> active;
+  std::unordered_map<int64_t, SrvJob *> jobs;
+  int64_t next_ticket = 1;
+  std::thread worker;
+  bool stop = false;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  DJob *dtab = nullptr, *htab = nullptr;
+  // statistics
+  std::vector<double> lat_ms;
+  int64_t submitted = 0, completed = 0, failed = 0, steps = 0, jobs_in_steps = 0;
+  double vox_done = 0;
+  bool have_first = false;
+  Clock::time_point t_first, t_last;
+};
+
+namespace {
+
+size_t srv_job_bytes(const Plan &pl) {
+  return al256(pl.g.N * 4) * 2 + al256(2 * sizeof(DJob)) + pl.total;
+}
+
+// Descriptor of one job for the stage it runs next.
+DJob srv_stage_job(const SrvJob *j, int stage, const bmnd_params &pr) {
+  const Plan &pl = j->plan;
+  DJob J;
+  memset(&J, 0, sizeof(J));
+  J.g = pl.g;
+  const int stages = j->spec.stages;
+  const int M = stage == 1 ? j->spec.group_size[0] : (stages == 2 ? j->spec.group_size[1] : j->spec.group_size[0]);
+  fill_stage(J.g, stage, M, j->spec.noise, pr);
+  const int mc = j->spec.mass_conserve & (stages == 2 ? 3 : 1);
+  const bool m = (mc >> (stage - 1)) & 1;
+  unsigned char *B = j->scratch;
+  float *pilot = (float *)(B + pl.o_pilot);
+  J.y = j->dy;
+  J.guide = stage == 1 ? j->dy : pilot;
+  J.out = stage == stages ? j->dout : pilot;
+  J.eta = m ? (float *)(B + pl.o_eta) : nullptr;
+  J.partial = (float2 *)(B + pl.o_partial);
+  J.ref_local = (const int *)(B + pl.o_refs);
+  J.ref_count = (const int *)(B + pl.o_rcount);
+  J.groups = m ? (int *)(B + pl.o_groups) : nullptr;
+  J.gcount = m ? (int *)(B + pl.o_gcount) : nullptr;
+  return J;
+}
+
+bmnd_status srv_fail(bmnd_server *S, const char *what, cudaError_t e) {
+  snprintf(S->ctx->err, sizeof(S->ctx->err), "%s: %s", what, cudaGetErrorString(e));
+  return BMND_ECUDA;
+}
+
+// One server step: every active job runs its next stage; jobs sharing a
+// kernel class (axes, last-axis patch length, candidates per lane) share
+// one launch of each kernel.
+bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
+  bmnd_params pr;
+  bmnd_default_params(&pr);
+  std::map<std::pair<int, int>, std::vector<SrvJob *>> classes;
+  for (SrvJob *j : run) classes[{j->plan.D, j->plan.g.jL * 16 + pick_kb(j->plan)}].push_back(j);
+  size_t tab_off = 0;
+  for (auto &kv : classes) {
+    std::vector<SrvJob *> &cj = kv.second;
+    const int D = kv.first.first, jL = kv.first.second / 16, kb = kv.first.second % 16;
+    int tiles = 0, smax = 0;
+    int64_t vox = 0;
+    bool any_mc = false;
+    for (size_t i = 0; i < cj.size(); ++i) {
+      SrvJob *j = cj[i];
+      const int stage = j->state == SJ_STAGE1 ? 1 : 2;
+      DJob J = srv_stage_job(j, stage, pr);
+      J.tile_base = tiles;
+      J.vox_base = vox;
+      tiles += j->plan.g.ntiles;
+      vox += j->plan.g.N;
+      const bool m = J.groups != nullptr;
+      any_mc = any_mc || m;
+      smax = std::max(smax, m ? std::max(j->plan.smem[stage - 1], j->plan.smem[2]) : j->plan.smem[stage - 1]);
+      S->htab[tab_off + i] = J;
+    }
+    DJob *dj = S->dtab + tab_off;
+    cudaError_t e = cudaMemcpyAsync(dj, S->htab + tab_off, cj.size() * sizeof(DJob), cudaMemcpyHostToDevice, S->st);
+    if (e != cudaSuccess) return srv_fail(S, "job table copy", e);
+    const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
+    bmnd_status rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 0, smax, S->st);
+    if (rc != BMND_OK) return rc;
+    launch_reduce(D, dj, (int)cj.size(), vox, any_mc ? 1 : 0, rgrid, S->st);
+    if (any_mc) {
+      rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 2, smax, S->st);
+      if (rc != BMND_OK) return rc;
+      launch_reduce(D, dj, (int)cj.size(), vox, 0, rgrid, S->st);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return srv_fail(S, "stage launch", e);
+    tab_off += cj.size();
+  }
+  cudaError_t e = cudaEventRecord(S->ev, S->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(S->ev);
+  if (e != cudaSuccess) return srv_fail(S, "step", e);
+  return BMND_OK;
+}
+
+// Admission set-up of one job: input copy, descriptor, reference schedule.
+bmnd_status srv_admit(bmnd_server *S, SrvJob *j) {
+  const Plan &pl = j->plan;
+  unsigned char *base = S->arena + j->off;
+  const size_t nb = al256(pl.g.N * 4);
+  j->dy = (float *)base;
+  j->dout = (float *)(base + nb);
+  j->djob = (DJob *)(base + 2 * nb);
+  j->scratch = base + 2 * nb + al256(2 * sizeof(DJob));
+  bmnd_params pr;
+  bmnd_default_params(&pr);
+  DJob J = srv_stage_job(j, 1, pr);
+  cudaError_t e = cudaMemcpyAsync(j->dy, j->spec.y, pl.g.N * 4, cudaMemcpyHostToDevice, S->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(j->djob, &J, sizeof(DJob), cudaMemcpyHostToDevice, S->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->scratch + pl.o_flags, 0, (size_t)pl.nflags, S->st);
+  if (e != cudaSuccess) return srv_fail(S, "admission copy", e);
+  launch_sched(pl.s, j->scratch + pl.o_flags, j->djob, pl.g.ntiles, (int *)(j->scratch + pl.o_refs),
+               (int *)(j->scratch + pl.o_rcount), S->st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return srv_fail(S, "schedule launch", e);
+  return BMND_OK;
+}
+
+void srv_finish(bmnd_server *S, SrvJob *j, bmnd_status rc) {
+  // caller holds S->mu
+  j->status = rc;
+  j->state = rc == BMND_OK ? SJ_DONE : SJ_FAILED;
+  j->t_done = Clock::now();
+  S->alloc.release(j->off, j->bytes);
+  if (rc == BMND_OK) {
+    ++S->completed;
+    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
+    S->vox_done += (double)j->plan.g.N;
+    S->t_last = j->t_done;
+  } else {
+    ++S->failed;
+  }
+}
+
+void srv_loop(bmnd_server *S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::vector<SrvJob *> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
+      if (S->stop && S->pending.empty() && S->active.empty()) break;
+      // memory-budgeted admission in arrival order
+      while (!S->pending.empty() && (int)(S->active.size() + admit.size()) < S->max_slots) {
+        SrvJob *j = S->pending.front();
+        size_t off = 0;
+        if (!S->alloc.alloc(j->bytes, off)) break;
+        j->off = off;
+        S->pending.pop_front();
+        admit.push_back(j);
+      }
+    }
+    bmnd_status rc = BMND_OK;
+    for (SrvJob *j : admit) {
+      rc = srv_admit(S, j);
+      if (rc != BMND_OK) break;
+    }
+    std::vector<SrvJob *> run;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (SrvJob *j : admit) {
+        j->state = SJ_STAGE1;
+        S->active.push_back(j);
+      }
+      run = S->active;
+    }
+    if (rc == BMND_OK && !run.empty()) rc = srv_step(S, run);
+    // results of jobs that ran their last stage go back to the host
+    std::vector<SrvJob *> finished;
+    for (SrvJob *j : run) {
+      const bool last = rc != BMND_OK || j->state == SJ_STAGE2 || j->spec.stages == 1;
+      if (!last) continue;
+      if (rc == BMND_OK) {
+        cudaError_t e = cudaMemcpyAsync(j->spec.out, j->dout, j->plan.g.N * 4, cudaMemcpyDeviceToHost, S->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          j->status = BMND_ECUDA;
+        }
+      }
+      finished.push_back(j);
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      ++S->steps;
+      S->jobs_in_steps += (int64_t)run.size();
+      for (SrvJob *j : run)
+        if (j->state == SJ_STAGE1 && j->spec.stages == 2 && rc == BMND_OK) j->state = SJ_STAGE2;
+      for (SrvJob *j : finished) {
+        S->active.erase(std::find(S->active.begin(), S->active.end(), j));
+        srv_finish(S, j, rc != BMND_OK ? rc : j->status);
+      }
+    }
+    S->cv_done.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+bmnd_status bmnd_server_create(bmnd_server **out, int device, const bmnd_server_config *cfg) {
+  if (!out) return BMND_EINVAL;
+  *out = nullptr;
+  bmnd_server *S = new bmnd_server();
+  S->device = device;
+  S->budget = cfg && cfg->mem_budget_bytes ? cfg->mem_budget_bytes : ((size_t)8 << 30);
+  S->max_slots = cfg && cfg->max_slots > 0 ? cfg->max_slots : 256;
+  bmnd_status rc = bmnd_create(&S->ctx, device, 0);
+  if (rc == BMND_OK) {
+    cudaSetDevice(device);
+    if (cudaMalloc(&S->arena, S->budget) != cudaSuccess ||
+        cudaMalloc(&S->dtab, sizeof(DJob) * S->max_slots) != cudaSuccess ||
+        cudaMallocHost(&S->htab, sizeof(DJob) * S->max_slots) != cudaSuccess) {
+      cudaGetLastError();
+      rc = BMND_ENOMEM;
+    } else if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) != cudaSuccess) {
+      rc = BMND_ECUDA;
+    }
+  }
+  if (rc != BMND_OK) {
+    if (S->arena) cudaFree(S->arena);
+    if (S->dtab) cudaFree(S->dtab);
+    if (S->htab) cudaFreeHost(S->htab);
+    if (S->ctx) bmnd_destroy(S->ctx);
+    delete S;
+    return rc;
+  }
+  S->alloc.init(S->budget);
+  S->worker = std::thread(srv_loop, S);
+  *out = S;
+  return BMND_OK;
+}
+
+bmnd_status bmnd_server_submit(bmnd_server *S, const bmnd_job *job, int64_t *ticket) {
+  if (!S || !job || !ticket) return BMND_EINVAL;
+  if (!job->y || !job->out) return fail(S->ctx, BMND_EINVAL, "null y or out");
+  SrvJob *j = new SrvJob();
+  j->spec = *job;
+  bmnd_params pr;
+  bmnd_default_params(&pr);
+  bmnd_status rc;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    rc = check_noise(S->ctx, job->noise);
+    if (rc == BMND_OK && (job->mass_conserve < 0 || job->mass_conserve > 3))
+      rc = fail(S->ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
+    if (rc == BMND_OK)
+      rc = make_plan(S->ctx, job->ndim, job->shape, job->patch, job->step, job->search, job->group_size, job->stages,
+                     job->mass_conserve, pr, j->plan);
+    if (rc == BMND_OK) {
+      j->bytes = al256(srv_job_bytes(j->plan));
+      if (j->bytes > S->budget)
+        rc = fail(S->ctx, BMND_ENOMEM, "job needs %zu bytes, the server budget is %zu", j->bytes, S->budget);
+    }
+    if (rc != BMND_OK) {
+      delete j;
+      return rc;
+    }
+    j->ticket = S->next_ticket++;
+    j->t_submit = Clock::now();
+    if (!S->have_first) {
+      S->have_first = true;
+      S->t_first = j->t_submit;
+    }
+    ++S->submitted;
+    S->jobs[j->ticket] = j;
+    S->pending.push_back(j);
+    *ticket = j->ticket;
+  }
+  S->cv_work.notify_one();
+  return BMND_OK;
+}
+
+bmnd_status bmnd_server_wait(bmnd_server *S, int64_t ticket, int timeout_ms, double *latency_ms) {
+  if (!S) return BMND_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) return BMND_EINVAL;
+  SrvJob *j = it->second;
+  auto done = [&] { return j->state == SJ_DONE || j->state == SJ_FAILED; };
+  if (timeout_ms < 0) S->cv_done.wait(lk, done);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) return BMND_ETIMEOUT;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+  bmnd_status rc = j->status;
+  S->jobs.erase(it);
+  delete j;
+  return rc;
+}
+
+bmnd_status bmnd_server_get_stats(bmnd_server *S, bmnd_server_stats *o) {
+  if (!S || !o) return BMND_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  memset(o, 0, sizeof(*o));
+  o->submitted = S->submitted;
+  o->completed = S->completed;
+  o->failed = S->failed;
+  o->steps = S->steps;
+  o->mean_jobs_per_step = S->steps ? (double)S->jobs_in_steps / S->steps : 0.0;
+  std::vector<double> l = S->lat_ms;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    auto q = [&](double f) { return l[std::min(l.size() - 1, (size_t)std::floor(f * (l.size() - 1) + 0.5))]; };
+    o->p50_ms = q(0.50);
+    o->p99_ms = q(0.99);
+    double s = 0;
+    for (double v : l) s += v;
+    o->mean_ms = s / l.size();
+    double span = std::chrono::duration<double>(S->t_last - S->t_first).count();
+    o->voxels_per_s = span > 0 ? S->vox_done / span : 0.0;
+  }
+  return BMND_OK;
+}
+
+bmnd_status bmnd_server_destroy(bmnd_server *S) {
+  if (!S) return BMND_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto &kv : S->jobs) delete kv.second;
+  cudaSetDevice(S->device);
+  cudaDeviceSynchronize();
+  if (S->ev) cudaEventDestroy(S->ev);
+  if (S->st) cudaStreamDestroy(S->st);
+  if (S->arena) cudaFree(S->arena);
+  if (S->dtab) cudaFree(S->dtab);
+  if (S->htab) cudaFreeHost(S->htab);
+  if (S->ctx) bmnd_destroy(S->ctx);
+  delete S;
+  return BMND_OK;
+}
+
+}  // extern "C"
