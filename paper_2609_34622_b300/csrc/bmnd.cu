@@ -165,15 +165,17 @@ struct Plan {
 };
 
 int stage_smem(const DGeom &g, int M, int nreg) {
+  if (g.lean) nreg = 1;  // only the matching guide is staged
   size_t b = al16(sizeof(DJob));
   b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4 + KMAXD * 4 + (g.fp ? (size_t)g.P * 4 : 0) +
            (size_t)g.fp * 4);
+  b = al16(b + (g.lean ? (size_t)g.P * 8 : 0));
   size_t mats = 0;
   for (int a = 0; a < g.D; ++a) mats += (size_t)mat_block(g.j[a]) * 4;
   b = al16(b + mats);
   b = al16(b + (size_t)nreg * (g.region + RPAD) * 4);
-  b += (size_t)g.region * 8;
-  b += (size_t)NW * warp_bytes(M, g.MS, g.fp);
+  b = al16(b + (size_t)g.region * 8);
+  b += (size_t)NW * warp_bytes(M, g.MS, g.fp, g.lean);
   return (int)b;
 }
 
@@ -258,7 +260,14 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   }
   g.jL = g.j[D - 1];
   g.rows = g.P / g.jL;
-  g.LS = g.jL + (g.jL % 2 == 0 ? 1 : 0);
+  // with three or more axes the halo of a tile (2 rad + j - 1 per axis)
+  // dominates its region: read y and eta from global memory and spend the
+  // shared memory on larger tiles
+  g.lean = D >= 3 ? 1 : 0;
+  // group-buffer line stride: odd (bank-conflict free lines), except in lean
+  // mode with rows of a multiple of 4 floats, where the unpadded layout keeps
+  // stride-1 lines float4-aligned and saves a fifth of the warp buffers
+  g.LS = (g.lean && g.jL % 4 == 0) ? g.jL : g.jL + (g.jL % 2 == 0 ? 1 : 0);
   g.MS = g.rows * g.LS;
   // private group footprint for the accumulation when it is small
   {

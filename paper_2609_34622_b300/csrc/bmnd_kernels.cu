@@ -379,10 +379,21 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 // (r = k for 0 < k < J/2 with s_k = +1, r = J - k for k > J/2 with s_k = -1,
 // and no V term for k = 0 and k = J/2).
 template <int J>
-__device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base, int st, int mode) {
+__device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base, int st, int mode, bool vec4) {
   float x[J];
+  // vec4: a stride-1 line of unpadded rows (LS a multiple of 4), which starts
+  // on a 16-byte boundary; read and written as float4
+  const bool vec = (J % 4 == 0) && vec4;
+  if (vec) {
 #pragma unroll
-  for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
+    for (int i = 0; i < J; i += 4) {
+      const float4 q = *reinterpret_cast<const float4 *>(buf + base + i);
+      x[i] = q.x; x[i + 1] = q.y; x[i + 2] = q.z; x[i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
+  }
   const float s0 = c_scale[2 * ilog2c(J)], s1 = c_scale[2 * ilog2c(J) + 1];
   if (mode == 0) {
     Lee<J>::fwd(x);
@@ -412,8 +423,14 @@ __device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base,
       for (int k = J / 2 + 1; k < J; ++k) x[k] = (S - a[J - k]) * invJ;
     }
   }
+  if (vec) {
 #pragma unroll
-  for (int i = 0; i < J; ++i) buf[base + i * st] = x[i];
+    for (int i = 0; i < J; i += 4)
+      *reinterpret_cast<float4 *>(buf + base + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < J; ++i) buf[base + i * st] = x[i];
+  }
 }
 
 // Shared-memory matrices of one patch axis: [forward | transposed | squared].
@@ -454,17 +471,18 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
     };
     const float *M = axis_matrix(mats, moff, a, ja, mode);
     const int nl = n * per, st = bs[a];
+    const bool vec4 = a == D - 1 && (g.LS & 3) == 0;
     if ((ja & (ja - 1)) == 0) {
       // power-of-two length: register butterflies, one lane per line
 #pragma unroll 1
       for (int l = lane; l < nl; l += 32) {
         const int base = base_of(l);
         switch (ja) {
-          case 2: fast_dct_line<2>(buf, base, st, mode); break;
-          case 4: fast_dct_line<4>(buf, base, st, mode); break;
-          case 8: fast_dct_line<8>(buf, base, st, mode); break;
-          case 16: fast_dct_line<16>(buf, base, st, mode); break;
-          default: fast_dct_line<32>(buf, base, st, mode); break;
+          case 2: fast_dct_line<2>(buf, base, st, mode, vec4); break;
+          case 4: fast_dct_line<4>(buf, base, st, mode, vec4); break;
+          case 8: fast_dct_line<8>(buf, base, st, mode, vec4); break;
+          case 16: fast_dct_line<16>(buf, base, st, mode, vec4); break;
+          default: fast_dct_line<32>(buf, base, st, mode, vec4); break;
         }
       }
       __syncwarp();
@@ -699,6 +717,38 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
     }                                                  \
   }
 
+// Lean gathers: entry (m, v) of the group from global arrays at
+// gb[m] + vgl[v], GGB independent loads in flight per lane, each value handed
+// to put(m, v, a[.], b[.]) (b may be null).
+constexpr int GGB = 8;
+template <typename Put>
+__device__ __forceinline__ void gather_global(const float *__restrict__ a, const float *__restrict__ b,
+                                              const int64_t *__restrict__ gb, const int64_t *__restrict__ vgl,
+                                              int n, int P, int lane, Put put) {
+  int m = lane / P, v = lane - (lane / P) * P;
+  while (m < n) {
+    float va[GGB], vb[GGB];
+    int m1 = m, v1 = v;
+#pragma unroll
+    for (int k = 0; k < GGB; ++k) {
+      va[k] = vb[k] = 0.f;
+      if (m1 < n) {
+        const int64_t u = gb[m1] + vgl[v1];
+        va[k] = __ldg(a + u);
+        if (b) vb[k] = __ldg(b + u);
+      }
+      v1 += 32;
+      while (v1 >= P) { v1 -= P; ++m1; }
+    }
+#pragma unroll
+    for (int k = 0; k < GGB; ++k) {
+      if (m < n) put(m, v, va[k], vb[k]);
+      v += 32;
+      while (v >= P) { v -= P; ++m; }
+    }
+  }
+}
+
 // Filters the group whose member origins (region offsets) are in mem[0..n).
 // Stage 1: hard thresholding of T y_g against sigma_k from the variance map;
 // stage 2: Wiener shrinkage of T y_g with gains from the pilot group.  Leaves
@@ -713,7 +763,9 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
                                          const float *__restrict__ Sy, const float *__restrict__ Se,
                                          float *__restrict__ bufA, float *__restrict__ bufB, float *__restrict__ wts,
                                          float *__restrict__ rr_s, const float *mats, const int *moff,
-                                         const float *tab, float *alpha_out) {
+                                         const float *tab, const float *__restrict__ gy,
+                                         const float *__restrict__ ge, const int64_t *__restrict__ gb,
+                                         const int64_t *__restrict__ vgl, float *alpha_out) {
   const int P = g.P, MS = g.MS;
   const bool stage2 = g.stage == 2;
   // The transforms run as one loop over a short phase list so that the
@@ -805,7 +857,11 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       __syncwarp();
       if (stage2) {
         // Wiener: the observation group, to be transformed next
-        BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
+        if (D >= 3 && g.lean)
+          gather_global(gy, nullptr, gb, vgl, n, P, lane,
+                        [&](int m, int v, float x, float) { bufA[m * MS + vbuf[v]] = x; });
+        else
+          BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
         __syncwarp();
         tb = bufA;
         tmode = 0;
@@ -835,13 +891,21 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
     // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
     // alpha = d_g / zeta^T 1 to every synthesized entry
     float dg = 0.f, z1 = 0.f;
-    BMND_FOR_ENTRIES({
-      const int u = mem[m] + vreg[v];
-      const float et = Se[u];
-      const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-      dg = fmaf(z, Sy[u] - syn[m * MS + vbuf[v]], dg);
-      z1 += z;
-    });
+    if (D >= 3 && g.lean) {
+      gather_global(ge, gy, gb, vgl, n, P, lane, [&](int m, int v, float et, float yv) {
+        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+        dg = fmaf(z, yv - syn[m * MS + vbuf[v]], dg);
+        z1 += z;
+      });
+    } else {
+      BMND_FOR_ENTRIES({
+        const int u = mem[m] + vreg[v];
+        const float et = Se[u];
+        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+        dg = fmaf(z, Sy[u] - syn[m * MS + vbuf[v]], dg);
+        z1 += z;
+      });
+    }
     dg = warp_sum(dg);
     z1 = warp_sum(z1);
     alpha = z1 > 0.f ? dg / z1 : 0.f;
@@ -857,6 +921,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
 // Shared-memory layout of one job (the host computes the same sizes).
 struct SmemLayout {
   int *vreg, *vbuf, *rowoff, *moff, *fvoff, *fpreg;
+  int64_t *vgl;  // lean: global offset of every patch entry
   float *omega, *mats, *Sg, *Sy, *Se;
   float2 *acc;
   unsigned char *warps;
@@ -878,19 +943,21 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
   s.fvoff = reinterpret_cast<int *>(p); p += sizeof(int) * (g.fp ? g.P : 0);
   s.fpreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.fp;
   p = al16p(p);
+  s.vgl = reinterpret_cast<int64_t *>(p); p += sizeof(int64_t) * (g.lean ? g.P : 0);
+  p = al16p(p);
   s.mats = reinterpret_cast<float *>(p);
   for (int a = 0; a < g.D; ++a) p += sizeof(float) * mat_block(g.j[a]);
   p = al16p(p);
   const int RS = g.region + RPAD;
   s.Sg = reinterpret_cast<float *>(p); p += sizeof(float) * RS;
   s.Sy = s.Sg;
-  if (stage2) { s.Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  if (stage2 && !g.lean) { s.Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
   s.Se = nullptr;
-  if (mc2) { s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  if (mc2 && !g.lean) { s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
   p = al16p(p);
   s.acc = reinterpret_cast<float2 *>(p); p += sizeof(float2) * g.region;
-  s.warps = p;
-  s.wbytes = warp_bytes(g.M, g.MS, g.fp);
+  s.warps = al16p(p);
+  s.wbytes = warp_bytes(g.M, g.MS, g.fp, g.lean);
   return s;
 }
 
@@ -943,6 +1010,16 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
         L.vreg[v] = ro;
         L.vbuf[v] = (v / g.jL) * g.LS + (v % g.jL);
+        if (g.lean) {
+          int r3 = v;
+          int64_t go = 0;
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) {
+            go += (int64_t)(r3 % g.j[d]) * g.st[d];
+            r3 /= g.j[d];
+          }
+          L.vgl[v] = go;
+        }
         L.omega[v] = w;
         if (v % g.jL == 0) L.rowoff[v / g.jL] = ro;
         if (g.fp) {
@@ -1001,6 +1078,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
     float *bufB = bufA + g.M * g.MS;
     float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * g.MS);
+    int64_t *gb = reinterpret_cast<int64_t *>(fpb + g.fp);
     float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
     float2 *acc = L.acc;
     const int *vreg = L.vreg, *vbuf = L.vbuf, *rowoff = L.rowoff;
@@ -1034,14 +1112,14 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
         if (in) {
           vg = __ldg(gsrc + gi);
-          if (stage2) vy = __ldg(ysrc + gi);
-          if (mc2) ve = __ldg(esrc + gi);
+          if (stage2 && !g.lean) vy = __ldg(ysrc + gi);
+          if (mc2 && !g.lean) ve = __ldg(esrc + gi);
         }
         acc[e] = make_float2(0.f, 0.f);
       }
       Sg[e] = vg;
-      if (stage2) Sy[e] = vy;
-      if (mc2) Se[e] = ve;
+      if (stage2 && !g.lean) Sy[e] = vy;
+      if (mc2 && !g.lean) Se[e] = ve;
     }
     __syncthreads();
 
@@ -1074,8 +1152,22 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           __syncwarp();
         }
         if (mode != 1) {
+          if (D >= 3 && g.lean) {
+            // global origin of every member
+            if (lane < n) {
+              int rem = mem[lane];
+              int64_t o = 0;
+#pragma unroll
+              for (int d = D - 1; d >= 0; --d) {
+                o += (int64_t)(org[d] + rem % g.RG[d]) * g.st[d];
+                rem /= g.RG[d];
+              }
+              gb[lane] = o;
+            }
+            __syncwarp();
+          }
           const int which = filter_group<D>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
-                                            rr_s, L.mats, L.moff, tab, &alpha);
+                                            rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
           syn = which ? bufA : bufB;
         }
       }

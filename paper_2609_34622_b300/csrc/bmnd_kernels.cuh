@@ -39,10 +39,11 @@ constexpr int GEN_TOTAL = 11440;
 cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
 
 // Bytes of one warp's shared block: member list, weights, plane sums and two
-// level lists (5 x MMAX words), two group buffers of M x MS floats, and the
-// private footprint (fp float2), rounded up to 16 bytes.
-__host__ __device__ constexpr int warp_bytes(int M, int MS, int fp) {
-  return (5 * MMAX * 4 + 2 * M * MS * 4 + fp * 8 + 15) & ~15;
+// level lists (5 x MMAX words), two group buffers of M x MS floats, the
+// private footprint (fp float2) and, when y and eta are read from global
+// memory (lean), the members' global origins (MMAX int64), rounded up to 16.
+__host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean) {
+  return (5 * MMAX * 4 + 2 * M * MS * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
 }
 
 // Floats reserved in shared memory for the three J x J matrices of one patch
@@ -79,6 +80,10 @@ struct DGeom {
   // group before merging it into the tile region; fp = 0 disables it
   int fp;
   int FW[KMAXD];
+  // lean: only the matching guide is staged in shared memory; the filter
+  // reads y (stage 2) and eta (second mass-conservation sweep) from global
+  // memory, which leaves room for larger tiles when D >= 3
+  int lean;
 };
 
 struct DJob {
