@@ -366,8 +366,20 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.var_g = (float)(g.poisson ? 0.0 : nz.sigma * nz.sigma);
 }
 
+// Patch side of the specialized stage kernel for a plan: the kernels with a
+// compile-time shape take cubic patches (side jL on every axis) of the sizes
+// instantiated below; 0 selects the generic kernel of the plan's rank.
+int kernel_jl(const Plan &pl) {
+  const int D = pl.D, jL = pl.g.jL;
+  for (int a = 0; a < D; ++a)
+    if (pl.g.j[a] != jL) return 0;
+  if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
+  return 0;
+}
+
+// Candidates per lane of the matching loop for the plan's stage kernel.
 int pick_kb(const Plan &pl) {
-  int D = pl.D, jL = pl.g.jL;
+  const int D = pl.D, jL = kernel_jl(pl);
   if (D == 1 && jL == 32) return 5;
   if (D == 1 && jL == 16) return 4;
   if (D == 2 && jL == 8) return 8;
@@ -516,9 +528,9 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
                  pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
   }
   CU(cudaGetLastError());
-  int kjL = plans[0].g.jL, kkb = pick_kb(plans[0]);
+  int kjL = kernel_jl(plans[0]), kkb = pick_kb(plans[0]);
   for (int i = 1; i < nj; ++i)
-    if (plans[i].g.jL != plans[0].g.jL) { kjL = 0; kkb = 4; }
+    if (kernel_jl(plans[i]) != kjL) { kjL = 0; kkb = 4; }
   int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = first_stage; s <= last_stage; ++s) {
     const DJob *dj = ctx->djobs + (s - 1) * nj;
@@ -778,7 +790,7 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   CU(cudaGetLastError());
   if (do_match) {
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
-    rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
     if (rc != BMND_OK) return rc;
   }
   std::vector<int> cnt(pl.g.ntiles);
@@ -983,12 +995,12 @@ bmnd_status noalloc_run(bmnd_ctx *ctx, NoallocDevice *dev, const float *y, int n
   const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = 1; s <= stages; ++s) {
     const DJob *dj = ctx->djobs + (s - 1);
-    rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
     if (rc != BMND_OK) return rc;
     launch_reduce(pl.D, dj, 1, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
     CU(cudaGetLastError());
     if (any_mc[s - 1]) {
-      rc = launch_stage(ctx, pl.D, pl.g.jL, pick_kb(pl), dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
+      rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
       if (rc != BMND_OK) return rc;
       launch_reduce(pl.D, dj, 1, vox, 0, rgrid, st);
       CU(cudaGetLastError());
@@ -1170,7 +1182,7 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
   bmnd_params pr;
   bmnd_default_params(&pr);
   std::map<std::pair<int, int>, std::vector<SrvJob *>> classes;
-  for (SrvJob *j : run) classes[{j->plan.D, j->plan.g.jL * 16 + pick_kb(j->plan)}].push_back(j);
+  for (SrvJob *j : run) classes[{j->plan.D, kernel_jl(j->plan) * 16 + pick_kb(j->plan)}].push_back(j);
   size_t tab_off = 0;
   for (auto &kv : classes) {
     std::vector<SrvJob *> &cj = kv.second;

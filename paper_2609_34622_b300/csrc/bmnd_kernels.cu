@@ -165,16 +165,9 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ int warp_max_i(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ int warp_sum_i(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+// single-instruction warp reductions of 32-bit integers
+__device__ __forceinline__ int warp_max_i(int v) { return __reduce_max_sync(0xffffffffu, v); }
+__device__ __forceinline__ int warp_sum_i(int v) { return __reduce_add_sync(0xffffffffu, v); }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -371,6 +364,19 @@ struct Lee<1> {
 };
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+__host__ __device__ constexpr int ipow(int b, int e) { return e <= 0 ? 1 : b * ipow(b, e - 1); }
+
+// Patch shape known at compile time: the specialized kernels take cubic
+// patches of side JC on all D axes (JC = 0: the shape is read from the
+// geometry at run time).  LS / MS follow the host's group-buffer layout:
+// rows padded to an odd stride, unpadded multiples of 4 in lean mode (D >= 3).
+template <int D, int JC>
+struct CubeShape {
+  static constexpr bool fixed = JC > 0;
+  static constexpr int P = fixed ? ipow(JC, D) : 0;
+  static constexpr int LS = fixed ? ((D >= 3 && JC % 4 == 0) ? JC : JC + (JC % 2 == 0 ? 1 : 0)) : 0;
+  static constexpr int MS = fixed ? ipow(JC, D - 1) * LS : 0;
+};
 
 // Orthonormal DCT of one line (length J, power of two) with stride st.
 // mode 0: C x; 1: C^T x; 2: (C.^2) x, using
@@ -440,38 +446,43 @@ __device__ __forceinline__ const float *axis_matrix(const float *mats, const int
 
 // Separable group transform T = (group axis) (x) DCT_j0 (x) ... on a warp's
 // shared group buffer of n members.  mode 0: T, 1: T^T = T^{-1}, 2: T.^2.
-template <int D>
+template <int D, int JC>
 __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
                             const float *mats, const int *moff, const float *tab) {
+  using SH = CubeShape<D, JC>;
+  const int P = SH::fixed ? SH::P : g.P;
+  const int LS = SH::fixed ? SH::LS : g.LS;
+  const int MS = SH::fixed ? SH::MS : g.MS;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int ja = g.j[a];
+    const int ja = SH::fixed ? JC : g.j[a];
     if (ja == 1) continue;
-    const int per = g.P / ja;  // lines per member along axis a
+    const int per = P / ja;  // lines per member along axis a
     int bs[D];
     {
       int s = 1;
 #pragma unroll
       for (int e = D - 1; e >= 0; --e) {
-        if (e == D - 1) { bs[e] = 1; s = g.LS; }
-        else { bs[e] = s; s *= g.j[e]; }
+        if (e == D - 1) { bs[e] = 1; s = LS; }
+        else { bs[e] = s; s *= SH::fixed ? JC : g.j[e]; }
       }
     }
     auto base_of = [&](int l) {
       int m = l / per, li = l - m * per;
-      int base = m * g.MS, rem = li;
+      int base = m * MS, rem = li;
 #pragma unroll
       for (int e = D - 1; e >= 0; --e) {
         if (e == a) continue;
-        int c = rem % g.j[e];
-        rem /= g.j[e];
+        const int je = SH::fixed ? JC : g.j[e];
+        int c = rem % je;
+        rem /= je;
         base += c * bs[e];
       }
       return base;
     };
     const float *M = axis_matrix(mats, moff, a, ja, mode);
     const int nl = n * per, st = bs[a];
-    const bool vec4 = a == D - 1 && (g.LS & 3) == 0;
+    const bool vec4 = a == D - 1 && (LS & 3) == 0;
     if ((ja & (ja - 1)) == 0) {
       // power-of-two length: register butterflies, one lane per line
 #pragma unroll 1
@@ -502,15 +513,15 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
   // group axis
   if (n > 1) {
 #pragma unroll 1
-    for (int v = lane; v < g.P; v += 32) {
+    for (int v = lane; v < P; v += 32) {
       const int base = vbuf[v];
-      if (g.gtrans == 1) { dct_line_generic(buf, base, g.MS, n, mode, tab); continue; }
+      if (g.gtrans == 1) { dct_line_generic(buf, base, MS, n, mode, tab); continue; }
       switch (n) {
-        case 2: haar_line_mode<2>(buf, base, g.MS, mode); break;
-        case 4: haar_line_mode<4>(buf, base, g.MS, mode); break;
-        case 8: haar_line_mode<8>(buf, base, g.MS, mode); break;
-        case 16: haar_line_mode<16>(buf, base, g.MS, mode); break;
-        case 32: haar_line_mode<32>(buf, base, g.MS, mode); break;
+        case 2: haar_line_mode<2>(buf, base, MS, mode); break;
+        case 4: haar_line_mode<4>(buf, base, MS, mode); break;
+        case 8: haar_line_mode<8>(buf, base, MS, mode); break;
+        case 16: haar_line_mode<16>(buf, base, MS, mode); break;
+        case 32: haar_line_mode<32>(buf, base, MS, mode); break;
         default: break;
       }
     }
@@ -756,7 +767,7 @@ __device__ __forceinline__ void gather_global(const float *__restrict__ a, const
 // weights in wts, and for the second mass-conservation sweep the correction
 // alpha = d_g / (zeta^T 1) of Def. "Aggregation-aware constant-synthesis
 // correction" in *alpha_out.
-template <int D>
+template <int D, int JC>
 __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
                                          const int *__restrict__ vreg, const int *__restrict__ vbuf,
                                          const float *__restrict__ omega, const float *__restrict__ Sg,
@@ -766,7 +777,9 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
                                          const float *tab, const float *__restrict__ gy,
                                          const float *__restrict__ ge, const int64_t *__restrict__ gb,
                                          const int64_t *__restrict__ vgl, float *alpha_out) {
-  const int P = g.P, MS = g.MS;
+  using SH = CubeShape<D, JC>;
+  const int P = SH::fixed ? SH::P : g.P;
+  const int MS = SH::fixed ? SH::MS : g.MS;
   const bool stage2 = g.stage == 2;
   // The transforms run as one loop over a short phase list so that the
   // transform code is inlined once: before each transform, the phase's own
@@ -884,7 +897,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
     } else {
       break;
     }
-    group_xform<D>(tb, g, n, tmode, lane, vbuf, mats, moff, tab);
+    group_xform<D, JC>(tb, g, n, tmode, lane, vbuf, mats, moff, tab);
   }
   float alpha = 0.f;
   if (mc2) {
@@ -1069,6 +1082,9 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     const int tile = gt - sj->tile_base;
     const bool stage2 = g.stage == 2;
     const bool mc2 = mode == 2;
+    using SH = CubeShape<D, JL>;
+    const int P = SH::fixed ? SH::P : g.P;
+    const int MS = SH::fixed ? SH::MS : g.MS;
     unsigned char *wp = L.warps + (size_t)warp * L.wbytes;
     int *mem = reinterpret_cast<int *>(wp);
     float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
@@ -1076,8 +1092,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
     int *lst = reinterpret_cast<int *>(wp + 4 * MMAX * 4);
     float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
-    float *bufB = bufA + g.M * g.MS;
-    float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * g.MS);
+    float *bufB = bufA + g.M * MS;
+    float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * MS);
     int64_t *gb = reinterpret_cast<int64_t *>(fpb + g.fp);
     float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
     float2 *acc = L.acc;
@@ -1166,7 +1182,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             }
             __syncwarp();
           }
-          const int which = filter_group<D>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
+          const int which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
                                             rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
           syn = which ? bufA : bufB;
         }
@@ -1220,14 +1236,14 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             unsigned mask = __ballot_sync(0xffffffffu, mine);
             if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
             __syncwarp();
-            int items = __popc(mask) * g.P;
+            int items = __popc(mask) * P;
             for (int it = lane; it < items; it += 32) {
-              int r = it / g.P, v = it - r * g.P;
+              int r = it / P, v = it - r * P;
               int m = lst[r];
               int a = lvl[m] + L.fvoff[v];
               float wo = wts[m] * omega[v];
               float2 t = fpb[a];
-              t.x = fmaf(wo, syn[m * g.MS + vbuf[v]] + alpha, t.x);
+              t.x = fmaf(wo, syn[m * MS + vbuf[v]] + alpha, t.x);
               t.y += wo;
               fpb[a] = t;
             }
@@ -1255,14 +1271,14 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             unsigned mask = __ballot_sync(0xffffffffu, mine);
             if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
             __syncwarp();
-            int items = __popc(mask) * g.P;
+            int items = __popc(mask) * P;
             for (int it = lane; it < items; it += 32) {
-              int r = it / g.P, v = it - r * g.P;
+              int r = it / P, v = it - r * P;
               int m = lst[r];
               int a = mem[m] + vreg[v];
               float wo = wts[m] * omega[v];
               float2 t = acc[a];
-              t.x = fmaf(wo, syn[m * g.MS + vbuf[v]] + alpha, t.x);
+              t.x = fmaf(wo, syn[m * MS + vbuf[v]] + alpha, t.x);
               t.y += wo;
               acc[a] = t;
             }
@@ -1401,8 +1417,9 @@ typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 template <int D, int JL, int KB>
 stage_fn stage_ptr(int minb) { return minb >= 2 ? &k_stage<D, JL, KB, 2> : &k_stage<D, JL, KB, 1>; }
 
-// Stage kernel for a geometry: D kernel axes, last-axis patch length jL,
-// candidates per lane kb, and the register budget: minb = 2 limits registers
+// Stage kernel for a geometry: D kernel axes, jL > 0 the side of a cubic
+// patch (compile-time shape) or 0 for any shape, candidates per lane kb, and
+// the register budget: minb = 2 limits registers
 // so that two CTAs share an SM (used when their shared memory fits), minb = 1
 // gives the kernel the whole register file.
 stage_fn select_stage_kernel(int D, int jL, int kb, int minb) {
