@@ -1090,7 +1090,6 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
     float *rr_s = reinterpret_cast<float *>(wp + 2 * MMAX * 4);
     int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
-    int *lst = reinterpret_cast<int *>(wp + 4 * MMAX * 4);
     float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
     float *bufB = bufA + g.M * MS;
     float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * MS);
@@ -1188,68 +1187,75 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
       }
       if (mode == 1) continue;
-      // ---- overlap levels of the group's members: level(m) = 1 + the
-      // highest level of an earlier member whose patch overlaps m's.  Members
-      // of one level cover disjoint locations, so adding them level by level
-      // keeps, at every location, the members' order.
-      int mylev = 0, maxlev = 0, boxbase = 0;
-      if (has) {
-        int cm[D];
-        {
-          int rem = lane < n ? mem[lane] : 0;
+      // ---- accumulation in the members' order: the warp adds one member
+      // after another, lanes over its patch entries (distinct locations), so
+      // every location receives its contributions in member order ----
+      auto add_members = [&](float2 *dst, const int *mbase, const int *eoff) {
+        if constexpr (SH::fixed && SH::P % 32 == 0) {
+          constexpr int KV = SH::P / 32;
+          int eo[KV], vb[KV];
+          float om[KV];
 #pragma unroll
-          for (int d = D - 1; d >= 0; --d) { cm[d] = rem % g.RG[d]; rem /= g.RG[d]; }
-        }
-        for (int m = 1; m < n; ++m) {
-          bool ov = lane < m;
-#pragma unroll
-          for (int d = 0; d < D; ++d) {
-            int o = __shfl_sync(0xffffffffu, cm[d], m);
-            ov = ov && abs(cm[d] - o) < g.j[d];
+          for (int k = 0; k < KV; ++k) {
+            eo[k] = eoff[lane + 32 * k];
+            vb[k] = vbuf[lane + 32 * k];
+            om[k] = omega[lane + 32 * k];
           }
-          int l = warp_max_i(ov ? mylev + 1 : 0);
-          if (lane == m) mylev = l;
-        }
-        maxlev = warp_max_i(lane < n ? mylev : 0);
-        if (g.fp) {
-          // private footprint: the box [core, core + 2 rad + j - 1] of the
-          // reference holds every member patch
-          int fo = 0, bb = 0;
-          {
-            int rem = sj->ref_local[tslot + ri], fs = 1;
-            int c[D];
+          for (int m = 0; m < n; ++m) {
+            const int b = mbase[m];
+            const float wm = wts[m];
+            const float *sr = syn + m * MS;
 #pragma unroll
-            for (int d = D - 1; d >= 0; --d) { c[d] = rem % g.C[d]; rem /= g.C[d]; }
-#pragma unroll
-            for (int d = D - 1; d >= 0; --d) {
-              bb += c[d] * g.rst[d];
-              fo += (cm[d] - c[d]) * fs;
-              fs *= g.FW[d];
-            }
-          }
-          boxbase = bb;
-          if (lane < n) lvl[lane] = fo;  // footprint offset of member `lane`
-          for (int f = lane; f < g.fp; f += 32) fpb[f] = make_float2(0.f, 0.f);
-          __syncwarp();
-          for (int Lv = 0; Lv <= maxlev; ++Lv) {
-            const bool mine = lane < n && mylev == Lv;
-            unsigned mask = __ballot_sync(0xffffffffu, mine);
-            if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
-            __syncwarp();
-            int items = __popc(mask) * P;
-            for (int it = lane; it < items; it += 32) {
-              int r = it / P, v = it - r * P;
-              int m = lst[r];
-              int a = lvl[m] + L.fvoff[v];
-              float wo = wts[m] * omega[v];
-              float2 t = fpb[a];
-              t.x = fmaf(wo, syn[m * MS + vbuf[v]] + alpha, t.x);
+            for (int k = 0; k < KV; ++k) {
+              const float wo = wm * om[k];
+              float2 t = dst[b + eo[k]];
+              t.x = fmaf(wo, sr[vb[k]] + alpha, t.x);
               t.y += wo;
-              fpb[a] = t;
+              dst[b + eo[k]] = t;
+            }
+            __syncwarp();
+          }
+        } else {
+          for (int m = 0; m < n; ++m) {
+            const int b = mbase[m];
+            const float wm = wts[m];
+            const float *sr = syn + m * MS;
+            for (int v = lane; v < P; v += 32) {
+              const float wo = wm * omega[v];
+              float2 t = dst[b + eoff[v]];
+              t.x = fmaf(wo, sr[vbuf[v]] + alpha, t.x);
+              t.y += wo;
+              dst[b + eoff[v]] = t;
             }
             __syncwarp();
           }
         }
+      };
+      int boxbase = 0;
+      if (has && g.fp) {
+        // private footprint: the box [core, core + 2 rad + j - 1] of the
+        // reference holds every member patch; lvl[m] = offset of member m
+        int c[D];
+        {
+          int rem = sj->ref_local[tslot + ri];
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) { c[d] = rem % g.C[d]; rem /= g.C[d]; }
+        }
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) boxbase += c[d] * g.rst[d];
+        if (lane < n) {
+          int rem = mem[lane], fo = 0, fs = 1;
+#pragma unroll
+          for (int d = D - 1; d >= 0; --d) {
+            fo += (rem % g.RG[d] - c[d]) * fs;
+            rem /= g.RG[d];
+            fs *= g.FW[d];
+          }
+          lvl[lane] = fo;
+        }
+        for (int f = lane; f < g.fp; f += 32) fpb[f] = make_float2(0.f, 0.f);
+        __syncwarp();
+        add_members(fpb, lvl, L.fvoff);
       }
       // ---- ordered, atomic-free accumulation into the tile region ----
       if (!(warp == 0 && rd == 0)) named_sync(1 + warp, 64);
@@ -1266,24 +1272,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             }
           }
         } else {
-          for (int Lv = 0; Lv <= maxlev; ++Lv) {
-            const bool mine = lane < n && mylev == Lv;
-            unsigned mask = __ballot_sync(0xffffffffu, mine);
-            if (mine) lst[__popc(mask & ((1u << lane) - 1u))] = lane;
-            __syncwarp();
-            int items = __popc(mask) * P;
-            for (int it = lane; it < items; it += 32) {
-              int r = it / P, v = it - r * P;
-              int m = lst[r];
-              int a = mem[m] + vreg[v];
-              float wo = wts[m] * omega[v];
-              float2 t = acc[a];
-              t.x = fmaf(wo, syn[m * MS + vbuf[v]] + alpha, t.x);
-              t.y += wo;
-              acc[a] = t;
-            }
-            __syncwarp();
-          }
+          add_members(acc, mem, vreg);
         }
       }
       __threadfence_block();
