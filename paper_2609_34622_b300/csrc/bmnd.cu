@@ -158,11 +158,24 @@ struct Plan {
   SGeom s;
   int64_t nflags;
   int Mmax;
+  int gtrans;            // group transform (Haar / DCT)
   int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
   size_t o_flags, o_refs, o_rcount, o_partial, o_pilot, o_eta, o_groups, o_gcount, total;
 };
+
+// Patch side of the specialized stage kernels for a shape: they take cubic
+// patches (side jL on every axis) of the sizes instantiated with the kernels,
+// with a Haar group transform; 0 selects the generic kernel of the rank.
+int cube_side(int D, const int *j, int gtrans) {
+  const int jL = j[D - 1];
+  if (gtrans != BMND_GROUP_HAAR) return 0;
+  for (int a = 0; a < D; ++a)
+    if (j[a] != jL) return 0;
+  if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
+  return 0;
+}
 
 int stage_smem(const DGeom &g, int M, int nreg) {
   if (g.lean) nreg = 1;  // only the matching guide is staged
@@ -264,11 +277,20 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   // dominates its region: read y and eta from global memory and spend the
   // shared memory on larger tiles
   g.lean = D >= 3 ? 1 : 0;
-  // group-buffer line stride: odd (bank-conflict free lines), except in lean
-  // mode with rows of a multiple of 4 floats, where the unpadded layout keeps
-  // stride-1 lines float4-aligned and saves a fifth of the warp buffers
-  g.LS = (g.lean && g.jL % 4 == 0) ? g.jL : g.jL + (g.jL % 2 == 0 ? 1 : 0);
-  g.MS = g.rows * g.LS;
+  pl.gtrans = pr.group_transform;
+  if (cube_side(D, g.j, pl.gtrans) && g.P <= 32) {
+    // specialized kernels with members in registers: unpadded rows, odd
+    // member stride (whole members and whole entry columns are read)
+    g.LS = g.jL;
+    g.MS = g.P | 1;
+  } else {
+    // group-buffer line stride: odd (bank-conflict free lines), except in
+    // lean mode with rows of a multiple of 4 floats, where the unpadded
+    // layout keeps stride-1 lines float4-aligned and saves a fifth of the
+    // warp buffers
+    g.LS = (g.lean && g.jL % 4 == 0) ? g.jL : g.jL + (g.jL % 2 == 0 ? 1 : 0);
+    g.MS = g.rows * g.LS;
+  }
   // private group footprint for the accumulation when it is small
   {
     int64_t fp = 1;
@@ -287,7 +309,33 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   int C[KMAXD];
   for (int a = 0; a < D; ++a) C[a] = (int)std::min<int64_t>(target[D], g.ell[a] + 1);
   int nreg_max = (stages == 2 ? 2 : 1) + (mass_conserve ? 1 : 0);
-  for (;;) {
+  if (D >= 3) {
+    // every core shape up to the target: the smallest staged region per core
+    // location, discounted while there are fewer than 2 tiles per SM
+    int best[KMAXD] = {0}, lim[KMAXD];
+    double best_cost = 0.0;
+    for (int a = 0; a < D; ++a) { lim[a] = C[a]; C[a] = 1; }
+    for (;;) {
+      set_tiles(g, C);
+      if (stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem) {
+        const double cost = (double)g.region / (double)g.cap / (double)std::min<int64_t>(g.ntiles, 2 * 148);
+        if (best[0] == 0 || cost < best_cost) {
+          best_cost = cost;
+          for (int a = 0; a < D; ++a) best[a] = C[a];
+        }
+      }
+      int a = D - 1;
+      while (a >= 0 && C[a] == lim[a]) C[a--] = 1;
+      if (a < 0) break;
+      ++C[a];
+    }
+    if (best[0] == 0) return fail(ctx, BMND_EUNSUPPORTED, "patch/group too large for shared memory (P=%d, M=%d)", g.P, pl.Mmax);
+    for (int a = 0; a < D; ++a) C[a] = best[a];
+    set_tiles(g, C);
+  }
+  // one or two axes: halve the largest core side until the tile fits and
+  // there are 2 tiles per SM (or the cores reach their minimum)
+  while (D < 3) {
     set_tiles(g, C);
     bool fits = stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem;
     int big = 0;
@@ -366,16 +414,8 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.var_g = (float)(g.poisson ? 0.0 : nz.sigma * nz.sigma);
 }
 
-// Patch side of the specialized stage kernel for a plan: the kernels with a
-// compile-time shape take cubic patches (side jL on every axis) of the sizes
-// instantiated below; 0 selects the generic kernel of the plan's rank.
-int kernel_jl(const Plan &pl) {
-  const int D = pl.D, jL = pl.g.jL;
-  for (int a = 0; a < D; ++a)
-    if (pl.g.j[a] != jL) return 0;
-  if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
-  return 0;
-}
+// Patch side of the specialized stage kernel for a plan (0: generic).
+int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans); }
 
 // Candidates per lane of the matching loop for the plan's stage kernel.
 int pick_kb(const Plan &pl) {

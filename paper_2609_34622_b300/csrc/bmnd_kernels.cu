@@ -2,6 +2,8 @@
 // decomposition.  Every kernel here is launched from bmnd.cu.
 #include "bmnd_kernels.cuh"
 
+#include <type_traits>
+
 #include <float.h>
 #include <limits.h>
 
@@ -368,45 +370,35 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e <= 0 ? 1 : b * i
 
 // Patch shape known at compile time: the specialized kernels take cubic
 // patches of side JC on all D axes (JC = 0: the shape is read from the
-// geometry at run time).  LS / MS follow the host's group-buffer layout:
-// rows padded to an odd stride, unpadded multiples of 4 in lean mode (D >= 3).
+// geometry at run time).  Patches of up to 32 entries are filtered with the
+// members in registers (rf): unpadded rows (LS = JC) and an odd member stride
+// MS = P | 1.  Larger ones use the shared-memory line transforms: rows
+// padded to an odd stride, unpadded multiples of 4 in lean mode (D >= 3).
+// The host lays the group buffers out the same way.
 template <int D, int JC>
 struct CubeShape {
   static constexpr bool fixed = JC > 0;
   static constexpr int P = fixed ? ipow(JC, D) : 0;
-  static constexpr int LS = fixed ? ((D >= 3 && JC % 4 == 0) ? JC : JC + (JC % 2 == 0 ? 1 : 0)) : 0;
-  static constexpr int MS = fixed ? ipow(JC, D - 1) * LS : 0;
+  static constexpr bool rf = fixed && P <= 32;
+  static constexpr int LS = !fixed ? 0 : (rf || (D >= 3 && JC % 4 == 0)) ? JC : JC + (JC % 2 == 0 ? 1 : 0);
+  static constexpr int MS = !fixed ? 0 : rf ? (P | 1) : ipow(JC, D - 1) * LS;
 };
 
-// Orthonormal DCT of one line (length J, power of two) with stride st.
-// mode 0: C x; 1: C^T x; 2: (C.^2) x, using
+// Orthonormal DCT of a line held in registers (length J, power of two).
+// MODE 0: C x; 1: C^T x; 2: (C.^2) x, using
 // C_ki^2 = c_k^2 (1 + cos(pi (2i+1) 2k / (2J))) / 2: the squared transform is
 // (sum_i m_i + s_k V_r) / J with V a length-J/2 DCT-II of m_i + m_{J-1-i}
 // (r = k for 0 < k < J/2 with s_k = +1, r = J - k for k > J/2 with s_k = -1,
 // and no V term for k = 0 and k = J/2).
-template <int J>
-__device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base, int st, int mode, bool vec4) {
-  float x[J];
-  // vec4: a stride-1 line of unpadded rows (LS a multiple of 4), which starts
-  // on a 16-byte boundary; read and written as float4
-  const bool vec = (J % 4 == 0) && vec4;
-  if (vec) {
-#pragma unroll
-    for (int i = 0; i < J; i += 4) {
-      const float4 q = *reinterpret_cast<const float4 *>(buf + base + i);
-      x[i] = q.x; x[i + 1] = q.y; x[i + 2] = q.z; x[i + 3] = q.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
-  }
+template <int J, int MODE>
+__device__ __forceinline__ void dct_reg(float (&x)[J]) {
   const float s0 = c_scale[2 * ilog2c(J)], s1 = c_scale[2 * ilog2c(J) + 1];
-  if (mode == 0) {
+  if constexpr (MODE == 0) {
     Lee<J>::fwd(x);
     x[0] *= s0;
 #pragma unroll
     for (int k = 1; k < J; ++k) x[k] *= s1;
-  } else if (mode == 1) {
+  } else if constexpr (MODE == 1) {
     x[0] *= s0;
 #pragma unroll
     for (int k = 1; k < J; ++k) x[k] *= s1;
@@ -427,8 +419,32 @@ __device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base,
       x[J / 2] = S * invJ;
 #pragma unroll
       for (int k = J / 2 + 1; k < J; ++k) x[k] = (S - a[J - k]) * invJ;
+    } else {
+      x[0] = S * invJ;
     }
   }
+}
+
+// The same on one line of a shared buffer with stride st (mode 0 / 1 / 2).
+template <int J>
+__device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base, int st, int mode, bool vec4) {
+  float x[J];
+  // vec4: a stride-1 line of unpadded rows (LS a multiple of 4), which starts
+  // on a 16-byte boundary; read and written as float4
+  const bool vec = (J % 4 == 0) && vec4;
+  if (vec) {
+#pragma unroll
+    for (int i = 0; i < J; i += 4) {
+      const float4 q = *reinterpret_cast<const float4 *>(buf + base + i);
+      x[i] = q.x; x[i + 1] = q.y; x[i + 2] = q.z; x[i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < J; ++i) x[i] = buf[base + i * st];
+  }
+  if (mode == 0) dct_reg<J, 0>(x);
+  else if (mode == 1) dct_reg<J, 1>(x);
+  else dct_reg<J, 2>(x);
   if (vec) {
 #pragma unroll
     for (int i = 0; i < J; i += 4)
@@ -436,6 +452,27 @@ __device__ __forceinline__ void fast_dct_line(float *__restrict__ buf, int base,
   } else {
 #pragma unroll
     for (int i = 0; i < J; ++i) buf[base + i * st] = x[i];
+  }
+}
+
+// Separable DCT (MODE as in dct_reg) of a whole cubic patch of side JC held
+// in registers, C-order entries; axes in order 0 .. D-1.
+template <int D, int JC, int MODE, int A = 0>
+__device__ __forceinline__ void dct_patch(float (&x)[ipow(JC, D)]) {
+  if constexpr (A < D) {
+    constexpr int S = ipow(JC, D - 1 - A);
+    constexpr int P = ipow(JC, D);
+#pragma unroll
+    for (int l = 0; l < P / JC; ++l) {
+      const int base = (l / S) * (S * JC) + (l % S);
+      float t[JC];
+#pragma unroll
+      for (int i = 0; i < JC; ++i) t[i] = x[base + i * S];
+      dct_reg<JC, MODE>(t);
+#pragma unroll
+      for (int i = 0; i < JC; ++i) x[base + i * S] = t[i];
+    }
+    dct_patch<D, JC, MODE, A + 1>(x);
   }
 }
 
@@ -928,6 +965,247 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
 }
 
 // ---------------------------------------------------------------------------
+// group filter with register-resident patches (cubic patches, P <= 64, Haar)
+// ---------------------------------------------------------------------------
+// Group buffers are [member][MS] with MS = P | 1 (odd), entry v in column v:
+// a lane reading one member's row and a lane reading one entry's column both
+// touch 32 distinct banks.  Row phases (lane = member) run the separable
+// patch DCT in registers; column phases (lane = entry) run the Haar along the
+// group axis in registers together with the shrinkage it feeds.
+
+// Column of entry v: y_m = buf[m * MS + v] for m < N.
+template <int N, int MS>
+__device__ __forceinline__ void col_load(float (&y)[N], const float *buf, int v) {
+#pragma unroll
+  for (int m = 0; m < N; ++m) y[m] = buf[m * MS + v];
+}
+template <int N, int MS>
+__device__ __forceinline__ void col_store(float *buf, int v, const float (&y)[N]) {
+#pragma unroll
+  for (int m = 0; m < N; ++m) buf[m * MS + v] = y[m];
+}
+
+// Stage 1, one column: sigma^2 = H^2 s (s = T_patch^2 m_v in bufA, or the
+// Gaussian variance), X = H x, hard threshold with weight terms into bufA,
+// then H^T of the kept coefficients back into bufB.
+template <int N, int MS>
+__device__ __forceinline__ void col_hard_threshold(const DGeom &g, float *bufA, float *bufB, int v, float lam2) {
+  float X[N], S[N];
+  col_load<N, MS>(X, bufB, v);
+  haar_fwd_levels<N, N, false>(X);
+  if (g.poisson) {
+    col_load<N, MS>(S, bufA, v);
+    haar_fwd_levels<N, N, true>(S);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) S[m] = g.var_g;
+  }
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
+    // with count data, are zeroed whatever the rounding)
+    const bool keep = X[m] * X[m] > lam2 * S[m];
+    bufA[m * MS + v] = keep ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
+    X[m] = keep ? X[m] : 0.f;
+  }
+  haar_inv_levels<N, 2>(X);
+  col_store<N, MS>(bufB, v, X);
+}
+
+// Stage 2, one column: sigma^2 as above from the pilot, Gamma = H gamma,
+// Wiener gains G into bufB and weight terms into bufA.
+template <int N, int MS>
+__device__ __forceinline__ void col_wiener_gain(const DGeom &g, float *bufA, float *bufB, int v) {
+  float X[N], S[N];
+  col_load<N, MS>(X, bufB, v);
+  haar_fwd_levels<N, N, false>(X);
+  if (g.poisson) {
+    col_load<N, MS>(S, bufA, v);
+    haar_fwd_levels<N, N, true>(S);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) S[m] = g.var_g;
+  }
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const float s2 = S[m];
+    const float Sx = fmaxf(X[m] * X[m] - g.a_power * s2, 0.f);
+    const float den = Sx + g.s_v * s2;
+    const float G = den > 0.f ? __fdividef(Sx, den) : 0.f;
+    bufB[m * MS + v] = G;
+    bufA[m * MS + v] = g.wmodel == 0 ? G * G
+                                     : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * Sx);
+  }
+}
+
+// Stage 2, one column: Y = H y, C = G Y, H^T C back into bufA.
+template <int N, int MS>
+__device__ __forceinline__ void col_wiener_apply(float *bufA, const float *bufB, int v) {
+  float Y[N];
+  col_load<N, MS>(Y, bufA, v);
+  haar_fwd_levels<N, N, false>(Y);
+#pragma unroll
+  for (int m = 0; m < N; ++m) Y[m] *= bufB[m * MS + v];
+  haar_inv_levels<N, 2>(Y);
+  col_store<N, MS>(bufA, v, Y);
+}
+
+// Runs the column operation OP(N) for the lane's entries, N = n.
+#define BMND_COLUMNS(OP)                                             \
+  for (int v = lane; v < P; v += 32) {                               \
+    switch (n) {                                                     \
+      case 1: OP(1); break;                                          \
+      case 2: OP(2); break;                                          \
+      case 4: OP(4); break;                                          \
+      case 8: OP(8); break;                                          \
+      case 16: OP(16); break;                                        \
+      default: OP(32); break;                                        \
+    }                                                                \
+  }
+
+template <int D, int JC>
+__device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
+                                            const int *__restrict__ vreg, const float *__restrict__ omega,
+                                            const float *__restrict__ Sg, const float *__restrict__ Sy,
+                                            const float *__restrict__ Se, float *__restrict__ bufA,
+                                            float *__restrict__ bufB, float *__restrict__ wts,
+                                            float *__restrict__ rr_s, const float *__restrict__ gy,
+                                            const float *__restrict__ ge, const int64_t *__restrict__ gb,
+                                            const int64_t *__restrict__ vgl, float *alpha_out) {
+  constexpr int P = ipow(JC, D);
+  constexpr int MS = CubeShape<D, JC>::MS;
+  static_assert(MS == (P | 1), "register filter layout");
+  const bool stage2 = g.stage == 2;
+  // ---- entries of a shared region into rows of buf (lanes over entries)
+  auto gather = [&](float *buf, const float *src) {
+    if constexpr (P % 32 == 0) {
+      constexpr int KV = P / 32;
+      int vr[KV];
+#pragma unroll
+      for (int k = 0; k < KV; ++k) vr[k] = vreg[lane + 32 * k];
+      for (int m = 0; m < n; ++m) {
+        const float *s0 = src + mem[m];
+#pragma unroll
+        for (int k = 0; k < KV; ++k) buf[m * MS + lane + 32 * k] = s0[vr[k]];
+      }
+    } else {
+      const int v = lane % P, vr = vreg[v];
+      for (int m = lane / P; m < n; m += 32 / P) buf[m * MS + v] = src[mem[m] + vr];
+    }
+  };
+  // ---- row phases: one member per lane, the patch DCT in registers
+  auto row_dct = [&](float *buf, auto mode) {
+    if (lane < n) {
+      float x[P];
+      float *row = buf + lane * MS;
+#pragma unroll
+      for (int i = 0; i < P; ++i) x[i] = row[i];
+      dct_patch<D, JC, decltype(mode)::value>(x);
+#pragma unroll
+      for (int i = 0; i < P; ++i) row[i] = x[i];
+    }
+  };
+  using F = std::integral_constant<int, 0>;
+  using I = std::integral_constant<int, 1>;
+  // guide group into bufB; for Poisson data also T_patch^2 m_v into bufA
+  gather(bufB, Sg);
+  __syncwarp();
+  if (g.poisson && lane < n) {
+    float x[P];
+    const float *row = bufB + lane * MS;
+#pragma unroll
+    for (int i = 0; i < P; ++i) x[i] = g.s_p * fmaxf(row[i], 0.f);
+    dct_patch<D, JC, 2>(x);
+    float *out = bufA + lane * MS;
+#pragma unroll
+    for (int i = 0; i < P; ++i) out[i] = x[i];
+  }
+  row_dct(bufB, F{});
+  __syncwarp();
+  if (!stage2) {
+    const float lam = g.lambda * 1.0001f, lam2 = lam * lam;
+#define BMND_OP(NN) col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2)
+    BMND_COLUMNS(BMND_OP)
+#undef BMND_OP
+  } else {
+#define BMND_OP(NN) col_wiener_gain<NN, MS>(g, bufA, bufB, v)
+    BMND_COLUMNS(BMND_OP)
+#undef BMND_OP
+  }
+  __syncwarp();
+  // ---- r_l = sum_q (term) for every group-axis plane l; weights
+  if (lane < n) {
+    float r = 0.f;
+    const float *row = bufA + lane * MS;
+#pragma unroll
+    for (int v = 0; v < P; ++v) r += row[v];
+    rr_s[lane] = r;
+  }
+  __syncwarp();
+  if (lane < n) {
+    float R = 0.f;
+    if (g.wscope == 1) {
+      for (int l = 0; l < n; ++l) R += rr_s[l];
+    } else {
+      // patch scope R_j = sum_l |V_jl|^2 r_l for the Haar basis ordered
+      // [scaling, coarsest detail, ..., finest details]
+      R = rr_s[0] / (float)n;
+      for (int bb = n; bb >= 2; bb >>= 1) R += rr_s[n / bb + lane / bb] / (float)bb;
+    }
+    wts[lane] = R > 0.f ? 1.f / R : 1.f;
+  }
+  __syncwarp();
+  float *syn;
+  if (!stage2) {
+    row_dct(bufB, I{});
+    syn = bufB;
+  } else {
+    // Wiener: the observation group, transformed, scaled by G, inverted
+    if (D >= 3 && g.lean)
+      gather_global(gy, nullptr, gb, vgl, n, P, lane, [&](int m, int v, float x, float) { bufA[m * MS + v] = x; });
+    else
+      gather(bufA, Sy);
+    __syncwarp();
+    row_dct(bufA, F{});
+    __syncwarp();
+#define BMND_OP(NN) col_wiener_apply<NN, MS>(bufA, bufB, v)
+    BMND_COLUMNS(BMND_OP)
+#undef BMND_OP
+    __syncwarp();
+    row_dct(bufA, I{});
+    syn = bufA;
+  }
+  __syncwarp();
+  float alpha = 0.f;
+  if (mc2) {
+    // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
+    // alpha = d_g / zeta^T 1 to every synthesized entry
+    float dg = 0.f, z1 = 0.f;
+    if (D >= 3 && g.lean) {
+      gather_global(ge, gy, gb, vgl, n, P, lane, [&](int m, int v, float et, float yv) {
+        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+        dg = fmaf(z, yv - syn[m * MS + v], dg);
+        z1 += z;
+      });
+    } else {
+      for (int e = lane; e < n * P; e += 32) {
+        const int m = e / P, v = e - m * P;
+        const int u = mem[m] + vreg[v];
+        const float et = Se[u];
+        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+        dg = fmaf(z, Sy[u] - syn[m * MS + v], dg);
+        z1 += z;
+      }
+    }
+    dg = warp_sum(dg);
+    z1 = warp_sum(z1);
+    alpha = z1 > 0.f ? dg / z1 : 0.f;
+  }
+  *alpha_out = alpha;
+  return stage2 ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
 // the stage kernel
 // ---------------------------------------------------------------------------
 
@@ -1181,8 +1459,13 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             }
             __syncwarp();
           }
-          const int which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
-                                            rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
+          int which;
+          if constexpr (SH::rf)
+            which = filter_group_rf<D, JL>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
+                                           sj->y, sj->eta, gb, L.vgl, &alpha);
+          else
+            which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
+                                        rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
           syn = which ? bufA : bufB;
         }
       }
