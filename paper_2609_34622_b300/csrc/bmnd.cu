@@ -23,6 +23,7 @@ void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off,
                    int64_t *groups, int32_t *counts, int64_t cap, cudaStream_t st);
 void launch_sched(const SGeom &s, unsigned char *flags, const DJob *jobs, int ntiles, int *ref_local,
                   int *ref_count, cudaStream_t st);
+void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t st);
 cudaError_t set_stage_smem(stage_fn f, int bytes);
 }  // namespace bmnd
 
@@ -163,7 +164,13 @@ struct Plan {
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
   size_t o_flags, o_refs, o_rcount, o_partial, o_pilot, o_eta, o_groups, o_gcount, total;
+  // optional synthesis cache of the first mass-conservation sweep
+  bool cache;
+  int smem_cached;       // dynamic shared bytes of the second sweep from the cache
+  int64_t cache_refs;
+  size_t o_refbase, o_pcache, o_wcache;
 };
+
 
 // Patch side of the specialized stage kernels for a shape: they take cubic
 // patches (side jL on every axis) of the sizes instantiated with the kernels,
@@ -177,8 +184,11 @@ int cube_side(int D, const int *j, int gtrans) {
   return 0;
 }
 
-int stage_smem(const DGeom &g, int M, int nreg) {
-  if (g.lean) nreg = 1;  // only the matching guide is staged
+// Dynamic shared memory of a stage launch; cached: second mass-conservation
+// sweep from the synthesis cache (y and eta staged, one group buffer).
+int stage_smem(const DGeom &g, int M, int nreg, bool cached = false) {
+  if (cached) nreg = 2;
+  else if (g.lean) nreg = 1;  // only the matching guide is staged
   size_t b = al16(sizeof(DJob));
   b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4 + KMAXD * 4 + (g.fp ? (size_t)g.P * 4 : 0) +
            (size_t)g.fp * 4);
@@ -188,8 +198,34 @@ int stage_smem(const DGeom &g, int M, int nreg) {
   b = al16(b + mats);
   b = al16(b + (size_t)nreg * (g.region + RPAD) * 4);
   b = al16(b + (size_t)g.region * 8);
-  b += (size_t)NW * warp_bytes(M, g.MS, g.fp, g.lean);
+  b += (size_t)NW * (cached ? warp_bytes(M, g.MS, g.fp, 0, 1) : warp_bytes(M, g.MS, g.fp, g.lean));
   return (int)b;
+}
+
+// Adds the synthesis cache of the first mass-conservation sweep to a plan's
+// scratch: per reference (at most one per patch origin, and at most
+// passes x slots of the schedule) the M x P synthesized entries and M
+// weights, plus the per-tile reference offsets.  The second sweep then
+// re-aggregates without filtering again.
+void add_mc_cache(Plan &pl) {
+  if (pl.cache) return;
+  pl.cache_refs = std::min<int64_t>(pl.nflags, (int64_t)pl.s.passes * pl.s.nslots);
+  pl.o_refbase = pl.total;
+  size_t o = pl.total;
+  o = al256(o + (size_t)pl.g.ntiles * 4);
+  pl.o_pcache = o;
+  o = al256(o + (size_t)pl.cache_refs * pl.Mmax * pl.g.P * 4);
+  pl.o_wcache = o;
+  o = al256(o + (size_t)pl.cache_refs * pl.Mmax * 4);
+  pl.total = o;
+  pl.cache = true;
+  pl.smem_cached = stage_smem(pl.g, pl.Mmax, 2, true);
+}
+
+void drop_mc_cache(Plan &pl) {
+  if (!pl.cache) return;
+  pl.total = pl.o_refbase;
+  pl.cache = false;
 }
 
 void set_tiles(DGeom &g, const int *C) {
@@ -390,6 +426,9 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.o_groups = o; o = al256(o + (size_t)g.ntiles * g.cap * pl.Mmax * 4);
   pl.o_gcount = o; o = al256(o + (size_t)g.ntiles * g.cap * 4);
   pl.total = o;
+  pl.cache = false;
+  pl.cache_refs = 0;
+  pl.o_refbase = pl.o_pcache = pl.o_wcache = 0;
   return BMND_OK;
 }
 
@@ -514,9 +553,18 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
   int D = plans[0].D;
   for (auto &pl : plans)
     if (pl.D != D) return fail(ctx, BMND_EUNSUPPORTED, "batched jobs must share the number of non-singleton axes");
+  // synthesis caches for mass-conserving jobs, unless they exceed the
+  // context's scratch budget
+  for (int i = 0; i < nj; ++i)
+    if (io[i].mass_conserve) add_mc_cache(plans[i]);
   std::vector<size_t> base(nj);
   size_t need = 0;
-  for (int i = 0; i < nj; ++i) { base[i] = need; need = al256(need + plans[i].total); }
+  for (int pass = 0; pass < 2; ++pass) {
+    need = 0;
+    for (int i = 0; i < nj; ++i) { base[i] = need; need = al256(need + plans[i].total); }
+    if (!ctx->budget || need <= ctx->budget) break;
+    for (auto &pl : plans) drop_mc_cache(pl);
+  }
   bmnd_status rc = ensure_arena(ctx, need, st);
   if (rc != BMND_OK) return rc;
   char *A = (char *)ctx->arena;
@@ -524,7 +572,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
   std::vector<DJob> h(2 * nj);
   int tiles = 0;
   int64_t vox = 0;
-  int smax[2] = {0, 0};
+  int smax[2] = {0, 0}, smax2[2] = {0, 0};
   bool any_mc[2] = {false, false};
   for (int i = 0; i < nj; ++i) {
     Plan &pl = plans[i];
@@ -548,10 +596,17 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
       J.ref_count = (const int *)(B + pl.o_rcount);
       J.groups = mc ? (int *)(B + pl.o_groups) : nullptr;
       J.gcount = mc ? (int *)(B + pl.o_gcount) : nullptr;
+      if (mc && pl.cache) {
+        J.pcache = (float *)(B + pl.o_pcache);
+        J.wcache = (float *)(B + pl.o_wcache);
+        J.ref_base = (const int *)(B + pl.o_refbase);
+        J.pcache_refs = pl.cache_refs;
+      }
       J.tile_base = tiles;
       J.vox_base = vox;
       if (mc) any_mc[s - 1] = true;
       smax[s - 1] = std::max(smax[s - 1], mc ? std::max(pl.smem[s - 1], pl.smem[2]) : pl.smem[s - 1]);
+      if (mc) smax2[s - 1] = std::max(smax2[s - 1], pl.cache ? pl.smem_cached : std::max(pl.smem[s - 1], pl.smem[2]));
     }
     tiles += pl.g.ntiles;
     vox += pl.g.N;
@@ -566,6 +621,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     ProfScope ps(ctx, BMND_KERNEL_SCHEDULE, st);
     launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), ctx->djobs + (first_stage == 2 ? nj : 0) + i,
                  pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
+    if (pl.cache) launch_ref_base((const int *)(B + pl.o_rcount), pl.g.ntiles, (int *)(B + pl.o_refbase), st);
   }
   CU(cudaGetLastError());
   int kjL = kernel_jl(plans[0]), kkb = pick_kb(plans[0]);
@@ -587,7 +643,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     if (any_mc[s - 1]) {
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
-        rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 2, smax[s - 1], st);
+        rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 2, smax2[s - 1], st);
       }
       if (rc != BMND_OK) return rc;
       {
@@ -1207,6 +1263,12 @@ DJob srv_stage_job(const SrvJob *j, int stage, const bmnd_params &pr) {
   J.ref_count = (const int *)(B + pl.o_rcount);
   J.groups = m ? (int *)(B + pl.o_groups) : nullptr;
   J.gcount = m ? (int *)(B + pl.o_gcount) : nullptr;
+  if (m && pl.cache) {
+    J.pcache = (float *)(B + pl.o_pcache);
+    J.wcache = (float *)(B + pl.o_wcache);
+    J.ref_base = (const int *)(B + pl.o_refbase);
+    J.pcache_refs = pl.cache_refs;
+  }
   return J;
 }
 
@@ -1227,7 +1289,7 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
   for (auto &kv : classes) {
     std::vector<SrvJob *> &cj = kv.second;
     const int D = kv.first.first, jL = kv.first.second / 16, kb = kv.first.second % 16;
-    int tiles = 0, smax = 0;
+    int tiles = 0, smax = 0, smax2 = 0;
     int64_t vox = 0;
     bool any_mc = false;
     for (size_t i = 0; i < cj.size(); ++i) {
@@ -1241,6 +1303,9 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
       const bool m = J.groups != nullptr;
       any_mc = any_mc || m;
       smax = std::max(smax, m ? std::max(j->plan.smem[stage - 1], j->plan.smem[2]) : j->plan.smem[stage - 1]);
+      if (m)
+        smax2 = std::max(smax2, j->plan.cache ? j->plan.smem_cached
+                                              : std::max(j->plan.smem[stage - 1], j->plan.smem[2]));
       S->htab[tab_off + i] = J;
     }
     DJob *dj = S->dtab + tab_off;
@@ -1251,7 +1316,7 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
     if (rc != BMND_OK) return rc;
     launch_reduce(D, dj, (int)cj.size(), vox, any_mc ? 1 : 0, rgrid, S->st);
     if (any_mc) {
-      rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 2, smax, S->st);
+      rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 2, smax2, S->st);
       if (rc != BMND_OK) return rc;
       launch_reduce(D, dj, (int)cj.size(), vox, 0, rgrid, S->st);
     }
@@ -1283,6 +1348,8 @@ bmnd_status srv_admit(bmnd_server *S, SrvJob *j) {
   if (e != cudaSuccess) return srv_fail(S, "admission copy", e);
   launch_sched(pl.s, j->scratch + pl.o_flags, j->djob, pl.g.ntiles, (int *)(j->scratch + pl.o_refs),
                (int *)(j->scratch + pl.o_rcount), S->st);
+  if (pl.cache)
+    launch_ref_base((const int *)(j->scratch + pl.o_rcount), pl.g.ntiles, (int *)(j->scratch + pl.o_refbase), S->st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return srv_fail(S, "schedule launch", e);
   return BMND_OK;
@@ -1422,6 +1489,12 @@ bmnd_status bmnd_server_submit(bmnd_server *S, const bmnd_job *job, int64_t *tic
       rc = make_plan(S->ctx, job->ndim, job->shape, job->patch, job->step, job->search, job->group_size, job->stages,
                      job->mass_conserve, pr, j->plan);
     if (rc == BMND_OK) {
+      // the synthesis cache of mass-conserving jobs, when it takes at most a
+      // quarter of the server's budget
+      if (job->mass_conserve) {
+        add_mc_cache(j->plan);
+        if (al256(srv_job_bytes(j->plan)) > S->budget / 4) drop_mc_cache(j->plan);
+      }
       j->bytes = al256(srv_job_bytes(j->plan));
       if (j->bytes > S->budget)
         rc = fail(S->ctx, BMND_ENOMEM, "job needs %zu bytes, the server budget is %zu", j->bytes, S->budget);

@@ -797,6 +797,42 @@ __device__ __forceinline__ void gather_global(const float *__restrict__ a, const
   }
 }
 
+// Correction of one group for the second mass-conservation sweep (Def.
+// "Aggregation-aware constant-synthesis correction"): zeta = w omega / eta,
+// d_g = zeta^T (y_g - p_g), and the sweep adds alpha = d_g / zeta^T 1 to
+// every synthesized entry.  p_g: syn[m * MS + vbuf[v]] (vbuf null: column v).
+// Entries are visited lane + 32 k in (member, entry) order on every path.
+template <int D, int PC>
+__device__ __forceinline__ float mc_alpha(const DGeom &g, int n, int lane, const int *__restrict__ mem,
+                                          const int *__restrict__ vreg, const int *__restrict__ vbuf,
+                                          const float *__restrict__ omega, const float *__restrict__ wts,
+                                          const float *__restrict__ syn, int MS, const float *__restrict__ Sy,
+                                          const float *__restrict__ Se, const float *__restrict__ gy,
+                                          const float *__restrict__ ge, const int64_t *__restrict__ gb,
+                                          const int64_t *__restrict__ vgl, bool lean) {
+  const int P = PC ? PC : g.P;
+  float dg = 0.f, z1 = 0.f;
+  auto term = [&](int m, int v, float et, float yv) {
+    const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
+    dg = fmaf(z, yv - syn[m * MS + (vbuf ? vbuf[v] : v)], dg);
+    z1 += z;
+  };
+  if (D >= 3 && lean) {
+    gather_global(ge, gy, gb, vgl, n, P, lane, term);
+  } else {
+    int m = lane / P, v = lane - (lane / P) * P;
+    while (m < n) {
+      const int u = mem[m] + vreg[v];
+      term(m, v, Se[u], Sy[u]);
+      v += 32;
+      while (v >= P) { v -= P; ++m; }
+    }
+  }
+  dg = warp_sum(dg);
+  z1 = warp_sum(z1);
+  return z1 > 0.f ? dg / z1 : 0.f;
+}
+
 // Filters the group whose member origins (region offsets) are in mem[0..n).
 // Stage 1: hard thresholding of T y_g against sigma_k from the variance map;
 // stage 2: Wiener shrinkage of T y_g with gains from the pilot group.  Leaves
@@ -937,29 +973,8 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
     group_xform<D, JC>(tb, g, n, tmode, lane, vbuf, mats, moff, tab);
   }
   float alpha = 0.f;
-  if (mc2) {
-    // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
-    // alpha = d_g / zeta^T 1 to every synthesized entry
-    float dg = 0.f, z1 = 0.f;
-    if (D >= 3 && g.lean) {
-      gather_global(ge, gy, gb, vgl, n, P, lane, [&](int m, int v, float et, float yv) {
-        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-        dg = fmaf(z, yv - syn[m * MS + vbuf[v]], dg);
-        z1 += z;
-      });
-    } else {
-      BMND_FOR_ENTRIES({
-        const int u = mem[m] + vreg[v];
-        const float et = Se[u];
-        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-        dg = fmaf(z, Sy[u] - syn[m * MS + vbuf[v]], dg);
-        z1 += z;
-      });
-    }
-    dg = warp_sum(dg);
-    z1 = warp_sum(z1);
-    alpha = z1 > 0.f ? dg / z1 : 0.f;
-  }
+  if (mc2)
+    alpha = mc_alpha<D, 0>(g, n, lane, mem, vreg, vbuf, omega, wts, syn, MS, Sy, Se, gy, ge, gb, vgl, g.lean);
   *alpha_out = alpha;
   return stage2 ? 1 : 0;
 }
@@ -1177,30 +1192,8 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   }
   __syncwarp();
   float alpha = 0.f;
-  if (mc2) {
-    // zeta = w omega / eta; d_g = zeta^T (y_g - p_g); the correction adds
-    // alpha = d_g / zeta^T 1 to every synthesized entry
-    float dg = 0.f, z1 = 0.f;
-    if (D >= 3 && g.lean) {
-      gather_global(ge, gy, gb, vgl, n, P, lane, [&](int m, int v, float et, float yv) {
-        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-        dg = fmaf(z, yv - syn[m * MS + v], dg);
-        z1 += z;
-      });
-    } else {
-      for (int e = lane; e < n * P; e += 32) {
-        const int m = e / P, v = e - m * P;
-        const int u = mem[m] + vreg[v];
-        const float et = Se[u];
-        const float z = et > 0.f ? wts[m] * omega[v] / et : 0.f;
-        dg = fmaf(z, Sy[u] - syn[m * MS + v], dg);
-        z1 += z;
-      }
-    }
-    dg = warp_sum(dg);
-    z1 = warp_sum(z1);
-    alpha = z1 > 0.f ? dg / z1 : 0.f;
-  }
+  if (mc2)
+    alpha = mc_alpha<D, P>(g, n, lane, mem, vreg, nullptr, omega, wts, syn, MS, Sy, Se, gy, ge, gb, vgl, g.lean);
   *alpha_out = alpha;
   return stage2 ? 1 : 0;
 }
@@ -1223,7 +1216,10 @@ __device__ __forceinline__ unsigned char *al16p(unsigned char *p) {
   return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
 }
 
-__device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stage2, bool mc2) {
+// cached: second mass-conservation sweep from the synthesis cache, which
+// stages y and eta (never read from global memory) and no guide, and needs
+// one group buffer per warp.
+__device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stage2, bool mc2, bool cached) {
   SmemLayout s;
   unsigned char *p = smem + ((sizeof(DJob) + 15) & ~(size_t)15);
   s.vreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.P;
@@ -1242,13 +1238,18 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
   const int RS = g.region + RPAD;
   s.Sg = reinterpret_cast<float *>(p); p += sizeof(float) * RS;
   s.Sy = s.Sg;
-  if (stage2 && !g.lean) { s.Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
   s.Se = nullptr;
-  if (mc2 && !g.lean) { s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  if (cached) {
+    // region 0 holds y, region 1 eta
+    s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS;
+  } else {
+    if (stage2 && !g.lean) { s.Sy = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+    if (mc2 && !g.lean) { s.Se = reinterpret_cast<float *>(p); p += sizeof(float) * RS; }
+  }
   p = al16p(p);
   s.acc = reinterpret_cast<float2 *>(p); p += sizeof(float2) * g.region;
   s.warps = al16p(p);
-  s.wbytes = warp_bytes(g.M, g.MS, g.fp, g.lean);
+  s.wbytes = cached ? warp_bytes(g.M, g.MS, g.fp, 0, 1) : warp_bytes(g.M, g.MS, g.fp, g.lean);
   return s;
 }
 
@@ -1288,7 +1289,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
       for (int i = threadIdx.x; i < (int)(sizeof(DJob) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
       const DGeom &g = sj->g;
-      L = smem_layout(smem, g, g.stage == 2, mode == 2);
+      L = smem_layout(smem, g, g.stage == 2, mode == 2, mode == 2 && sj->pcache != nullptr);
       for (int v = threadIdx.x; v < g.P; v += blockDim.x) {
         int rem = v, ro = 0;
         float w = 1.f;
@@ -1360,16 +1361,22 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     const int tile = gt - sj->tile_base;
     const bool stage2 = g.stage == 2;
     const bool mc2 = mode == 2;
+    // second sweep from the synthesis cache: y and eta staged, no filtering
+    const bool cmode = mc2 && sj->pcache != nullptr;
+    const bool leanx = g.lean && !cmode;  // y / eta gathered from global memory
     using SH = CubeShape<D, JL>;
     const int P = SH::fixed ? SH::P : g.P;
     const int MS = SH::fixed ? SH::MS : g.MS;
+    // float4 loads per lane of one cached group (compile-time shapes)
+    constexpr int CQ = (SH::fixed && SH::P % 4 == 0) ? SH::P * MMAX / 128 : 0;
+    const int tile_ref0 = cmode ? sj->ref_base[tile] : 0;
     unsigned char *wp = L.warps + (size_t)warp * L.wbytes;
     int *mem = reinterpret_cast<int *>(wp);
     float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
     float *rr_s = reinterpret_cast<float *>(wp + 2 * MMAX * 4);
     int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
     float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
-    float *bufB = bufA + g.M * MS;
+    float *bufB = cmode ? bufA : bufA + g.M * MS;
     float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * MS);
     int64_t *gb = reinterpret_cast<int64_t *>(fpb + g.fp);
     float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
@@ -1404,15 +1411,24 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           gi += x * g.st[d];
         }
         if (in) {
-          vg = __ldg(gsrc + gi);
-          if (stage2 && !g.lean) vy = __ldg(ysrc + gi);
-          if (mc2 && !g.lean) ve = __ldg(esrc + gi);
+          if (cmode) {
+            vg = __ldg(ysrc + gi);
+            ve = __ldg(esrc + gi);
+          } else {
+            vg = __ldg(gsrc + gi);
+            if (stage2 && !g.lean) vy = __ldg(ysrc + gi);
+            if (mc2 && !g.lean) ve = __ldg(esrc + gi);
+          }
         }
         acc[e] = make_float2(0.f, 0.f);
       }
-      Sg[e] = vg;
-      if (stage2 && !g.lean) Sy[e] = vy;
-      if (mc2 && !g.lean) Se[e] = ve;
+      Sg[e] = vg;  // y in the cached sweep
+      if (cmode) {
+        Se[e] = ve;
+      } else {
+        if (stage2 && !g.lean) Sy[e] = vy;
+        if (mc2 && !g.lean) Se[e] = ve;
+      }
     }
     __syncthreads();
 
@@ -1439,13 +1455,48 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
             if (lane == 0) sj->gcount[tslot + ri] = n;
           }
+        } else if (CQ > 0 && cmode) {
+          // second sweep from the cache: the group-table entry, the cached
+          // synthesis (float4) and the weights are requested together
+          const int64_t slot = tslot + ri, cr = (int64_t)tile_ref0 + ri;
+          const bool ok = cr < sj->pcache_refs;
+          const int gm = lane < g.M ? sj->groups[slot * g.M + lane] : 0;
+          const int gc = sj->gcount[slot];
+          const float wv = (ok && lane < g.M) ? sj->wcache[cr * g.M + lane] : 0.f;
+          const float4 *pc4 = reinterpret_cast<const float4 *>(sj->pcache + (ok ? cr : 0) * g.M * P);
+          const int nq = ok ? g.M * P / 4 : 0;
+          float4 q[CQ > 0 ? CQ : 1];
+#pragma unroll
+          for (int k = 0; k < CQ; ++k) {
+            const int i = lane + 32 * k;
+            q[k] = i < nq ? __ldg(pc4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          n = ok ? gc : 0;
+          if (lane < n) {
+            mem[lane] = gm;
+            wts[lane] = wv;
+          }
+#pragma unroll
+          for (int k = 0; k < CQ; ++k) {
+            const int e = 4 * (lane + 32 * k);
+            if (e < n * P) {
+              // P is a multiple of 4: the four entries belong to one member
+              const int m = e / P, v = e - m * P;
+              float *d = bufA + m * MS;
+              d[vbuf[v]] = q[k].x;
+              d[vbuf[v + 1]] = q[k].y;
+              d[vbuf[v + 2]] = q[k].z;
+              d[vbuf[v + 3]] = q[k].w;
+            }
+          }
+          __syncwarp();
         } else {
           n = sj->gcount[tslot + ri];
           for (int m = lane; m < n; m += 32) mem[m] = sj->groups[(tslot + ri) * g.M + m];
           __syncwarp();
         }
         if (mode != 1) {
-          if (D >= 3 && g.lean) {
+          if (D >= 3 && leanx) {
             // global origin of every member
             if (lane < n) {
               int rem = mem[lane];
@@ -1459,14 +1510,58 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             }
             __syncwarp();
           }
-          int which;
-          if constexpr (SH::rf)
-            which = filter_group_rf<D, JL>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
-                                           sj->y, sj->eta, gb, L.vgl, &alpha);
-          else
-            which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
-                                        rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
-          syn = which ? bufA : bufB;
+          // reference slot in the synthesis cache of the first sweep (the
+          // cache holds a slot for every possible reference)
+          const int64_t cr = sj->pcache ? (int64_t)sj->ref_base[tile] + ri : -1;
+          const bool cached = cr >= 0 && cr < sj->pcache_refs;
+          if (cmode) {
+            // second sweep: the first sweep's synthesis and weights, then
+            // only the correction alpha
+            if (!cached) n = 0;
+            const float *pc = sj->pcache + (cached ? cr : 0) * g.M * P;
+            const int tot = CQ > 0 ? 0 : n * P;  // CQ > 0: loaded with the group
+            for (int e0 = 0; e0 < tot; e0 += 32 * 8) {
+              float t[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int e = e0 + 32 * k + lane;
+                t[k] = e < tot ? __ldg(pc + e) : 0.f;
+              }
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int e = e0 + 32 * k + lane;
+                if (e < tot) {
+                  const int m = e / P, v = e - m * P;
+                  bufA[m * MS + vbuf[v]] = t[k];
+                }
+              }
+            }
+            if (CQ == 0 && lane < n) wts[lane] = sj->wcache[cr * g.M + lane];
+            __syncwarp();
+            syn = bufA;
+            alpha = mc_alpha<D, SH::P>(g, n, lane, mem, vreg, vbuf, omega, wts, syn, MS, Sg, Se, sj->y, sj->eta,
+                                       gb, L.vgl, false);
+          } else {
+            int which;
+            if constexpr (SH::rf)
+              which = filter_group_rf<D, JL>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
+                                             sj->y, sj->eta, gb, L.vgl, &alpha);
+            else
+              which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
+                                          rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
+            syn = which ? bufA : bufB;
+            if (!mc2 && cached && sj->groups) {
+              // first sweep of a mass-conserving stage: keep the synthesis
+              float *pc = sj->pcache + cr * g.M * P;
+              int m = lane / P, v = lane - (lane / P) * P;
+              for (int e = lane; e < n * P; e += 32) {
+                pc[e] = syn[m * MS + vbuf[v]];
+                v += 32;
+                while (v >= P) { v -= P; ++m; }
+              }
+              if (lane < n) sj->wcache[cr * g.M + lane] = wts[lane];
+            }
+          }
         }
       }
       if (mode == 1) continue;
@@ -1680,6 +1775,30 @@ __global__ void k_export_groups(const DJob *__restrict__ jobs, const int64_t *__
   }
 }
 
+// Exclusive prefix sum of the per-tile reference counts (one CTA of 1024
+// threads, contiguous chunks per thread): ref_base[t] = sum_{t' < t} count[t'].
+__global__ void __launch_bounds__(1024) k_ref_base(const int *__restrict__ count, int ntiles, int *ref_base) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const int per = (ntiles + 1023) / 1024;
+  const int lo = min(ntiles, t * per), hi = min(ntiles, lo + per);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += count[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int add = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  int run = t ? part[t - 1] : 0;
+  for (int i = lo; i < hi; ++i) {
+    ref_base[i] = run;
+    run += count[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // explicit instantiations and launch helpers
 // ---------------------------------------------------------------------------
@@ -1712,6 +1831,10 @@ stage_fn select_stage_kernel(int D, int jL, int kb, int minb) {
     case 6: return stage_ptr<6, 0, 4>(minb);
   }
   return nullptr;
+}
+
+void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t st) {
+  k_ref_base<<<1, 1024, 0, st>>>(count, ntiles, ref_base);
 }
 
 void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,

@@ -39,11 +39,13 @@ constexpr int GEN_TOTAL = 11440;
 cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
 
 // Bytes of one warp's shared block: member list, weights, plane sums and two
-// level lists (5 x MMAX words), two group buffers of M x MS floats, the
-// private footprint (fp float2) and, when y and eta are read from global
-// memory (lean), the members' global origins (MMAX int64), rounded up to 16.
-__host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean) {
-  return (5 * MMAX * 4 + 2 * M * MS * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
+// spare lists (5 x MMAX words), nbuf group buffers of M x MS floats (two for
+// filtering, one for a second mass-conservation sweep from the synthesis
+// cache), the private footprint (fp float2) and, when y and eta are read
+// from global memory (lean), the members' global origins (MMAX int64),
+// rounded up to 16.
+__host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean, int nbuf = 2) {
+  return (5 * MMAX * 4 + nbuf * M * MS * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
 }
 
 // Floats reserved in shared memory for the three J x J matrices of one patch
@@ -100,6 +102,13 @@ struct DJob {
   int tile_base;       // first tile of this job in a batched grid
   int pad0;
   int64_t vox_base;    // first location of this job in a batched reduce
+  // synthesis cache of the first mass-conservation sweep (or null): for the
+  // reference r = ref_base[tile] + slot, pcache[(r M + m) P + v] holds entry
+  // v of synthesized member m and wcache[r M + m] its weight; r < pcache_refs
+  float *pcache;
+  float *wcache;
+  const int *ref_base;
+  int64_t pcache_refs;
 };
 
 // Schedule geometry on the full (unsqueezed) shape.
