@@ -37,7 +37,7 @@ SMS = 148
 FP32_LANES = 128
 
 
-def workload(name: str, item: int):
+def workload(name: str, item: int, edge: int = 128):
     if name == "c1":
         j = synth.config1(item)
         return [j], "2-D 64x64 discs/rectangles, Poisson peak 10, patch 8x8, step 3, search 19x19, groups 16/32"
@@ -50,9 +50,9 @@ def workload(name: str, item: int):
         return jobs, ("2-D batch: 16 images 512x512 Poisson (peaks 1,2,5,10,30) + the same 16 with Gaussian "
                       "sigma 25/255, patch 8x8, step 3, search 39x39, groups 16/32, one batched call")
     if name == "c4":
-        j = synth.config4(item)
-        return [j], ("3-D 128^3 ellipsoid phantom, Poisson 0.5-5 counts, patch 4x4x4, step 2, search 11^3, "
-                     "groups 16/32, mass conservation in both stages")
+        j = synth.config4(item, n=edge)
+        return [j], ("3-D %d^3 ellipsoid phantom, Poisson 0.5-5 counts, patch 4x4x4, step 2, search 11^3, "
+                     "groups 16/32, mass conservation in both stages" % edge)
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -280,6 +280,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--requests", type=int, default=512, help="serving mix size (c5)")
     ap.add_argument("--budget-gb", type=int, default=40, help="server memory budget (c5)")
+    ap.add_argument("--edge", type=int, default=128, help="volume edge of the 3-D workload (c4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -292,7 +293,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        jobs, desc = workload(args.workload, 0)
+        jobs, desc = workload(args.workload, 0, args.edge)
         sample, sdesc = oracle_sample(args.workload, jobs)
         vox = sum(j.y.size for j in sample)
         for _ in range(args.warmup):
@@ -333,7 +334,7 @@ def main():
             run_c5(args, local)
         return
 
-    jobs, desc = workload(args.workload, rank)
+    jobs, desc = workload(args.workload, rank, args.edge)
     ctx = bm.Context(local)
     stream = torch.cuda.current_stream()
     ys = [torch.from_numpy(j.y).to(dev) for j in jobs]
