@@ -16,7 +16,7 @@
 
 namespace bmnd {
 typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
-stage_fn select_stage_kernel(int D, int jL, int kb, int minb);
+stage_fn select_stage_kernel(int D, int jL, int kb, int minb, int stage);
 void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,
                    cudaStream_t st);
 void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off, int64_t *origins,
@@ -484,12 +484,13 @@ bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
 }
 
 // Launch the persistent stage kernel: one CTA per resident slot, tiles handed
-// out by an atomic counter that is cleared first.
-bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, const DJob *dj, int nj, int tiles, int mode,
-                         int smem, cudaStream_t st) {
+// out by an atomic counter that is cleared first.  Every job of the launch
+// runs the given stage (1 or 2).
+bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, int stage, const DJob *dj, int nj, int tiles,
+                         int mode, int smem, cudaStream_t st) {
   // two CTAs per SM when their shared memory fits, else the full register file
   const int minb = 2 * (smem + 1024) <= 233472 ? 2 : 1;
-  stage_fn f = select_stage_kernel(D, jL, kb, minb);
+  stage_fn f = select_stage_kernel(D, jL, kb, minb, stage);
   CU(set_stage_smem(f, smem));
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)f, NW * 32, smem));
@@ -632,7 +633,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     const DJob *dj = ctx->djobs + (s - 1) * nj;
     {
       ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
-      rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 0, smax[s - 1], st);
+      rc = launch_stage(ctx, D, kjL, kkb, s, dj, nj, tiles, 0, smax[s - 1], st);
     }
     if (rc != BMND_OK) return rc;
     {
@@ -643,7 +644,7 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
     if (any_mc[s - 1]) {
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
-        rc = launch_stage(ctx, D, kjL, kkb, dj, nj, tiles, 2, smax2[s - 1], st);
+        rc = launch_stage(ctx, D, kjL, kkb, s, dj, nj, tiles, 2, smax2[s - 1], st);
       }
       if (rc != BMND_OK) return rc;
       {
@@ -886,7 +887,7 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   CU(cudaGetLastError());
   if (do_match) {
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
-    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), stage == 2 ? 2 : 1, ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
     if (rc != BMND_OK) return rc;
   }
   std::vector<int> cnt(pl.g.ntiles);
@@ -1091,12 +1092,12 @@ bmnd_status noalloc_run(bmnd_ctx *ctx, NoallocDevice *dev, const float *y, int n
   const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = 1; s <= stages; ++s) {
     const DJob *dj = ctx->djobs + (s - 1);
-    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
     if (rc != BMND_OK) return rc;
     launch_reduce(pl.D, dj, 1, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
     CU(cudaGetLastError());
     if (any_mc[s - 1]) {
-      rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
+      rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
       if (rc != BMND_OK) return rc;
       launch_reduce(pl.D, dj, 1, vox, 0, rgrid, st);
       CU(cudaGetLastError());
@@ -1284,11 +1285,15 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
   bmnd_params pr;
   bmnd_default_params(&pr);
   std::map<std::pair<int, int>, std::vector<SrvJob *>> classes;
-  for (SrvJob *j : run) classes[{j->plan.D, kernel_jl(j->plan) * 16 + pick_kb(j->plan)}].push_back(j);
+  for (SrvJob *j : run) {
+    const int stage = j->state == SJ_STAGE1 ? 1 : 2;
+    classes[{j->plan.D, (kernel_jl(j->plan) * 16 + pick_kb(j->plan)) * 4 + stage}].push_back(j);
+  }
   size_t tab_off = 0;
   for (auto &kv : classes) {
     std::vector<SrvJob *> &cj = kv.second;
-    const int D = kv.first.first, jL = kv.first.second / 16, kb = kv.first.second % 16;
+    const int D = kv.first.first, key = kv.first.second / 4, stage_c = kv.first.second % 4;
+    const int jL = key / 16, kb = key % 16;
     int tiles = 0, smax = 0, smax2 = 0;
     int64_t vox = 0;
     bool any_mc = false;
@@ -1312,11 +1317,11 @@ bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
     cudaError_t e = cudaMemcpyAsync(dj, S->htab + tab_off, cj.size() * sizeof(DJob), cudaMemcpyHostToDevice, S->st);
     if (e != cudaSuccess) return srv_fail(S, "job table copy", e);
     const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
-    bmnd_status rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 0, smax, S->st);
+    bmnd_status rc = launch_stage(S->ctx, D, jL, kb, stage_c, dj, (int)cj.size(), tiles, 0, smax, S->st);
     if (rc != BMND_OK) return rc;
     launch_reduce(D, dj, (int)cj.size(), vox, any_mc ? 1 : 0, rgrid, S->st);
     if (any_mc) {
-      rc = launch_stage(S->ctx, D, jL, kb, dj, (int)cj.size(), tiles, 2, smax2, S->st);
+      rc = launch_stage(S->ctx, D, jL, kb, stage_c, dj, (int)cj.size(), tiles, 2, smax2, S->st);
       if (rc != BMND_OK) return rc;
       launch_reduce(D, dj, (int)cj.size(), vox, 0, rgrid, S->st);
     }

@@ -570,7 +570,7 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
 // block matching of one reference (Sec. 4.2 / 4.4, App. A group rules)
 // ---------------------------------------------------------------------------
 
-template <int D, int JL, int KB>
+template <int D, int JL, int KB, int ST>
 __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
                           const int *org, const int *rowoff, int lane, int *mem) {
   int lo[D], W[D];
@@ -643,7 +643,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           float q[KB];
 #pragma unroll
           for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
-          if (g.bias_on) {
+          if (ST != 2 && g.bias_on) {
 #pragma unroll 1
             for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
@@ -687,7 +687,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
               float qv = qrow[i + b];
               float df = __fsub_rn(qv, pv);
               acc[b] = fmaf(df, df, acc[b]);
-              if (g.bias_on) bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, qv), 0.f));
+              if (ST != 2 && g.bias_on) bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, qv), 0.f));
             }
           }
         }
@@ -840,7 +840,7 @@ __device__ __forceinline__ float mc_alpha(const DGeom &g, int n, int lane, const
 // weights in wts, and for the second mass-conservation sweep the correction
 // alpha = d_g / (zeta^T 1) of Def. "Aggregation-aware constant-synthesis
 // correction" in *alpha_out.
-template <int D, int JC>
+template <int D, int JC, int ST>
 __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
                                          const int *__restrict__ vreg, const int *__restrict__ vbuf,
                                          const float *__restrict__ omega, const float *__restrict__ Sg,
@@ -853,7 +853,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
   using SH = CubeShape<D, JC>;
   const int P = SH::fixed ? SH::P : g.P;
   const int MS = SH::fixed ? SH::MS : g.MS;
-  const bool stage2 = g.stage == 2;
+  const bool stage2 = ST ? ST == 2 : g.stage == 2;  // ST: stage fixed at compile time
   // The transforms run as one loop over a short phase list so that the
   // transform code is inlined once: before each transform, the phase's own
   // gather / shrink / gain step.
@@ -1078,7 +1078,7 @@ __device__ __forceinline__ void col_wiener_apply(float *bufA, const float *bufB,
     }                                                                \
   }
 
-template <int D, int JC>
+template <int D, int JC, int ST>
 __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
                                             const int *__restrict__ vreg, const float *__restrict__ omega,
                                             const float *__restrict__ Sg, const float *__restrict__ Sy,
@@ -1090,7 +1090,7 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   constexpr int P = ipow(JC, D);
   constexpr int MS = CubeShape<D, JC>::MS;
   static_assert(MS == (P | 1), "register filter layout");
-  const bool stage2 = g.stage == 2;
+  const bool stage2 = ST ? ST == 2 : g.stage == 2;  // ST: stage fixed at compile time
   // ---- entries of a shared region into rows of buf (lanes over entries)
   auto gather = [&](float *buf, const float *src) {
     if constexpr (P % 32 == 0) {
@@ -1257,7 +1257,7 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
 // mode 1: match only, group tables written; mode 2: mass-conservation sweep 2
 // (groups read back, corrected patches aggregated with the sweep-1 weights).
 // Persistent: each CTA takes tiles from *counter until all are done.
-template <int D, int JL, int KB, int MINB>
+template <int D, int JL, int KB, int MINB, int ST>
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, const float *__restrict__ tab,
         int *counter) {
@@ -1289,7 +1289,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
       for (int i = threadIdx.x; i < (int)(sizeof(DJob) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
       const DGeom &g = sj->g;
-      L = smem_layout(smem, g, g.stage == 2, mode == 2, mode == 2 && sj->pcache != nullptr);
+      L = smem_layout(smem, g, ST ? ST == 2 : g.stage == 2, mode == 2, mode == 2 && sj->pcache != nullptr);
       for (int v = threadIdx.x; v < g.P; v += blockDim.x) {
         int rem = v, ro = 0;
         float w = 1.f;
@@ -1359,7 +1359,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     if (mode == 2 && sj->groups == nullptr) continue;
     const DGeom &g = sj->g;
     const int tile = gt - sj->tile_base;
-    const bool stage2 = g.stage == 2;
+    const bool stage2 = ST ? ST == 2 : g.stage == 2;
     const bool mc2 = mode == 2;
     // second sweep from the synthesis cache: y and eta staged, no filtering
     const bool cmode = mc2 && sj->pcache != nullptr;
@@ -1449,7 +1449,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           for (int d = D - 1; d >= 0; --d) { rr[d] = rem % g.C[d] + g.rad[d]; rem /= g.C[d]; }
         }
         if (!mc2) {
-          n = warp_match<D, JL, KB>(g, Sg, rr, org, rowoff, lane, mem);
+          n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem);
           if (sj->groups) {
             for (int m = lane; m < g.M; m += 32)
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
@@ -1544,10 +1544,10 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           } else {
             int which;
             if constexpr (SH::rf)
-              which = filter_group_rf<D, JL>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
+              which = filter_group_rf<D, JL, ST>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
                                              sj->y, sj->eta, gb, L.vgl, &alpha);
             else
-              which = filter_group<D, JL>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
+              which = filter_group<D, JL, ST>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
                                           rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
             syn = which ? bufA : bufB;
             if (!mc2 && cached && sj->groups) {
@@ -1805,26 +1805,34 @@ __global__ void __launch_bounds__(1024) k_ref_base(const int *__restrict__ count
 
 typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 
+template <int D, int JL, int KB, int ST = 0>
+stage_fn stage_ptr(int minb) { return minb >= 2 ? &k_stage<D, JL, KB, 2, ST> : &k_stage<D, JL, KB, 1, ST>; }
+
+// The cubic-patch kernels exist per stage (1 or 2), which keeps each
+// launch's code to the stage it runs; all jobs of such a launch share it.
 template <int D, int JL, int KB>
-stage_fn stage_ptr(int minb) { return minb >= 2 ? &k_stage<D, JL, KB, 2> : &k_stage<D, JL, KB, 1>; }
+stage_fn stage_ptr_st(int minb, int stage) {
+  return stage == 1 ? stage_ptr<D, JL, KB, 1>(minb) : stage_ptr<D, JL, KB, 2>(minb);
+}
 
 // Stage kernel for a geometry: D kernel axes, jL > 0 the side of a cubic
-// patch (compile-time shape) or 0 for any shape, candidates per lane kb, and
-// the register budget: minb = 2 limits registers
+// patch (compile-time shape) or 0 for any shape, candidates per lane kb, the
+// stage of every job in the launch (1 or 2; the generic kernels read it from
+// each job), and the register budget: minb = 2 limits registers
 // so that two CTAs share an SM (used when their shared memory fits), minb = 1
 // gives the kernel the whole register file.
-stage_fn select_stage_kernel(int D, int jL, int kb, int minb) {
+stage_fn select_stage_kernel(int D, int jL, int kb, int minb, int stage) {
   switch (D) {
     case 1:
-      if (jL == 32 && kb == 5) return stage_ptr<1, 32, 5>(minb);
-      if (jL == 16 && kb == 4) return stage_ptr<1, 16, 4>(minb);
+      if (jL == 32 && kb == 5) return stage_ptr_st<1, 32, 5>(minb, stage);
+      if (jL == 16 && kb == 4) return stage_ptr_st<1, 16, 4>(minb, stage);
       return stage_ptr<1, 0, 4>(minb);
     case 2:
-      if (jL == 8 && kb == 8) return stage_ptr<2, 8, 8>(minb);
-      if (jL == 4 && kb == 4) return stage_ptr<2, 4, 4>(minb);
+      if (jL == 8 && kb == 8) return stage_ptr_st<2, 8, 8>(minb, stage);
+      if (jL == 4 && kb == 4) return stage_ptr_st<2, 4, 4>(minb, stage);
       return stage_ptr<2, 0, 4>(minb);
     case 3:
-      if (jL == 4 && kb == 4) return stage_ptr<3, 4, 4>(minb);
+      if (jL == 4 && kb == 4) return stage_ptr_st<3, 4, 4>(minb, stage);
       return stage_ptr<3, 0, 4>(minb);
     case 4: return stage_ptr<4, 0, 4>(minb);
     case 5: return stage_ptr<5, 0, 4>(minb);
