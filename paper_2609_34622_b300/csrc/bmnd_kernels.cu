@@ -571,8 +571,10 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
 // ---------------------------------------------------------------------------
 
 template <int D, int JL, int KB, int ST>
+// nonneg: every staged guide value is >= 0 (count data), where
+// [p + q]_+ = p + q exactly and the bias term skips the max.
 __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
-                          const int *org, const int *rowoff, int lane, int *mem) {
+                          const int *org, const int *rowoff, int lane, int *mem, bool nonneg) {
   int lo[D], W[D];
   int64_t ncand = 1;
 #pragma unroll
@@ -643,7 +645,25 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           float q[KB];
 #pragma unroll
           for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
-          if (ST != 2 && g.bias_on) {
+          if (ST != 2 && g.bias_on && nonneg) {
+#pragma unroll 1
+            for (int i0 = 0; i0 < JJ; i0 += IB) {
+#pragma unroll
+              for (int ii = 0; ii < IB; ++ii) {
+                const int i = i0 + ii;
+                q[KB - 1] = qrow[i + KB - 1];
+                const float pv = prow[i];
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                  float df = __fsub_rn(q[b], pv);
+                  acc[b] = fmaf(df, df, acc[b]);
+                  bs[b] = __fadd_rn(bs[b], __fadd_rn(pv, q[b]));
+                }
+#pragma unroll
+                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
+              }
+            }
+          } else if (ST != 2 && g.bias_on) {
 #pragma unroll 1
             for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
@@ -1396,6 +1416,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     // patch entries (candidates are clipped) and are set to zero
     const float *gsrc = sj->guide, *ysrc = sj->y, *esrc = sj->eta;
     const int RS = g.region + RPAD;
+    bool nonneg_t = true;
     for (int e = threadIdx.x; e < RS; e += blockDim.x) {
       float vg = 0.f, vy = 0.f, ve = 0.f;
       if (e < g.region) {
@@ -1429,8 +1450,9 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         if (stage2 && !g.lean) Sy[e] = vy;
         if (mc2 && !g.lean) Se[e] = ve;
       }
+      nonneg_t = nonneg_t && vg >= 0.f;
     }
-    __syncthreads();
+    const bool tile_nonneg = __syncthreads_and(nonneg_t) != 0;
 
     const int nref = sj->ref_count[tile];
     const int rounds = (nref + NW - 1) / NW;
@@ -1449,7 +1471,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           for (int d = D - 1; d >= 0; --d) { rr[d] = rem % g.C[d] + g.rad[d]; rem /= g.C[d]; }
         }
         if (!mc2) {
-          n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem);
+          n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg);
           if (sj->groups) {
             for (int m = lane; m < g.M; m += 32)
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
