@@ -211,13 +211,17 @@ bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launc
  * path to many concurrent requests).  A worker thread admits submitted jobs in
  * arrival order while the device-memory budget and the slot count allow,
  * copies each admitted job's input to the device and builds its reference
- * schedule, then runs steps: in every step each active job runs its next
- * stage, and jobs of the same kernel class share one launch of each kernel
- * (continuous batching: jobs that arrive while a step runs join the next one;
- * a job's stage-1 estimate and buffers stay on the device between its
- * stages).  When a job's last stage is done its output is copied to the host
- * and its memory is released.  Each job owns its tiles and partial sums, so
- * its result is bitwise the same as bmnd_denoise on the job alone.
+ * schedule.  Jobs go to one of two lanes by their estimated GPU time (1 ms):
+ * each lane has its own stream (the small-job lane at the higher priority)
+ * and keeps up to two steps queued, in which its jobs run both stages.  The
+ * small-job lane batches all its waiting jobs into a step, jobs of the same
+ * kernel class sharing one launch of each kernel; the large-job lane runs one
+ * job per step, the shortest estimate first, aged by the time waited, with
+ * one CTA per tile, so that the small-job lane's CTAs take SMs between its
+ * tiles.
+ * When a job's step is done its output is copied to the host and its memory
+ * is released.  Each job owns its tiles and partial sums, so its result is
+ * bitwise the same as bmnd_denoise on the job alone.
  * Jobs use the App. A profile. */
 typedef struct bmnd_server bmnd_server;
 typedef struct {

@@ -483,11 +483,13 @@ bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
   return BMND_OK;
 }
 
-// Launch the persistent stage kernel: one CTA per resident slot, tiles handed
-// out by an atomic counter that is cleared first.  Every job of the launch
-// runs the given stage (1 or 2).
+// Launch the stage kernel: tiles handed out by an atomic counter that is
+// cleared first (the context's unless another is given); one CTA per resident
+// slot (persistent), or one CTA per tile when tile_ctas is set, which lets the
+// block scheduler place higher-priority work between tiles.  Every job of the
+// launch runs the given stage (1 or 2).
 bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, int stage, const DJob *dj, int nj, int tiles,
-                         int mode, int smem, cudaStream_t st) {
+                         int mode, int smem, cudaStream_t st, int *counter = nullptr, bool tile_ctas = false) {
   // two CTAs per SM when their shared memory fits, else the full register file
   const int minb = 2 * (smem + 1024) <= 233472 ? 2 : 1;
   stage_fn f = select_stage_kernel(D, jL, kb, minb, stage);
@@ -495,9 +497,10 @@ bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, int stage, const 
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)f, NW * 32, smem));
   if (per_sm < 1) return fail(ctx, BMND_EUNSUPPORTED, "stage kernel does not fit on an SM (%d bytes)", smem);
-  int grid = std::min(tiles, per_sm * ctx->num_sms);
-  CU(cudaMemsetAsync(ctx->counters, 0, sizeof(int), st));
-  f<<<grid, NW * 32, smem, st>>>(dj, nj, tiles, mode, ctx->tab, ctx->counters);
+  if (!counter) counter = ctx->counters;
+  int grid = tile_ctas ? tiles : std::min(tiles, per_sm * ctx->num_sms);
+  CU(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  f<<<grid, NW * 32, smem, st>>>(dj, nj, tiles, mode, ctx->tab, counter);
   CU(cudaGetLastError());
   return BMND_OK;
 }
@@ -1206,6 +1209,35 @@ struct SrvJob {
   float *dy = nullptr, *dout = nullptr;
   DJob *djob = nullptr;        // this job's own descriptor (schedule kernels)
   unsigned char *scratch = nullptr;
+  int lane = 0;                // 0 small jobs, 1 large jobs
+  double est_ms = 0;           // estimated GPU time of both stages
+  bool in_step = false;        // part of a step in flight
+};
+
+struct SrvStepRef {
+  bmnd_server *S;
+  int lane, slot;
+};
+
+// A step in flight: its jobs, the descriptor-table region it owns
+// (2 x max_slots) and the flag its host callback sets at the end.
+struct SrvStep {
+  std::vector<SrvJob *> jobs;
+  int tab_base = 0;
+  bool busy = false, done = false;
+  bmnd_status rc = BMND_OK;
+  SrvStepRef ref;
+};
+
+// One lane of the server: its own stream (the small-job lane has the higher
+// priority) and tile counter; up to two steps in flight, so that the next
+// step is queued on the GPU while the host finishes the previous one.
+struct SrvLane {
+  cudaStream_t st = nullptr;
+  int *counter = nullptr;
+  bool tile_ctas = false;          // one CTA per tile (the large-job lane)
+  std::vector<SrvJob *> active;    // admitted jobs, in a step or waiting for one
+  SrvStep steps[2];
 };
 
 }  // namespace
@@ -1220,14 +1252,15 @@ struct bmnd_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<SrvJob *> pending;
-  std::vector<SrvJob *> active;
   std::unordered_map<int64_t, SrvJob *> jobs;
   int64_t next_ticket = 1;
   std::thread worker;
   bool stop = false;
-  cudaStream_t st = nullptr;
-  cudaEvent_t ev = nullptr;
-  DJob *dtab = nullptr, *htab = nullptr;
+  bool admit_blocked = false;  // the oldest pending job waits for memory or a slot
+  SrvLane lanes[2];
+  cudaStream_t cst = nullptr;      // host <-> device copies and schedules
+  cudaEvent_t ev_admit = nullptr;  // end of the latest admissions on cst
+  DJob *dtab = nullptr, *htab = nullptr;  // 2 lanes x 2 steps x 2 stages x max_slots descriptors
   // statistics
   std::vector<double> lat_ms;
   int64_t submitted = 0, completed = 0, failed = 0, steps = 0, jobs_in_steps = 0;
@@ -1278,64 +1311,78 @@ bmnd_status srv_fail(bmnd_server *S, const char *what, cudaError_t e) {
   return BMND_ECUDA;
 }
 
-// One server step: every active job runs its next stage; jobs sharing a
-// kernel class (axes, last-axis patch length, candidates per lane) share
-// one launch of each kernel.
-bmnd_status srv_step(bmnd_server *S, std::vector<SrvJob *> &run) {
+// Host callback at the end of a step (no CUDA calls here).
+void CUDART_CB srv_step_done(void *p) {
+  SrvStepRef *r = static_cast<SrvStepRef *>(p);
+  {
+    std::lock_guard<std::mutex> lk(r->S->mu);
+    r->S->lanes[r->lane].steps[r->slot].done = true;
+  }
+  r->S->cv_work.notify_all();
+}
+
+// One step of a lane, launched asynchronously: every job of T.jobs runs all
+// its stages (stage 1, then stage 2 on the pilot), so it completes in this
+// step; jobs sharing a kernel class (axes, patch side, candidates per lane)
+// share one launch of each kernel per stage.  The lane's stream first waits
+// for the latest admissions.
+bmnd_status srv_step(bmnd_server *S, SrvLane &L, SrvStep &T) {
   bmnd_params pr;
   bmnd_default_params(&pr);
-  std::map<std::pair<int, int>, std::vector<SrvJob *>> classes;
-  for (SrvJob *j : run) {
-    const int stage = j->state == SJ_STAGE1 ? 1 : 2;
-    classes[{j->plan.D, (kernel_jl(j->plan) * 16 + pick_kb(j->plan)) * 4 + stage}].push_back(j);
-  }
-  size_t tab_off = 0;
-  for (auto &kv : classes) {
-    std::vector<SrvJob *> &cj = kv.second;
-    const int D = kv.first.first, key = kv.first.second / 4, stage_c = kv.first.second % 4;
-    const int jL = key / 16, kb = key % 16;
-    int tiles = 0, smax = 0, smax2 = 0;
-    int64_t vox = 0;
-    bool any_mc = false;
-    for (size_t i = 0; i < cj.size(); ++i) {
-      SrvJob *j = cj[i];
-      const int stage = j->state == SJ_STAGE1 ? 1 : 2;
-      DJob J = srv_stage_job(j, stage, pr);
-      J.tile_base = tiles;
-      J.vox_base = vox;
-      tiles += j->plan.g.ntiles;
-      vox += j->plan.g.N;
-      const bool m = J.groups != nullptr;
-      any_mc = any_mc || m;
-      smax = std::max(smax, m ? std::max(j->plan.smem[stage - 1], j->plan.smem[2]) : j->plan.smem[stage - 1]);
-      if (m)
-        smax2 = std::max(smax2, j->plan.cache ? j->plan.smem_cached
-                                              : std::max(j->plan.smem[stage - 1], j->plan.smem[2]));
-      S->htab[tab_off + i] = J;
-    }
-    DJob *dj = S->dtab + tab_off;
-    cudaError_t e = cudaMemcpyAsync(dj, S->htab + tab_off, cj.size() * sizeof(DJob), cudaMemcpyHostToDevice, S->st);
-    if (e != cudaSuccess) return srv_fail(S, "job table copy", e);
-    const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
-    bmnd_status rc = launch_stage(S->ctx, D, jL, kb, stage_c, dj, (int)cj.size(), tiles, 0, smax, S->st);
-    if (rc != BMND_OK) return rc;
-    launch_reduce(D, dj, (int)cj.size(), vox, any_mc ? 1 : 0, rgrid, S->st);
-    if (any_mc) {
-      rc = launch_stage(S->ctx, D, jL, kb, stage_c, dj, (int)cj.size(), tiles, 2, smax2, S->st);
+  cudaError_t e = cudaStreamWaitEvent(L.st, S->ev_admit, 0);
+  if (e != cudaSuccess) return srv_fail(S, "admission wait", e);
+  for (int stage = 1; stage <= 2; ++stage) {
+    std::map<std::pair<int, int>, std::vector<SrvJob *>> classes;
+    for (SrvJob *j : T.jobs)
+      if (stage <= j->spec.stages) classes[{j->plan.D, kernel_jl(j->plan) * 16 + pick_kb(j->plan)}].push_back(j);
+    size_t tab_off = T.tab_base + (size_t)(stage - 1) * S->max_slots;
+    for (auto &kv : classes) {
+      std::vector<SrvJob *> &cj = kv.second;
+      const int D = kv.first.first, jL = kv.first.second / 16, kb = kv.first.second % 16;
+      int tiles = 0, smax = 0, smax2 = 0;
+      int64_t vox = 0;
+      bool any_mc = false;
+      for (size_t i = 0; i < cj.size(); ++i) {
+        SrvJob *j = cj[i];
+        DJob J = srv_stage_job(j, stage, pr);
+        J.tile_base = tiles;
+        J.vox_base = vox;
+        tiles += j->plan.g.ntiles;
+        vox += j->plan.g.N;
+        const bool m = J.groups != nullptr;
+        any_mc = any_mc || m;
+        smax = std::max(smax, m ? std::max(j->plan.smem[stage - 1], j->plan.smem[2]) : j->plan.smem[stage - 1]);
+        if (m)
+          smax2 = std::max(smax2, j->plan.cache ? j->plan.smem_cached
+                                                : std::max(j->plan.smem[stage - 1], j->plan.smem[2]));
+        S->htab[tab_off + i] = J;
+      }
+      DJob *dj = S->dtab + tab_off;
+      e = cudaMemcpyAsync(dj, S->htab + tab_off, cj.size() * sizeof(DJob), cudaMemcpyHostToDevice, L.st);
+      if (e != cudaSuccess) return srv_fail(S, "job table copy", e);
+      const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
+      bmnd_status rc = launch_stage(S->ctx, D, jL, kb, stage, dj, (int)cj.size(), tiles, 0, smax, L.st, L.counter,
+                                    L.tile_ctas);
       if (rc != BMND_OK) return rc;
-      launch_reduce(D, dj, (int)cj.size(), vox, 0, rgrid, S->st);
+      launch_reduce(D, dj, (int)cj.size(), vox, any_mc ? 1 : 0, rgrid, L.st);
+      if (any_mc) {
+        rc = launch_stage(S->ctx, D, jL, kb, stage, dj, (int)cj.size(), tiles, 2, smax2, L.st, L.counter,
+                          L.tile_ctas);
+        if (rc != BMND_OK) return rc;
+        launch_reduce(D, dj, (int)cj.size(), vox, 0, rgrid, L.st);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return srv_fail(S, "stage launch", e);
+      tab_off += cj.size();
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return srv_fail(S, "stage launch", e);
-    tab_off += cj.size();
   }
-  cudaError_t e = cudaEventRecord(S->ev, S->st);
-  if (e == cudaSuccess) e = cudaEventSynchronize(S->ev);
-  if (e != cudaSuccess) return srv_fail(S, "step", e);
+  e = cudaLaunchHostFunc(L.st, srv_step_done, &T.ref);
+  if (e != cudaSuccess) return srv_fail(S, "step callback", e);
   return BMND_OK;
 }
 
-// Admission set-up of one job: input copy, descriptor, reference schedule.
+// Admission set-up of one job on the copy stream: input copy, descriptor,
+// reference schedule.
 bmnd_status srv_admit(bmnd_server *S, SrvJob *j) {
   const Plan &pl = j->plan;
   unsigned char *base = S->arena + j->off;
@@ -1347,14 +1394,14 @@ bmnd_status srv_admit(bmnd_server *S, SrvJob *j) {
   bmnd_params pr;
   bmnd_default_params(&pr);
   DJob J = srv_stage_job(j, 1, pr);
-  cudaError_t e = cudaMemcpyAsync(j->dy, j->spec.y, pl.g.N * 4, cudaMemcpyHostToDevice, S->st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(j->djob, &J, sizeof(DJob), cudaMemcpyHostToDevice, S->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(j->scratch + pl.o_flags, 0, (size_t)pl.nflags, S->st);
+  cudaError_t e = cudaMemcpyAsync(j->dy, j->spec.y, pl.g.N * 4, cudaMemcpyHostToDevice, S->cst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(j->djob, &J, sizeof(DJob), cudaMemcpyHostToDevice, S->cst);
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->scratch + pl.o_flags, 0, (size_t)pl.nflags, S->cst);
   if (e != cudaSuccess) return srv_fail(S, "admission copy", e);
   launch_sched(pl.s, j->scratch + pl.o_flags, j->djob, pl.g.ntiles, (int *)(j->scratch + pl.o_refs),
-               (int *)(j->scratch + pl.o_rcount), S->st);
+               (int *)(j->scratch + pl.o_rcount), S->cst);
   if (pl.cache)
-    launch_ref_base((const int *)(j->scratch + pl.o_rcount), pl.g.ntiles, (int *)(j->scratch + pl.o_refbase), S->st);
+    launch_ref_base((const int *)(j->scratch + pl.o_rcount), pl.g.ntiles, (int *)(j->scratch + pl.o_refbase), S->cst);
   e = cudaGetLastError();
   if (e != cudaSuccess) return srv_fail(S, "schedule launch", e);
   return BMND_OK;
@@ -1366,6 +1413,7 @@ void srv_finish(bmnd_server *S, SrvJob *j, bmnd_status rc) {
   j->state = rc == BMND_OK ? SJ_DONE : SJ_FAILED;
   j->t_done = Clock::now();
   S->alloc.release(j->off, j->bytes);
+  S->admit_blocked = false;  // memory and a slot came free
   if (rc == BMND_OK) {
     ++S->completed;
     S->lat_ms.push_back(std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count());
@@ -1376,67 +1424,175 @@ void srv_finish(bmnd_server *S, SrvJob *j, bmnd_status rc) {
   }
 }
 
+// Estimated milliseconds of a job on one B300 (both stages): candidate
+// comparisons x patch entries, at a per-rank rate measured on the paper's
+// configurations.  It only chooses the lane.
+double srv_job_ms(const Plan &pl, int stages) {
+  double cand = 1.0;
+  for (int a = 0; a < pl.D; ++a) cand *= 2.0 * pl.g.rad[a] + 1.0;
+  const double units = (double)pl.s.nslots * pl.s.passes * cand * pl.g.P * stages;
+  const double ms_per_g = pl.D == 1 ? 1.5 : (pl.D == 2 ? 0.55 : 1.0);
+  return units * 1e-9 * ms_per_g;
+}
+
+// Jobs estimated above this run in the large-job lane.
+constexpr double kLargeJobMs = 1.0;
+
+// The worker: completes finished lane steps (results back to the host),
+// admits pending jobs in arrival order within the memory budget, and starts
+// the next step of every idle lane that has jobs.  Small and large jobs run
+// in separate lanes, so a large job's stage (one CTA per tile, low priority)
+// never holds back the small jobs' steps by more than a tile.  CUDA calls are
+// made without holding the lock.
 void srv_loop(bmnd_server *S) {
   cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto waiting = [&](const SrvLane &L) {
+    for (const SrvJob *j : L.active)
+      if (!j->in_step) return true;
+    return false;
+  };
+  auto lane_ready = [&](const SrvLane &L) {
+    bool free_slot = false;
+    for (const SrvStep &T : L.steps) {
+      if (T.busy && T.done) return true;
+      free_slot = free_slot || !T.busy;
+    }
+    return free_slot && waiting(L);
+  };
   for (;;) {
-    std::vector<SrvJob *> admit;
-    {
-      std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
-      if (S->stop && S->pending.empty() && S->active.empty()) break;
-      // memory-budgeted admission in arrival order
-      while (!S->pending.empty() && (int)(S->active.size() + admit.size()) < S->max_slots) {
-        SrvJob *j = S->pending.front();
-        size_t off = 0;
-        if (!S->alloc.alloc(j->bytes, off)) break;
-        j->off = off;
-        S->pending.pop_front();
-        admit.push_back(j);
-      }
-    }
-    bmnd_status rc = BMND_OK;
-    for (SrvJob *j : admit) {
-      rc = srv_admit(S, j);
-      if (rc != BMND_OK) break;
-    }
-    std::vector<SrvJob *> run;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      for (SrvJob *j : admit) {
-        j->state = SJ_STAGE1;
-        S->active.push_back(j);
-      }
-      run = S->active;
-    }
-    if (rc == BMND_OK && !run.empty()) rc = srv_step(S, run);
-    // results of jobs that ran their last stage go back to the host
-    std::vector<SrvJob *> finished;
-    for (SrvJob *j : run) {
-      const bool last = rc != BMND_OK || j->state == SJ_STAGE2 || j->spec.stages == 1;
-      if (!last) continue;
-      if (rc == BMND_OK) {
-        cudaError_t e = cudaMemcpyAsync(j->spec.out, j->dout, j->plan.g.N * 4, cudaMemcpyDeviceToHost, S->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
-        if (e != cudaSuccess) {
-          cudaGetLastError();
-          j->status = BMND_ECUDA;
+    S->cv_work.wait(lk, [&] {
+      return S->stop || (!S->pending.empty() && !S->admit_blocked) || lane_ready(S->lanes[0]) ||
+             lane_ready(S->lanes[1]);
+    });
+    bool idle = true;
+    for (const SrvLane &L : S->lanes) idle = idle && L.active.empty() && !L.steps[0].busy && !L.steps[1].busy;
+    if (S->stop && S->pending.empty() && idle) break;
+    // ---- finished steps
+    for (int li = 0; li < 2; ++li) {
+      SrvLane &L = S->lanes[li];
+      for (SrvStep &T : L.steps) {
+        if (!(T.busy && T.done)) continue;
+        std::vector<SrvJob *> run;
+        run.swap(T.jobs);
+        bmnd_status rc = T.rc;
+        lk.unlock();
+        if (rc == BMND_OK) {
+          cudaError_t e = cudaStreamQuery(L.st);
+          if (e != cudaSuccess && e != cudaErrorNotReady) rc = srv_fail(S, "step", e);
         }
+        for (SrvJob *j : run) {
+          if (rc != BMND_OK) continue;
+          // pageable destination: the copy has completed when this returns
+          cudaError_t e = cudaMemcpyAsync(j->spec.out, j->dout, j->plan.g.N * 4, cudaMemcpyDeviceToHost, S->cst);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(S->cst);
+          if (e != cudaSuccess) {
+            cudaGetLastError();
+            j->status = BMND_ECUDA;
+          }
+        }
+        lk.lock();
+        T.busy = T.done = false;
+        ++S->steps;
+        S->jobs_in_steps += (int64_t)run.size();
+        for (SrvJob *j : run) {
+          L.active.erase(std::find(L.active.begin(), L.active.end(), j));
+          srv_finish(S, j, rc != BMND_OK ? rc : j->status);
+        }
+        S->cv_done.notify_all();
       }
-      finished.push_back(j);
     }
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      ++S->steps;
-      S->jobs_in_steps += (int64_t)run.size();
-      for (SrvJob *j : run)
-        if (j->state == SJ_STAGE1 && j->spec.stages == 2 && rc == BMND_OK) j->state = SJ_STAGE2;
-      for (SrvJob *j : finished) {
-        S->active.erase(std::find(S->active.begin(), S->active.end(), j));
-        srv_finish(S, j, rc != BMND_OK ? rc : j->status);
+    // ---- admission in arrival order within the memory budget
+    std::vector<SrvJob *> admit;
+    while (!S->pending.empty()) {
+      if ((int)(S->lanes[0].active.size() + S->lanes[1].active.size() + admit.size()) >= S->max_slots) {
+        S->admit_blocked = true;
+        break;
+      }
+      SrvJob *j = S->pending.front();
+      size_t off = 0;
+      if (!S->alloc.alloc(j->bytes, off)) {
+        S->admit_blocked = true;
+        break;
+      }
+      j->off = off;
+      S->pending.pop_front();
+      admit.push_back(j);
+    }
+    if (!admit.empty()) {
+      lk.unlock();
+      bmnd_status rc = BMND_OK;
+      for (SrvJob *j : admit)
+        if (rc == BMND_OK) rc = srv_admit(S, j);
+      if (rc == BMND_OK) {
+        cudaError_t e = cudaEventRecord(S->ev_admit, S->cst);
+        if (e != cudaSuccess) rc = srv_fail(S, "admission event", e);
+      }
+      if (rc != BMND_OK) cudaStreamSynchronize(S->cst);
+      lk.lock();
+      for (SrvJob *j : admit) {
+        if (rc != BMND_OK) {
+          srv_finish(S, j, rc);
+          continue;
+        }
+        j->state = SJ_STAGE1;
+        S->lanes[j->lane].active.push_back(j);
+      }
+      if (rc != BMND_OK) S->cv_done.notify_all();
+    }
+    // ---- next steps: every free step slot of a lane with waiting jobs
+    for (int li = 0; li < 2; ++li) {
+      SrvLane &L = S->lanes[li];
+      for (SrvStep &T : L.steps) {
+        if (T.busy || !waiting(L)) continue;
+        T.jobs.clear();
+        if (li == 0) {
+          // small jobs: all waiting ones, batched
+          for (SrvJob *j : L.active)
+            if (!j->in_step) T.jobs.push_back(j);
+        } else {
+          // larger jobs: one per step, the shortest estimate first, aged by
+          // the time waited so that none starves
+          const Clock::time_point now = Clock::now();
+          SrvJob *best = nullptr;
+          double best_key = 0;
+          for (SrvJob *j : L.active) {
+            if (j->in_step) continue;
+            const double key = j->est_ms - std::chrono::duration<double, std::milli>(now - j->t_submit).count();
+            if (!best || key < best_key) {
+              best = j;
+              best_key = key;
+            }
+          }
+          T.jobs.push_back(best);
+        }
+        for (SrvJob *j : T.jobs) j->in_step = true;
+        T.busy = true;
+        T.done = false;
+        lk.unlock();
+        bmnd_status rc = srv_step(S, L, T);
+        if (rc != BMND_OK) cudaStreamSynchronize(L.st);
+        lk.lock();
+        T.rc = rc;
+        if (rc != BMND_OK) T.done = true;  // no callback was queued
       }
     }
-    S->cv_done.notify_all();
   }
+}
+
+// Frees a server's device and host resources (the worker has stopped).
+void srv_release(bmnd_server *S) {
+  for (int li = 0; li < 2; ++li) {
+    if (S->lanes[li].st) cudaStreamDestroy(S->lanes[li].st);
+    if (S->lanes[li].counter) cudaFree(S->lanes[li].counter);
+  }
+  if (S->ev_admit) cudaEventDestroy(S->ev_admit);
+  if (S->cst) cudaStreamDestroy(S->cst);
+  if (S->arena) cudaFree(S->arena);
+  if (S->dtab) cudaFree(S->dtab);
+  if (S->htab) cudaFreeHost(S->htab);
+  if (S->ctx) bmnd_destroy(S->ctx);
+  delete S;
 }
 
 }  // namespace
@@ -1453,22 +1609,33 @@ bmnd_status bmnd_server_create(bmnd_server **out, int device, const bmnd_server_
   bmnd_status rc = bmnd_create(&S->ctx, device, 0);
   if (rc == BMND_OK) {
     cudaSetDevice(device);
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     if (cudaMalloc(&S->arena, S->budget) != cudaSuccess ||
-        cudaMalloc(&S->dtab, sizeof(DJob) * S->max_slots) != cudaSuccess ||
-        cudaMallocHost(&S->htab, sizeof(DJob) * S->max_slots) != cudaSuccess) {
+        cudaMalloc(&S->dtab, sizeof(DJob) * 8 * S->max_slots) != cudaSuccess ||
+        cudaMallocHost(&S->htab, sizeof(DJob) * 8 * S->max_slots) != cudaSuccess ||
+        cudaMalloc(&S->lanes[0].counter, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&S->lanes[1].counter, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       rc = BMND_ENOMEM;
-    } else if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
-               cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) != cudaSuccess) {
+    } else if (cudaStreamCreateWithPriority(&S->lanes[0].st, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+               cudaStreamCreateWithPriority(&S->lanes[1].st, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+               cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventRecord(S->ev_admit, S->cst) != cudaSuccess) {
       rc = BMND_ECUDA;
     }
+    for (int li = 0; li < 2; ++li)
+      for (int k = 0; k < 2; ++k) {
+        S->lanes[li].steps[k].tab_base = (li * 2 + k) * 2 * S->max_slots;
+        S->lanes[li].steps[k].ref = SrvStepRef{S, li, k};
+      }
+    // the large-job lane launches one CTA per tile: the small-job lane's
+    // higher-priority CTAs take SMs as the large job's tiles finish
+    S->lanes[1].tile_ctas = true;
   }
   if (rc != BMND_OK) {
-    if (S->arena) cudaFree(S->arena);
-    if (S->dtab) cudaFree(S->dtab);
-    if (S->htab) cudaFreeHost(S->htab);
-    if (S->ctx) bmnd_destroy(S->ctx);
-    delete S;
+    srv_release(S);
     return rc;
   }
   S->alloc.init(S->budget);
@@ -1501,6 +1668,8 @@ bmnd_status bmnd_server_submit(bmnd_server *S, const bmnd_job *job, int64_t *tic
         if (al256(srv_job_bytes(j->plan)) > S->budget / 4) drop_mc_cache(j->plan);
       }
       j->bytes = al256(srv_job_bytes(j->plan));
+      j->est_ms = srv_job_ms(j->plan, job->stages);
+      j->lane = j->est_ms > kLargeJobMs ? 1 : 0;
       if (j->bytes > S->budget)
         rc = fail(S->ctx, BMND_ENOMEM, "job needs %zu bytes, the server budget is %zu", j->bytes, S->budget);
     }
@@ -1516,6 +1685,7 @@ bmnd_status bmnd_server_submit(bmnd_server *S, const bmnd_job *job, int64_t *tic
     }
     ++S->submitted;
     S->jobs[j->ticket] = j;
+    if (S->pending.empty()) S->admit_blocked = false;
     S->pending.push_back(j);
     *ticket = j->ticket;
   }
@@ -1574,13 +1744,7 @@ bmnd_status bmnd_server_destroy(bmnd_server *S) {
   for (auto &kv : S->jobs) delete kv.second;
   cudaSetDevice(S->device);
   cudaDeviceSynchronize();
-  if (S->ev) cudaEventDestroy(S->ev);
-  if (S->st) cudaStreamDestroy(S->st);
-  if (S->arena) cudaFree(S->arena);
-  if (S->dtab) cudaFree(S->dtab);
-  if (S->htab) cudaFreeHost(S->htab);
-  if (S->ctx) bmnd_destroy(S->ctx);
-  delete S;
+  srv_release(S);
   return BMND_OK;
 }
 

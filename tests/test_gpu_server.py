@@ -57,9 +57,12 @@ def test_server_mix_equals_alone(budget_mb, slots):
     tickets = []
 
     def client():
+        # a burst (all jobs queued while the first steps run) with the large
+        # budget; spaced arrivals with the small one
         for k, (y, c) in enumerate(jobs):
             tickets.append(srv.bmnd_server_submit(y, c))
-            time.sleep(0.002 * (k % 3))
+            if slots != 64:
+                time.sleep(0.002 * (k % 3))
     th = threading.Thread(target=client)
     th.start()
     th.join()
