@@ -251,6 +251,35 @@ bmnd_status bmnd_server_get_stats(bmnd_server *srv, bmnd_server_stats *stats);
 /* Finish all submitted jobs, stop the worker and release everything. */
 bmnd_status bmnd_server_destroy(bmnd_server *srv);
 
+/* ---- Replayable graphs ----------------------------------------------------
+ * The computation of bmnd_denoise_ex (both stages, Sec. 4-5 as for that call)
+ * on one array, recorded once as a CUDA graph and replayed: for arrays that
+ * are denoised again and again with the same shape and parameters (frames of
+ * a detector, slices of a series), where the host-side planning and the
+ * dozen launches of a call would otherwise be repeated.  The paper has no
+ * counterpart: this is an execution convenience.
+ *   - bmnd_graph_create plans the array, allocates the graph's own scratch
+ *     and descriptor table (device memory, held until bmnd_graph_destroy),
+ *     uploads the table (synchronously) and records the launches with stream
+ *     capture on a private stream.  Call it outside any stream capture.
+ *   - y and out are device arrays BOUND at creation: refill y (float32,
+ *     C-order, shape as given) and launch again to denoise new data; out
+ *     receives the estimate.  They must stay allocated while the graph lives.
+ *   - bmnd_graph_launch enqueues the graph on `stream`; launches of one graph
+ *     share its scratch, so they must not overlap on the GPU (launch on one
+ *     stream, or order them).  A replay gives bitwise the output of
+ *     bmnd_denoise_ex on the same input.
+ *   - bmnd_graph_destroy waits for the device to be idle, then frees it.
+ * Errors: those of bmnd_denoise_ex; BMND_ENOMEM / BMND_ECUDA when the scratch
+ * cannot be allocated or the recording fails (bmnd_last_error of ctx says). */
+typedef struct bmnd_graph bmnd_graph;
+bmnd_status bmnd_graph_create(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                              const int *patch, const int *step, const int *search, const int *group_size,
+                              int stages, int mass_conserve, const bmnd_params *params, float *out,
+                              bmnd_graph **graph);
+bmnd_status bmnd_graph_launch(bmnd_graph *graph, void *stream);
+bmnd_status bmnd_graph_destroy(bmnd_graph *graph);
+
 /* Allocation-free denoising (the paper has no counterpart: this is a
  * deployment convenience).  Same computation and arguments as bmnd_denoise
  * with the App. A profile, but no context and no allocation: it calls no

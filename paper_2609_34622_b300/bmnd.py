@@ -68,7 +68,8 @@ class bmnd_server_stats(ctypes.Structure):
 EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_error", "bmnd_denoise",
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
-           "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy"]
+           "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
+           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4}
 
 _lib = None
@@ -109,6 +110,9 @@ def load(path: str = LIB_PATH):
     lib.bmnd_denoise_noalloc.argtypes = [vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ip, ctypes.c_int,
                                          ctypes.c_int, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.bmnd_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double)]
+    lib.bmnd_graph_create.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, P(vp)]
+    lib.bmnd_graph_launch.argtypes = [vp, vp]
+    lib.bmnd_graph_destroy.argtypes = [vp]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -214,6 +218,21 @@ class Context:
         self._check(st)
         return out
 
+    def bmnd_graph_create(self, y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,
+                          mass_conserve=0, prm: bmnd_params | None = None):
+        """Record both stages on the bound CUDA tensors y / out as a replayable
+        graph (refill y, then Graph.bmnd_graph_launch)."""
+        _check_tensor(y, "y")
+        _check_tensor(out, "out")
+        shape = tuple(y.shape)
+        h = ctypes.c_void_p()
+        st = self._lib.bmnd_graph_create(self.handle, _ptr(y), len(shape), _ints(shape, ctypes.c_int64),
+                                         noise(noise_spec), _ints(patch), _ints(step), _ints(search),
+                                         _ints(group_size), int(stages), int(mass_conserve),
+                                         ctypes.byref(prm) if prm is not None else None, _ptr(out), ctypes.byref(h))
+        self._check(st)
+        return Graph(self._lib, h, y, out)
+
     def bmnd_stage(self, y, pilot, out, noise_spec, patch, step, search, group_max, stage, mass_conserve=0,
                    prm: bmnd_params | None = None, stream=None):
         _check_tensor(y, "y")
@@ -303,6 +322,31 @@ class Context:
                                                     ctypes.byref(ms)))
             res[name] = (n.value, ms.value)
         return res
+
+
+class Graph:
+    """A recorded bmnd_denoise_ex call on bound device tensors (bmnd_graph_*).
+    Refill the bound input tensor, then launch again."""
+
+    def __init__(self, lib, handle, y, out):
+        self._lib, self.handle, self.y, self.out = lib, handle, y, out
+
+    def bmnd_graph_launch(self, stream=None):
+        st = self._lib.bmnd_graph_launch(self.handle, _stream(stream))
+        if st != OK:
+            raise BmndError(st, "graph launch failed")
+        return self.out
+
+    def close(self):
+        if self.handle:
+            self._lib.bmnd_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _fill_job(j, y_ptr, out_ptr, shape, c):

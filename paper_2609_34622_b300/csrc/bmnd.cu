@@ -547,42 +547,31 @@ bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz) {
   return BMND_OK;
 }
 
-// Run both requested stages of several arrays with shared launches.  All
-// plans must have the same kernel rank D.  first_stage/last_stage select a
-// sub-range (bmnd_stage runs one stage with an external pilot).
-bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<JobIO> &io,
-                     const bmnd_params &pr, int first_stage, int last_stage, const float *ext_pilot,
-                     cudaStream_t st) {
-  int nj = (int)plans.size();
-  int D = plans[0].D;
-  for (auto &pl : plans)
-    if (pl.D != D) return fail(ctx, BMND_EUNSUPPORTED, "batched jobs must share the number of non-singleton axes");
-  // synthesis caches for mass-conserving jobs, unless they exceed the
-  // context's scratch budget
-  for (int i = 0; i < nj; ++i)
-    if (io[i].mass_conserve) add_mc_cache(plans[i]);
-  std::vector<size_t> base(nj);
-  size_t need = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    need = 0;
-    for (int i = 0; i < nj; ++i) { base[i] = need; need = al256(need + plans[i].total); }
-    if (!ctx->budget || need <= ctx->budget) break;
-    for (auto &pl : plans) drop_mc_cache(pl);
-  }
-  bmnd_status rc = ensure_arena(ctx, need, st);
-  if (rc != BMND_OK) return rc;
-  char *A = (char *)ctx->arena;
-  // job tables: [stage 1 | stage 2]
-  std::vector<DJob> h(2 * nj);
-  int tiles = 0;
+// Job tables of several arrays laid out from scratch base A (job i at
+// A + base[i]): h = [stage 1 | stage 2] descriptors, plus what the launches
+// need.  first_stage / last_stage select a sub-range (bmnd_stage runs one
+// stage with an external pilot).
+struct JobTables {
+  std::vector<DJob> h;
+  int nj = 0, D = 0, tiles = 0;
   int64_t vox = 0;
   int smax[2] = {0, 0}, smax2[2] = {0, 0};
   bool any_mc[2] = {false, false};
+  int kjL = 0, kkb = 4;
+};
+
+void build_tables(const std::vector<Plan> &plans, const std::vector<JobIO> &io, const bmnd_params &pr,
+                  int first_stage, int last_stage, const float *ext_pilot, char *A, const std::vector<size_t> &base,
+                  JobTables &t) {
+  const int nj = (int)plans.size();
+  t.nj = nj;
+  t.D = plans[0].D;
+  t.h.assign(2 * nj, DJob());
   for (int i = 0; i < nj; ++i) {
-    Plan &pl = plans[i];
+    const Plan &pl = plans[i];
     char *B = A + base[i];
     for (int s = 1; s <= 2; ++s) {
-      DJob &J = h[(s - 1) * nj + i];
+      DJob &J = t.h[(s - 1) * nj + i];
       memset(&J, 0, sizeof(J));
       J.g = pl.g;
       int M = io[i].group_size[s - 1];
@@ -606,58 +595,130 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
         J.ref_base = (const int *)(B + pl.o_refbase);
         J.pcache_refs = pl.cache_refs;
       }
-      J.tile_base = tiles;
-      J.vox_base = vox;
-      if (mc) any_mc[s - 1] = true;
-      smax[s - 1] = std::max(smax[s - 1], mc ? std::max(pl.smem[s - 1], pl.smem[2]) : pl.smem[s - 1]);
-      if (mc) smax2[s - 1] = std::max(smax2[s - 1], pl.cache ? pl.smem_cached : std::max(pl.smem[s - 1], pl.smem[2]));
+      J.tile_base = t.tiles;
+      J.vox_base = t.vox;
+      if (mc) t.any_mc[s - 1] = true;
+      t.smax[s - 1] = std::max(t.smax[s - 1], mc ? std::max(pl.smem[s - 1], pl.smem[2]) : pl.smem[s - 1]);
+      if (mc)
+        t.smax2[s - 1] =
+            std::max(t.smax2[s - 1], pl.cache ? pl.smem_cached : std::max(pl.smem[s - 1], pl.smem[2]));
     }
-    tiles += pl.g.ntiles;
-    vox += pl.g.N;
+    t.tiles += pl.g.ntiles;
+    t.vox += pl.g.N;
   }
-  rc = stage_jobs(ctx, h, st);
-  if (rc != BMND_OK) return rc;
+  t.kjL = kernel_jl(plans[0]);
+  t.kkb = pick_kb(plans[0]);
+  for (int i = 1; i < nj; ++i)
+    if (kernel_jl(plans[i]) != t.kjL) { t.kjL = 0; t.kkb = 4; }
+}
+
+// The launches of both requested stages, with the job tables already on the
+// device at dtab and tile counter `counter`: schedules, stage kernels,
+// reductions (and the second mass-conservation sweeps).  Only stream work:
+// it can be recorded into a CUDA graph.
+bmnd_status record_launches(bmnd_ctx *ctx, const std::vector<Plan> &plans, const JobTables &t, char *A,
+                            const std::vector<size_t> &base, int first_stage, int last_stage, DJob *dtab,
+                            int *counter, cudaStream_t st) {
+  const int nj = t.nj, D = t.D;
   // schedule of every job (shared by both stages)
   for (int i = 0; i < nj; ++i) {
-    Plan &pl = plans[i];
+    const Plan &pl = plans[i];
     char *B = A + base[i];
     CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
     ProfScope ps(ctx, BMND_KERNEL_SCHEDULE, st);
-    launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), ctx->djobs + (first_stage == 2 ? nj : 0) + i,
+    launch_sched(pl.s, (unsigned char *)(B + pl.o_flags), dtab + (first_stage == 2 ? nj : 0) + i,
                  pl.g.ntiles, (int *)(B + pl.o_refs), (int *)(B + pl.o_rcount), st);
     if (pl.cache) launch_ref_base((const int *)(B + pl.o_rcount), pl.g.ntiles, (int *)(B + pl.o_refbase), st);
   }
   CU(cudaGetLastError());
-  int kjL = kernel_jl(plans[0]), kkb = pick_kb(plans[0]);
-  for (int i = 1; i < nj; ++i)
-    if (kernel_jl(plans[i]) != kjL) { kjL = 0; kkb = 4; }
-  int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
+  const int rgrid = (int)std::min<int64_t>((t.vox + 255) / 256, 148 * 32);
   for (int s = first_stage; s <= last_stage; ++s) {
-    const DJob *dj = ctx->djobs + (s - 1) * nj;
+    const DJob *dj = dtab + (s - 1) * nj;
+    bmnd_status rc;
     {
       ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
-      rc = launch_stage(ctx, D, kjL, kkb, s, dj, nj, tiles, 0, smax[s - 1], st);
+      rc = launch_stage(ctx, D, t.kjL, t.kkb, s, dj, nj, t.tiles, 0, t.smax[s - 1], st, counter);
     }
     if (rc != BMND_OK) return rc;
     {
       ProfScope ps(ctx, BMND_KERNEL_REDUCE, st);
-      launch_reduce(D, dj, nj, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
+      launch_reduce(D, dj, nj, t.vox, t.any_mc[s - 1] ? 1 : 0, rgrid, st);
     }
     CU(cudaGetLastError());
-    if (any_mc[s - 1]) {
+    if (t.any_mc[s - 1]) {
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
-        rc = launch_stage(ctx, D, kjL, kkb, s, dj, nj, tiles, 2, smax2[s - 1], st);
+        rc = launch_stage(ctx, D, t.kjL, t.kkb, s, dj, nj, t.tiles, 2, t.smax2[s - 1], st, counter);
       }
       if (rc != BMND_OK) return rc;
       {
         ProfScope ps(ctx, BMND_KERNEL_REDUCE, st);
-        launch_reduce(D, dj, nj, vox, 0, rgrid, st);
+        launch_reduce(D, dj, nj, t.vox, 0, rgrid, st);
       }
       CU(cudaGetLastError());
     }
   }
   return BMND_OK;
+}
+
+// Scratch layout of several arrays: the synthesis caches of mass-conserving
+// jobs when they fit `budget` (0: no limit), job i at offset base[i].
+size_t layout_jobs(std::vector<Plan> &plans, const std::vector<JobIO> &io, size_t budget, std::vector<size_t> &base) {
+  const int nj = (int)plans.size();
+  for (int i = 0; i < nj; ++i)
+    if (io[i].mass_conserve) add_mc_cache(plans[i]);
+  base.assign(nj, 0);
+  size_t need = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    need = 0;
+    for (int i = 0; i < nj; ++i) { base[i] = need; need = al256(need + plans[i].total); }
+    if (!budget || need <= budget) break;
+    for (auto &pl : plans) drop_mc_cache(pl);
+  }
+  return need;
+}
+
+}  // namespace
+
+// A recorded call (bmnd_graph_create): its own scratch, descriptor table and
+// tile counter, and the instantiated graph of its launches.
+struct bmnd_graph {
+  int device = 0;
+  void *scratch = nullptr;
+  DJob *dtab = nullptr;
+  int *counter = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void graph_release(bmnd_graph *G) {
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->scratch) cudaFree(G->scratch);
+  if (G->dtab) cudaFree(G->dtab);
+  if (G->counter) cudaFree(G->counter);
+  delete G;
+}
+
+// Run both requested stages of several arrays with shared launches.  All
+// plans must have the same kernel rank D.  first_stage/last_stage select a
+// sub-range (bmnd_stage runs one stage with an external pilot).
+bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<JobIO> &io,
+                     const bmnd_params &pr, int first_stage, int last_stage, const float *ext_pilot,
+                     cudaStream_t st) {
+  const int D = plans[0].D;
+  for (auto &pl : plans)
+    if (pl.D != D) return fail(ctx, BMND_EUNSUPPORTED, "batched jobs must share the number of non-singleton axes");
+  std::vector<size_t> base;
+  const size_t need = layout_jobs(plans, io, ctx->budget, base);
+  bmnd_status rc = ensure_arena(ctx, need, st);
+  if (rc != BMND_OK) return rc;
+  char *A = (char *)ctx->arena;
+  JobTables t;
+  build_tables(plans, io, pr, first_stage, last_stage, ext_pilot, A, base, t);
+  rc = stage_jobs(ctx, t.h, st);
+  if (rc != BMND_OK) return rc;
+  return record_launches(ctx, plans, t, A, base, first_stage, last_stage, ctx->djobs, ctx->counters, st);
 }
 
 }  // namespace
@@ -813,6 +874,88 @@ bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t 
                          void *stream) {
   return bmnd_denoise_ex(ctx, y, ndim, shape, noise, patch, step, search, group_size, stages,
                          mass_conserve, nullptr, out, stream);
+}
+
+bmnd_status bmnd_graph_create(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                              const int *patch, const int *step, const int *search, const int *group_size,
+                              int stages, int mass_conserve, const bmnd_params *params, float *out,
+                              bmnd_graph **graph) {
+  if (!ctx || !graph) return BMND_EINVAL;
+  *graph = nullptr;
+  ctx->err[0] = 0;
+  if (!y || !out) return fail(ctx, BMND_EINVAL, "null y or out");
+  if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  bmnd_status rc = check_noise(ctx, noise);
+  if (rc != BMND_OK) return rc;
+  if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
+  CU(cudaSetDevice(ctx->device));
+  std::vector<Plan> plans(1);
+  rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, plans[0]);
+  if (rc != BMND_OK) return rc;
+  const int64_t N = plans[0].g.N;
+  if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
+  JobIO io{y, out, noise, {group_size[0], stages == 2 ? group_size[1] : group_size[0]}, stages,
+           mass_conserve & (stages == 2 ? 3 : 1)};
+  std::vector<JobIO> ios{io};
+  std::vector<size_t> base;
+  const size_t need = layout_jobs(plans, ios, ctx->budget, base);
+  bmnd_graph *G = new bmnd_graph();
+  G->device = ctx->device;
+  if (cudaMalloc(&G->scratch, std::max<size_t>(need, 256)) != cudaSuccess ||
+      cudaMalloc(&G->dtab, 2 * sizeof(DJob)) != cudaSuccess || cudaMalloc(&G->counter, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    graph_release(G);
+    return fail(ctx, BMND_ENOMEM, "graph scratch of %zu bytes could not be allocated", need);
+  }
+  JobTables t;
+  build_tables(plans, ios, pr, 1, stages, nullptr, (char *)G->scratch, base, t);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaMemcpy(G->dtab, t.h.data(), 2 * sizeof(DJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (cs) cudaStreamDestroy(cs);
+    graph_release(G);
+    return fail(ctx, BMND_ECUDA, "graph set-up: %s", cudaGetErrorString(e));
+  }
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  rc = record_launches(ctx, plans, t, (char *)G->scratch, base, 1, stages, G->dtab, G->counter, cs);
+  ctx->profiling = prof;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  if (rc == BMND_OK && e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (rc != BMND_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    graph_release(G);
+    if (rc != BMND_OK) return rc;
+    return fail(ctx, BMND_ECUDA, "graph recording: %s", cudaGetErrorString(e));
+  }
+  *graph = G;
+  return BMND_OK;
+}
+
+bmnd_status bmnd_graph_launch(bmnd_graph *graph, void *stream) {
+  if (!graph || !graph->exec) return BMND_EINVAL;
+  if (cudaSetDevice(graph->device) != cudaSuccess ||
+      cudaGraphLaunch(graph->exec, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BMND_ECUDA;
+  }
+  return BMND_OK;
+}
+
+bmnd_status bmnd_graph_destroy(bmnd_graph *graph) {
+  if (!graph) return BMND_EINVAL;
+  cudaSetDevice(graph->device);
+  cudaDeviceSynchronize();
+  graph_release(graph);
+  return BMND_OK;
 }
 
 bmnd_status bmnd_stage(bmnd_ctx *ctx, const float *y, const float *pilot, int ndim,
