@@ -725,8 +725,27 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
         }
       }
     }
-    // merge this round's candidates into the running best list (one copy of
-    // the merge code: the candidates rotate through key[0] / idx[0])
+    // once the running list is full (finite threshold), each lane's
+    // candidates go in ascending (score, index) order (odd-even transposition
+    // network): rotation b then offers every lane's b-th best, and when no
+    // lane's next candidate beats the threshold none of its later ones can,
+    // so the round ends
+    const bool sorted = thr != FLT_MAX;  // warp-uniform
+    if (sorted) {
+#pragma unroll
+      for (int p = 0; p < KB; ++p) {
+#pragma unroll
+        for (int t = p & 1; t + 1 < KB; t += 2) {
+          const bool sw = kv_less(key[t + 1], idx[t + 1], key[t], idx[t]);
+          const float k0 = sw ? key[t + 1] : key[t], k1 = sw ? key[t] : key[t + 1];
+          const int i0 = sw ? idx[t + 1] : idx[t], i1 = sw ? idx[t] : idx[t + 1];
+          key[t] = k0; key[t + 1] = k1;
+          idx[t] = i0; idx[t + 1] = i1;
+        }
+      }
+    }
+    // merge into the running best list (one copy of the merge code: the
+    // candidates rotate through key[0] / idx[0])
 #pragma unroll 1
     for (int b = 0; b < KB; ++b) {
       bool offer = kv_less(key[0], idx[0], thr, thri);
@@ -737,6 +756,8 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
         warp_merge(lk, li, ok, oi, lane);
         thr = __shfl_sync(0xffffffffu, lk, g.M - 2 >= 0 ? g.M - 2 : 0);
         thri = __shfl_sync(0xffffffffu, li, g.M - 2 >= 0 ? g.M - 2 : 0);
+      } else if (sorted) {
+        break;
       }
 #pragma unroll
       for (int t = 0; t < KB - 1; ++t) { key[t] = key[t + 1]; idx[t] = idx[t + 1]; }
