@@ -371,6 +371,8 @@ def main():
 
     # algorithmic work per stage launch (outside any timing)
     flops = {1: 0.0, 2: 0.0}
+    mflops = {1: 0.0, 2: 0.0}
+    pilots = []
     for j, y in zip(jobs, ys):
         c = j.cfg
         o, _, cnt1 = ctx.bmnd_match(y, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1)
@@ -382,12 +384,32 @@ def main():
         pois = c["noise"][0] == "poisson"
         flops[1] += stage_flops(ncand, cnt1.cpu().numpy(), c["patch"], 1, pois)
         flops[2] += stage_flops(ncand, cnt2.cpu().numpy(), c["patch"], 2, pois)
+        P = int(np.prod(c["patch"]))
+        mflops[1] += float(np.sum(ncand - 1)) * P * (6.0 if pois else 3.0)
+        mflops[2] += float(np.sum(ncand - 1)) * P * 3.0
+        pilots.append(pilot)
         if c["mass_conserve"]:
             # the second sweep repeats the filtering (not the matching)
             pass
 
     for _ in range(args.warmup):
         step(ys, outs)
+    torch.cuda.synchronize()
+
+    # ---- matching alone: the match-only stage launches of bmnd_match ----
+    match_frac = {}
+    ctx.bmnd_set_profiling(True)
+    reps = max(1, min(20, 2048 // len(jobs)))
+    for s_ in (1, 2):
+        ctx.bmnd_kernel_stats(reset=True)
+        for _ in range(reps):
+            for j, y, pl in zip(jobs, ys, pilots):
+                c = j.cfg
+                ctx.bmnd_match(y if s_ == 1 else pl, c["noise"], c["patch"], c["step"], c["search"],
+                               c["group_size"][s_ - 1], s_)
+        n_m, ms_m = ctx.bmnd_kernel_stats(reset=True)["match"]
+        match_frac[s_] = (mflops[s_] * reps / (ms_m / 1e3) / 1e12) if ms_m > 0 else None
+    ctx.bmnd_set_profiling(False)
     torch.cuda.synchronize()
 
     # ---- device-resident timing ----
@@ -480,7 +502,13 @@ def main():
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median sampled SM clock)" % mhz,
                      "stage_kernel_ms_per_step": stage_ms / args.steps,
                      "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
-                     "share_of_step": stage_ms / step_ms_total if step_ms_total else None},
+                     "share_of_step": stage_ms / step_ms_total if step_ms_total else None,
+                     "matching_alone": {
+                         "note": "match-only launches (bmnd_match): SSD (+ Poisson bias in stage 1) and top-k "
+                                 "selection; algorithmic FLOPs of the scores only",
+                         "stage1_tflops": match_frac[1], "stage2_tflops": match_frac[2],
+                         "stage1_frac": match_frac[1] / peak if match_frac[1] else None,
+                         "stage2_frac": match_frac[2] / peak if match_frac[2] else None}},
     }
     if plain_ms is not None:
         line["plain"] = {"value": vox_step * args.steps / (plain_ms / 1e3), "unit": UNIT,

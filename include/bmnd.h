@@ -201,7 +201,9 @@ bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
  * milliseconds since the last reset (reset != 0 clears all totals after
  * reading).  Kinds: */
 enum { BMND_KERNEL_SCHEDULE = 0, BMND_KERNEL_STAGE1 = 1, BMND_KERNEL_STAGE2 = 2,
-       BMND_KERNEL_REDUCE = 3, BMND_KERNEL_MC_SWEEP = 4, BMND_KERNEL_KINDS = 5 };
+       BMND_KERNEL_REDUCE = 3, BMND_KERNEL_MC_SWEEP = 4,
+       BMND_KERNEL_MATCH = 5,  /* match-only stage launches of bmnd_match */
+       BMND_KERNEL_KINDS = 6 };
 bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable);
 bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches,
                               double *total_ms);

@@ -70,7 +70,7 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
            "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy"]
-KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4}
+KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
 

@@ -1033,6 +1033,7 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   CU(cudaGetLastError());
   if (do_match) {
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
+    ProfScope ps(ctx, BMND_KERNEL_MATCH, st);
     rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), stage == 2 ? 2 : 1, ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
     if (rc != BMND_OK) return rc;
   }

@@ -749,11 +749,28 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
 #pragma unroll 1
     for (int b = 0; b < KB; ++b) {
       bool offer = kv_less(key[0], idx[0], thr, thri);
-      if (__any_sync(0xffffffffu, offer)) {
-        float ok = offer ? key[0] : FLT_MAX;
-        int oi = offer ? idx[0] : INT_MAX;
-        warp_sort(ok, oi, lane);
-        warp_merge(lk, li, ok, oi, lane);
+      unsigned omask = __ballot_sync(0xffffffffu, offer);
+      if (omask) {
+        if (__popc(omask) <= 8) {
+          // few offers: insert them one at a time (the list keeps its 32
+          // smallest entries, as the merge does)
+          while (omask) {
+            const int src = __ffs(omask) - 1;
+            omask &= omask - 1;
+            const float ck = __shfl_sync(0xffffffffu, key[0], src);
+            const int ci = __shfl_sync(0xffffffffu, idx[0], src);
+            const int pos = __popc(__ballot_sync(0xffffffffu, kv_less(lk, li, ck, ci)));
+            const float uk = __shfl_up_sync(0xffffffffu, lk, 1);
+            const int ui = __shfl_up_sync(0xffffffffu, li, 1);
+            if (lane > pos) { lk = uk; li = ui; }
+            else if (lane == pos) { lk = ck; li = ci; }
+          }
+        } else {
+          float ok = offer ? key[0] : FLT_MAX;
+          int oi = offer ? idx[0] : INT_MAX;
+          warp_sort(ok, oi, lane);
+          warp_merge(lk, li, ok, oi, lane);
+        }
         thr = __shfl_sync(0xffffffffu, lk, g.M - 2 >= 0 ? g.M - 2 : 0);
         thri = __shfl_sync(0xffffffffu, li, g.M - 2 >= 0 ? g.M - 2 : 0);
       } else if (sorted) {
