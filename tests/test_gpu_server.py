@@ -92,3 +92,32 @@ def test_server_rejects_oversized_and_invalid():
                                                                search=(18,)))
     assert e.value.status == bm.EINVAL
     srv.close()
+
+
+def test_server_large_lane_equals_alone():
+    """Jobs estimated above a millisecond run in the large-job lane (one CTA
+    per tile, shortest first) beside the small-job lane; each result is still
+    bitwise the job alone."""
+    import paper_2609_34622_b300.bmnd as bm
+    rng = np.random.default_rng(83)
+    jobs = _jobs()[:6]
+    for i in range(2):
+        x = synth.texture_edge_image((512, 512), rng)
+        y, sp = synth.poisson_observe(x, 10.0, rng)
+        jobs.insert(2 * i, (y, dict(noise=("poisson", sp), patch=(8, 8), step=(3, 3), search=(39, 39),
+                                    group_size=(16, 32))))
+    lam = synth.ellipsoid_phantom((64, 64, 64), rng)
+    y, sp = synth.poisson_observe(lam / lam.max(), 3.0, rng)
+    jobs.append((y, dict(noise=("poisson", sp), patch=(4, 4, 4), step=(2, 2, 2), search=(11, 11, 11),
+                         group_size=(16, 32), mass_conserve=3)))
+    ctx = bm.Context(0)
+    alone = [_alone(ctx, y, c) for y, c in jobs]
+    srv = bm.Server(0, mem_budget=8 << 30, max_slots=32)
+    tickets = [srv.bmnd_server_submit(y, c) for y, c in jobs]
+    for k, t in enumerate(tickets):
+        out, _ = srv.bmnd_server_wait(t, 120000)
+        np.testing.assert_array_equal(out, alone[k])
+    st = srv.bmnd_server_get_stats()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    srv.close()
+    ctx.close()
