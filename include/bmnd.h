@@ -253,6 +253,26 @@ bmnd_status bmnd_server_get_stats(bmnd_server *srv, bmnd_server_stats *stats);
 /* Finish all submitted jobs, stop the worker and release everything. */
 bmnd_status bmnd_server_destroy(bmnd_server *srv);
 
+/* ---- Tile autotuning ------------------------------------------------------
+ * Times the computation of bmnd_denoise_ex on this array with several tile
+ * cores (the part of the array whose reference patches one CTA owns; the
+ * planner's choice, powers of two per axis for one or two axes, steps of one
+ * and two around the planner's choice for more) and keeps the fastest in the
+ * context, keyed by shape, patch, step, search, group sizes, stages, mass
+ * conservation and profile (not the noise level).  Later calls on this
+ * context with the same key -- bmnd_denoise, bmnd_denoise_ex, the batched
+ * and graph entry points -- plan with that core.  The paper has no
+ * counterpart: tiling is an execution choice and changes the output only by
+ * the order of floating-point additions.
+ *   - Synchronous: it runs each candidate three times on `stream` and waits.
+ *   - out receives the estimate with the chosen core.
+ *   - core (host int[ndim], may be NULL) receives the chosen core per axis
+ *     (1 for axes of length 1).
+ * Errors: those of bmnd_denoise_ex. */
+bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                          const int *patch, const int *step, const int *search, const int *group_size, int stages,
+                          int mass_conserve, const bmnd_params *params, float *out, void *stream, int *core);
+
 /* ---- Replayable graphs ----------------------------------------------------
  * The computation of bmnd_denoise_ex (both stages, Sec. 4-5 as for that call)
  * on one array, recorded once as a CUDA graph and replayed: for arrays that

@@ -69,7 +69,7 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
-           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy"]
+           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.bmnd_kernel_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double)]
     lib.bmnd_graph_create.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, P(vp)]
     lib.bmnd_graph_launch.argtypes = [vp, vp]
+    lib.bmnd_autotune.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp, ip]
     lib.bmnd_graph_destroy.argtypes = [vp]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
@@ -217,6 +218,22 @@ class Context:
                                        _ptr(out), _stream(stream))
         self._check(st)
         return out
+
+    def bmnd_autotune(self, y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,
+                      mass_conserve=0, prm: bmnd_params | None = None, stream=None):
+        """Time several tile cores on y and keep the fastest for this problem in
+        the context; returns the chosen core (one entry per axis)."""
+        _check_tensor(y, "y")
+        _check_tensor(out, "out")
+        shape = tuple(y.shape)
+        core = (ctypes.c_int * len(shape))()
+        st = self._lib.bmnd_autotune(self.handle, _ptr(y), len(shape), _ints(shape, ctypes.c_int64),
+                                     noise(noise_spec), _ints(patch), _ints(step), _ints(search),
+                                     _ints(group_size), int(stages), int(mass_conserve),
+                                     ctypes.byref(prm) if prm is not None else None, _ptr(out), _stream(stream),
+                                     core)
+        self._check(st)
+        return tuple(core)
 
     def bmnd_graph_create(self, y, out, noise_spec, patch, step, search, group_size=(16, 32), stages=2,
                           mass_conserve=0, prm: bmnd_params | None = None):

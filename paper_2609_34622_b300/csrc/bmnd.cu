@@ -11,7 +11,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 namespace bmnd {
@@ -51,6 +53,10 @@ struct bmnd_ctx {
   std::vector<cudaEvent_t> event_pool;
   int64_t k_launches[BMND_KERNEL_KINDS] = {0};
   double k_ms[BMND_KERNEL_KINDS] = {0};
+  // tile cores chosen by bmnd_autotune, per problem key; force_core
+  // overrides the planner while the tuner times a candidate
+  std::map<std::string, std::vector<int>> tuned;
+  const std::vector<int> *force_core = nullptr;
 };
 
 namespace {
@@ -244,6 +250,23 @@ void set_tiles(DGeom &g, const int *C) {
   for (int d = g.D - 1; d >= 0; --d) { g.rst[d] = s; s *= g.RG[d]; }
 }
 
+// Key of a problem for the tile tuner: everything the tiling depends on
+// (shape, patch, step, search, group sizes, stages, mass conservation and
+// the profile), not the noise level.
+std::string tune_key(int ndim, const int64_t *shape, const int *patch, const int *step, const int *search,
+                     const int *group_size, int stages, int mass_conserve, const bmnd_params &pr) {
+  std::string k;
+  char b[96];
+  for (int d = 0; d < ndim; ++d) {
+    snprintf(b, sizeof(b), "%lld/%d/%d/%d;", (long long)shape[d], patch[d], step[d], search[d]);
+    k += b;
+  }
+  snprintf(b, sizeof(b), "g%d,%d s%d m%d t%d sc%d p%d w%d,%d", group_size[0], stages == 2 ? group_size[1] : 0,
+           stages, mass_conserve, pr.group_transform, pr.schedule, pr.passes, pr.weight_model, pr.weight_scope);
+  k += b;
+  return k;
+}
+
 bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
                       const int *search, const int *group_size, int stages, int mass_conserve,
                       const bmnd_params &pr, Plan &pl) {
@@ -382,6 +405,31 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
       break;
     }
     C[big] = (C[big] + 1) / 2;
+  }
+  // a core chosen by bmnd_autotune for this problem (or forced while the
+  // tuner times it), if it fits
+  {
+    const std::vector<int> *core = ctx->force_core;
+    if (!core) {
+      auto it = ctx->tuned.find(tune_key(ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr));
+      if (it != ctx->tuned.end()) core = &it->second;
+    }
+    if (core && (int)core->size() == D) {
+      int T[KMAXD];
+      bool ok = true;
+      for (int a = 0; a < D; ++a) {
+        T[a] = (*core)[a];
+        ok = ok && T[a] >= 1 && T[a] <= g.ell[a] + 1;
+      }
+      if (ok) {
+        set_tiles(g, T);
+        if (stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem) {
+          for (int a = 0; a < D; ++a) C[a] = T[a];
+        } else {
+          set_tiles(g, C);
+        }
+      }
+    }
   }
   // enable the private footprint if it costs no resident CTA per SM
   if (pl.fp_candidate) {
@@ -874,6 +922,103 @@ bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t 
                          void *stream) {
   return bmnd_denoise_ex(ctx, y, ndim, shape, noise, patch, step, search, group_size, stages,
                          mass_conserve, nullptr, out, stream);
+}
+
+bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
+                          const int *patch, const int *step, const int *search, const int *group_size, int stages,
+                          int mass_conserve, const bmnd_params *params, float *out, void *stream, int *core) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (!y || !out) return fail(ctx, BMND_EINVAL, "null y or out");
+  if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  bmnd_status rc = check_noise(ctx, noise);
+  if (rc != BMND_OK) return rc;
+  if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
+  CU(cudaSetDevice(ctx->device));
+  const std::string key = tune_key(ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr);
+  ctx->tuned.erase(key);
+  std::vector<Plan> plans(1);
+  rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, plans[0]);
+  if (rc != BMND_OK) return rc;
+  const Plan &p0 = plans[0];
+  const int D = p0.D;
+  const int64_t N = p0.g.N;
+  if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
+  // candidates: the planner's core, powers of two per axis for one or two
+  // axes, steps of one and two around the planner's core for more
+  std::vector<std::vector<int>> cand;
+  auto add = [&](std::vector<int> c) {
+    for (int a = 0; a < D; ++a) c[a] = (int)std::max<int64_t>(1, std::min<int64_t>(c[a], p0.g.ell[a] + 1));
+    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+  };
+  std::vector<int> def(D);
+  for (int a = 0; a < D; ++a) def[a] = p0.g.C[a];
+  add(def);
+  if (D == 1) {
+    for (int v : {16, 32, 64, 128, 256, 512}) add({v});
+  } else if (D == 2) {
+    for (int v0 : {4, 8, 16, 32})
+      for (int v1 : {4, 8, 16, 32}) add({v0, v1});
+  } else {
+    for (int a = 0; a < D; ++a)
+      for (int dl : {-2, -1, 1, 2}) {
+        std::vector<int> c = def;
+        c[a] += dl;
+        if (c[a] >= 1) add(c);
+      }
+  }
+  const JobIO io{y, out, noise, {group_size[0], stages == 2 ? group_size[1] : group_size[0]}, stages,
+                 mass_conserve & (stages == 2 ? 3 : 1)};
+  const std::vector<JobIO> ios{io};
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  double best_ms = 1e30;
+  std::vector<int> best = def;
+  for (const std::vector<int> &c : cand) {
+    ctx->force_core = &c;
+    std::vector<Plan> pc(1);
+    rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, pc[0]);
+    if (rc != BMND_OK) break;
+    bool fits = true;
+    for (int a = 0; a < D; ++a) fits = fits && pc[0].g.C[a] == c[a];
+    if (!fits) continue;
+    // one untimed run, then two timed ones
+    rc = run_jobs(ctx, pc, ios, pr, 1, stages, nullptr, st);
+    if (rc != BMND_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == BMND_OK; ++r) rc = run_jobs(ctx, pc, ios, pr, 1, stages, nullptr, st);
+    if (rc != BMND_OK) break;
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(ctx, BMND_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  ctx->force_core = nullptr;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BMND_OK) return rc;
+  ctx->tuned[key] = best;
+  // the tuned estimate in out
+  std::vector<Plan> pf(1);
+  rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, pf[0]);
+  if (rc == BMND_OK) rc = run_jobs(ctx, pf, ios, pr, 1, stages, nullptr, st);
+  if (rc == BMND_OK && core) {
+    for (int d = 0; d < ndim; ++d) core[d] = 1;
+    for (int a = 0; a < D; ++a) core[pf[0].kax_of[a]] = pf[0].g.C[a];
+  }
+  return rc;
 }
 
 bmnd_status bmnd_graph_create(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
