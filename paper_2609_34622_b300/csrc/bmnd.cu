@@ -363,7 +363,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.Mmax = group_size[0];
   if (stages == 2) pl.Mmax = std::max(pl.Mmax, group_size[1]);
   // tile geometry: large cores within the shared-memory budget, enough tiles
-  static const int target[KMAXD + 1] = {0, 512, 32, 8, 4, 3, 2};
+  static const int target[KMAXD + 1] = {0, 64, 32, 8, 4, 3, 2};
   static const int minc[KMAXD + 1] = {0, 32, 8, 4, 2, 2, 1};
   int C[KMAXD];
   for (int a = 0; a < D; ++a) C[a] = (int)std::min<int64_t>(target[D], g.ell[a] + 1);
