@@ -38,8 +38,8 @@ constexpr int GEN_TOTAL = 11440;
 // scale12[2 log2 N] = sqrt(1/N), scale12[2 log2 N + 1] = sqrt(2/N), N = 1..32.
 cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
 
-// Bytes of one warp's shared block: member list, weights, plane sums and two
-// spare lists (5 x MMAX words), nbuf group buffers of M x MS floats (two for
+// Bytes of one warp's shared block: member list, weights, plane sums, the
+// members' footprint offsets and one spare list (5 x MMAX words), nbuf group buffers of M x MS floats (two for
 // filtering, one for a second mass-conservation sweep from the synthesis
 // cache), the private footprint (fp float2) and, when y and eta are read
 // from global memory (lean), the members' global origins (MMAX int64),
