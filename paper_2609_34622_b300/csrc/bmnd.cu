@@ -510,6 +510,7 @@ int pick_kb(const Plan &pl) {
   if (D == 1 && jL == 32) return 5;
   if (D == 1 && jL == 16) return 4;
   if (D == 2 && jL == 8) return 8;
+  if (D == 3 && jL == 4) return 11;
   return 4;
 }
 

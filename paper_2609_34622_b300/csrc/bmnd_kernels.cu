@@ -1892,7 +1892,7 @@ stage_fn select_stage_kernel(int D, int jL, int kb, int minb, int stage) {
       if (jL == 4 && kb == 4) return stage_ptr_st<2, 4, 4>(minb, stage);
       return stage_ptr<2, 0, 4>(minb);
     case 3:
-      if (jL == 4 && kb == 4) return stage_ptr_st<3, 4, 4>(minb, stage);
+      if (jL == 4 && kb == 11) return stage_ptr_st<3, 4, 11>(minb, stage);
       return stage_ptr<3, 0, 4>(minb);
     case 4: return stage_ptr<4, 0, 4>(minb);
     case 5: return stage_ptr<5, 0, 4>(minb);
