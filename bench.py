@@ -393,10 +393,11 @@ def main():
             # the second sweep repeats the filtering (not the matching)
             pass
 
-    # tile autotuning (outside any timing): one tuning per problem key (the
-    # arrays of a batch share theirs when shape and parameters agree)
+    # tile autotuning (outside any timing) for single-array workloads: it
+    # times one array alone on the whole GPU, which is not how the arrays of a
+    # batch run (they share the SMs), so a batch keeps the planner's tiles
     tuned = {}
-    if not args.no_autotune:
+    if not args.no_autotune and len(jobs) == 1:
         for j, y, o in zip(jobs, ys, outs):
             c = j.cfg
             key = (tuple(j.y.shape), tuple(c["patch"]), tuple(c["step"]), tuple(c["search"]),
