@@ -57,6 +57,11 @@ class _Params(ctypes.Structure):
         ("min_group", ctypes.c_int),
         ("weight_model", ctypes.c_int),
         ("weight_scope", ctypes.c_int),
+        ("match_metric", ctypes.c_int),
+        ("match_policy", ctypes.c_int),
+        ("match_t", ctypes.c_double),
+        ("beta_s", ctypes.c_double),
+        ("kappa_s", ctypes.c_double),
     ]
 
 
@@ -65,6 +70,9 @@ POWER_MODES = {"classic": 0, "noise_floor": 1, "variance_scaled": 2}
 GROUP_TRANSFORMS = {"haar": 0, "dct": 1}
 WEIGHT_MODELS = {"classic": 0, "variance": 1, "risk": 2}
 WEIGHT_SCOPES = {"patch": 0, "group": 1}
+METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
+POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
+NMAX = 4096  # moment tables cover pooled counts 0..NMAX (larger counts use NMAX)
 
 _lib = None
 
@@ -91,6 +99,16 @@ def _load():
         _lib.or_bessel_i0.argtypes = [ctypes.c_double]
         _lib.or_bessel_i0.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_anscombe.argtypes = [ctypes.c_double]
+        _lib.or_anscombe.restype = ctypes.c_double
+        _lib.or_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        _lib.or_phi.restype = ctypes.c_double
+        _lib.or_moments.argtypes = [ctypes.c_int, ctypes.c_int, d, d]
+        _lib.or_moment_table_f32.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_float), P(ctypes.c_float)]
+        _lib.or_log_f32.argtypes = [ctypes.c_float]
+        _lib.or_log_f32.restype = ctypes.c_float
+        _lib.or_phi_f32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_float]
+        _lib.or_phi_f32.restype = ctypes.c_float
     return _lib
 
 
@@ -135,6 +153,13 @@ def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 3
     p.min_group = kw.pop("min_group", 2)
     p.weight_model = WEIGHT_MODELS[kw.pop("weight_model", "variance")]
     p.weight_scope = WEIGHT_SCOPES[kw.pop("weight_scope", "patch")]
+    # stage-1 matching distance and acceptance policy (Secs. 4.2-4.3); the
+    # defaults are App. A's SSD, beta_s = 0.1 and kappa_s = 1 (Sec. 9.4), t = 3
+    p.match_metric = METRICS[kw.pop("match_metric", "ssd")]
+    p.match_policy = POLICIES[kw.pop("match_policy", "fixed")]
+    p.match_t = kw.pop("match_t", 3.0)
+    p.beta_s = kw.pop("beta_s", 0.1)
+    p.kappa_s = kw.pop("kappa_s", 1.0)
     if kw:
         raise TypeError("unknown oracle parameters: %s" % sorted(kw))
     return p
@@ -264,3 +289,41 @@ def bessel_i0(x: float) -> float:
 
 def num_threads() -> int:
     return _load().or_num_threads()
+
+
+# ---- Poisson-aware matching (Secs. 4.2-4.3) ----
+
+def anscombe(n: float) -> float:
+    """A(n) = 2 sqrt(n + 3/8)."""
+    return _load().or_anscombe(float(n))
+
+
+def phi(metric: str, r: float, c: float) -> float:
+    """FP64 per-entry contribution phi_m(r, c) of Eq. (varphi)."""
+    return _load().or_phi(METRICS[metric], float(r), float(c))
+
+
+def moments(metric: str, n: int):
+    """FP64 finite-count moments (mu_m(n), v_m(n)) (Prop. "Universal finite-count moments")."""
+    mu, v = ctypes.c_double(), ctypes.c_double()
+    _load().or_moments(METRICS[metric], int(n), ctypes.byref(mu), ctypes.byref(v))
+    return mu.value, v.value
+
+
+def moment_table_f32(metric: str, count: int = NMAX + 1):
+    """The float32 tables (mu, v) for n = 0..count-1 that the decisions read."""
+    mu = np.zeros(count, np.float32)
+    v = np.zeros(count, np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _load().or_moment_table_f32(METRICS[metric], int(count), mu.ctypes.data_as(fp), v.ctypes.data_as(fp))
+    return mu, v
+
+
+def log_f32(x: float) -> float:
+    """The single-precision logarithm of the decision path (artanh series)."""
+    return _load().or_log_f32(float(x))
+
+
+def phi_f32(metric: str, r: float, c: float) -> float:
+    """phi_m(r, c) in the single precision of the decision path."""
+    return _load().or_phi_f32(METRICS[metric], float(r), float(c))

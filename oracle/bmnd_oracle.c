@@ -40,6 +40,7 @@
  * left without a pin in the test suite, but the absolute PSNR of the whole
  * pipeline is only fixed by those pins, not by a printed worked example.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -77,6 +78,13 @@ typedef struct or_params {
     int min_group;         /* App. A: 2                                        */
     int weight_model;      /* 0 classic, 1 variance, 2 risk (Wiener only)      */
     int weight_scope;      /* 0 patch, 1 group                                 */
+    int match_metric;      /* stage-1 distance: 0 SSD, 1 Poisson deviance,     */
+                           /* 2 Pearson, 3 Anscombe-SSD (Sec. 4.2)             */
+    int match_policy;      /* 0 fixed, 1 reference finite-count,               */
+                           /* 2 candidate-standardized (Sec. 4.3)              */
+    double match_t;        /* threshold multiplier t                           */
+    double beta_s;         /* structural allowance beta_s (0.1 in App. B)      */
+    double kappa_s;        /* its intensity exponent kappa_s (1 in App. B)     */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -368,6 +376,217 @@ static void patch_offsets(const or_params *p, int64_t *off)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Poisson-aware matching distances (Sec. 4.2) and their finite-count        */
+/* calibration (Sec. 4.3)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Anscombe transform A(n) = 2 sqrt(n + 3/8) (Def. "Anscombe-SSD matching
+ * statistic"). */
+double or_anscombe(double n) { return 2.0 * sqrt(n + 0.375); }
+
+/* Per-entry contribution phi_m(r, c) of Eq. (varphi), in FP64, for metric
+ * m = 1 deviance (Eq. deviance, 0 log 0 = 0, zero total -> 0), 2 Pearson
+ * (Eq. pearson, zero total -> 0), 3 Anscombe-SSD (Eq. anscombe-distance).
+ * r and c are the raw counts of Eq. (raw-counts). */
+double or_phi(int metric, double r, double c)
+{
+    double n = r + c;
+    if (metric == 1) {
+        if (n <= 0.0) return 0.0;
+        double a = r > 0.0 ? r * log(2.0 * r / n) : 0.0;
+        double b = c > 0.0 ? c * log(2.0 * c / n) : 0.0;
+        return 2.0 * (a + b);
+    }
+    if (metric == 2) {
+        if (n <= 0.0) return 0.0;
+        return (r - c) * (r - c) / n;
+    }
+    double d = or_anscombe(c) - or_anscombe(r);
+    return 0.5 * d * d;
+}
+
+/* Prop. "Universal finite-count moments": mean and variance of phi_m(x, n-x)
+ * with x ~ Bin(n, 1/2) (Lemma "Conditional Poisson splitting"), the weights
+ * C(n, x) 2^-n taken from log-gamma.  n = 0 has the single allocation (0, 0)
+ * (mu = v = 0); at n = 1 both allocations give the same contribution, so
+ * v = 0 exactly and mu = phi_m(1, 0) (written out so that no rounding of the
+ * weights leaves a spurious variance).  READING: a variance that rounding
+ * makes negative is set to 0. */
+void or_moments(int metric, int n, double *mu, double *v)
+{
+    if (n <= 0) { *mu = 0.0; *v = 0.0; return; }
+    if (n == 1) { *mu = or_phi(metric, 1.0, 0.0); *v = 0.0; return; }
+    double m1 = 0.0, m2 = 0.0;
+    double lgn = lgamma((double)n + 1.0) - (double)n * log(2.0);
+    for (int x = 0; x <= n; ++x) {
+        double w = exp(lgn - lgamma((double)x + 1.0) - lgamma((double)(n - x) + 1.0));
+        double f = or_phi(metric, (double)x, (double)(n - x));
+        m1 += w * f;
+        m2 += w * f * f;
+    }
+    *mu = m1;
+    *v = pos(m2 - m1 * m1);
+}
+
+/* READING: the moment tables cover pooled counts n = 0..OR_NMAX; a (rounded)
+ * pooled count above OR_NMAX uses the moments at OR_NMAX. */
+#define OR_NMAX 4096
+
+static float or_mu_f[4][OR_NMAX + 1], or_v_f[4][OR_NMAX + 1];
+static int or_tab_ready[4];
+
+/* The single-precision tables the acceptance decisions read: the FP64
+ * moments rounded to float.  Built once per metric, outside parallel code. */
+void or_moment_tables(int metric)
+{
+    if (metric < 1 || metric > 3 || or_tab_ready[metric]) return;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int n = 0; n <= OR_NMAX; ++n) {
+        double mu, v;
+        or_moments(metric, n, &mu, &v);
+        or_mu_f[metric][n] = (float)mu;
+        or_v_f[metric][n] = (float)v;
+    }
+    or_tab_ready[metric] = 1;
+}
+
+/* Copies of the float tables (n = 0..count-1, count <= OR_NMAX + 1). */
+void or_moment_table_f32(int metric, int count, float *mu, float *v)
+{
+    or_moment_tables(metric);
+    for (int n = 0; n < count && n <= OR_NMAX; ++n) { mu[n] = or_mu_f[metric][n]; v[n] = or_v_f[metric][n]; }
+}
+
+/* READING: ranking and acceptance under a Poisson metric are integer
+ * decisions and are taken in single precision, with every operation below
+ * rounded once, in the order written (the file is built without
+ * floating-point contraction).  The logarithm is the artanh series
+ * ln x = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
+ * s = (m - 1) / (m + 1), after writing x = 2^e m with m in [1/sqrt 2, sqrt 2]
+ * (|s| <= 0.172, so the terms after s^9 are below 1e-9 relative), and
+ * e ln 2 added with ln 2 split into a 16-bit head and a float tail. */
+static float or_log_f(float x)
+{
+    int e = 0;
+    if (x < FLT_MIN) { x = x * 0x1p23f; e = -23; }
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    e += (int)((b >> 23) & 0xffu) - 127;
+    b = (b & 0x007fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &b, 4);
+    if (m > 0x1.6a09e6p+0f) { m = m * 0.5f; e += 1; }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float q = fmaf(s2, 0x1.c71c72p-3f, 0x1.24924ap-2f);   /* 2/9, 2/7 */
+    q = fmaf(s2, q, 0x1.99999ap-2f);                       /* 2/5 */
+    q = fmaf(s2, q, 0x1.555556p-1f);                       /* 2/3 */
+    q = fmaf(s2, q, 2.0f);
+    float lm = s * q;
+    float fe = (float)e;
+    return fmaf(fe, 0x1.62e4p-1f, fmaf(fe, 0x1.7f7d1cp-20f, lm));
+}
+
+/* phi_m(r, c) in single precision (same definitions as or_phi). */
+static float or_phi_f(int metric, float r, float c)
+{
+    float n = r + c;
+    if (metric == 1) {
+        if (!(n > 0.0f)) return 0.0f;
+        float a = r > 0.0f ? r * or_log_f((2.0f * r) / n) : 0.0f;
+        float b = c > 0.0f ? c * or_log_f((2.0f * c) / n) : 0.0f;
+        return 2.0f * (a + b);
+    }
+    if (metric == 2) {
+        if (!(n > 0.0f)) return 0.0f;
+        float d = r - c;
+        return (d * d) / n;
+    }
+    float d = 2.0f * sqrtf(c + 0.375f) - 2.0f * sqrtf(r + 0.375f);
+    return 0.5f * (d * d);
+}
+
+/* Exported for the tests: the single-precision log and contribution. */
+float or_log_f32(float x) { return or_log_f(x); }
+float or_phi_f32(int metric, float r, float c) { return or_phi_f(metric, r, c); }
+
+/* Table index of a pooled count: nearest integer (ties to even), capped. */
+static int or_count_index(float x)
+{
+    if (x > (float)OR_NMAX) x = (float)OR_NMAX;
+    return (int)rintf(x);
+}
+
+/* Eq. (raw-counts) in single precision: [p / s_P]_+ as p times the float
+ * reciprocal of s_P. */
+static float or_raw_count_f(double p, float inv_sp) { return fmaxf((float)p * inv_sp, 0.0f); }
+
+/* r-bar^kappa of Eq. (reference-threshold): the exponents of the paper's
+ * sensitivity grid (Sec. 9.4: 0.25, 0.5, 1, 2, 3, 4) by square roots and
+ * products, any other by powf. */
+static float or_pow_kappa(float x, double kappa)
+{
+    if (kappa == 1.0) return x;
+    if (kappa == 0.5) return sqrtf(x);
+    if (kappa == 0.25) return sqrtf(sqrtf(x));
+    if (kappa == 2.0) return x * x;
+    if (kappa == 3.0) return (x * x) * x;
+    if (kappa == 4.0) { float x2 = x * x; return x2 * x2; }
+    return powf(x, (float)kappa);
+}
+
+/* Acceptance threshold of one reference in sum units (P d_m), from the
+ * reference patch alone (entries pr[i], C order):
+ *   fixed:      P tau, tau = tau_ht if set, else the high-count null
+ *               1 + t sqrt(2 / P) (READING; Thm. "Common high-count limit":
+ *               mean 1 and variance 2 per entry);
+ *   reference:  P T_ref of Eq. (reference-threshold) = sum mu(2 r_i)
+ *               + t sqrt(sum v(2 r_i)) + beta_s P r-bar^kappa_s;
+ *   standardized: t (Def. "Candidate-standardized distance": Z < t). */
+static float or_metric_threshold(const or_params *p, const double *pr, const int64_t *off, int64_t P)
+{
+    if (p->match_policy == 0) {
+        double tau = p->tau_ht > 0.0 ? p->tau_ht : 1.0 + p->match_t * sqrt(2.0 / (double)P);
+        return (float)(tau * (double)P);
+    }
+    if (p->match_policy == 2) return (float)p->match_t;
+    int m = p->match_metric;
+    float inv = (float)(1.0 / p->s_p);
+    float msum = 0.0f, vsum = 0.0f, rsum = 0.0f;
+    for (int64_t i = 0; i < P; ++i) {
+        float r = or_raw_count_f(pr[off[i]], inv);
+        int n = or_count_index(2.0f * r);
+        msum = msum + or_mu_f[m][n];
+        vsum = vsum + or_v_f[m][n];
+        rsum = rsum + r;
+    }
+    float rbar = rsum / (float)P;
+    float allow = (float)(p->beta_s * (double)P) * or_pow_kappa(rbar, p->kappa_s);
+    return (msum + (float)p->match_t * sqrtf(vsum)) + allow;
+}
+
+/* Score of one candidate under a Poisson metric: P d_m (fixed and reference
+ * policies) or Z_m of Eq. (standardized-distance). */
+static float or_metric_score(const or_params *p, const double *pr, const double *pq, const int64_t *off,
+                             int64_t P)
+{
+    int m = p->match_metric;
+    float inv = (float)(1.0 / p->s_p);
+    float acc = 0.0f, msum = 0.0f, vsum = 0.0f;
+    for (int64_t i = 0; i < P; ++i) {
+        float r = or_raw_count_f(pr[off[i]], inv), c = or_raw_count_f(pq[off[i]], inv);
+        acc = acc + or_phi_f(m, r, c);
+        if (p->match_policy == 2) {
+            int n = or_count_index(r + c);
+            msum = msum + or_mu_f[m][n];
+            vsum = vsum + or_v_f[m][n];
+        }
+    }
+    if (p->match_policy != 2) return acc;
+    return vsum > 0.0f ? (acc - msum) / sqrtf(vsum) : 0.0f;
+}
+
 /* Match one reference patch.  Guide g is y in stage 1 and the stage-1
  * estimate in stage 2.  Candidates are the patch origins c with
  * |c_d - r_d| <= (w_d - 1)/2 and 0 <= c_d <= l_d (READING: candidates outside
@@ -400,6 +619,14 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
     patch_offsets(p, off);
     double gamma = stage == 1 ? p->gamma_ht : p->gamma_wie;
     double tau = resolve_tau(p, stage);
+    /* Poisson-aware matching applies to stage 1 (App. B: the Wiener stage
+     * keeps SSD on the pilot with a fixed threshold) */
+    int metric = stage == 1 ? p->match_metric : 0;
+    float taus = (float)tau;
+    if (metric) {
+        or_moment_tables(metric);
+        taus = or_metric_threshold(p, g + ref_lin, off, P);
+    }
     or_cand *cs = (or_cand *)malloc(sizeof(or_cand) * (size_t)ncand);
     int64_t nc = 0;
     for (int64_t t = 0; t < ncand; ++t) {
@@ -410,6 +637,12 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
             rem /= w;
         }
         if (lin == ref_lin) continue;
+        if (metric) {
+            cs[nc].score = or_metric_score(p, g + ref_lin, g + lin, off, P);
+            cs[nc].lin = lin;
+            ++nc;
+            continue;
+        }
         /* READING: the paper fixes no precision; the ranking is an integer
          * decision, so it is taken in single precision (the kernel's), with
          * the sum over patch entries in their C order and each squared
@@ -430,7 +663,6 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
         ++nc;
     }
     qsort(cs, (size_t)nc, sizeof(or_cand), cmp_cand);
-    float taus = (float)tau;
     int64_t nacc = 0;
     while (nacc < nc && (float)cs[nacc].score < taus) ++nacc;
     int64_t take = nacc < M - 1 ? nacc : M - 1;
@@ -619,6 +851,7 @@ int64_t or_stage(const or_params *p, const double *y, const double *pilot, int s
     int M = p->group_max[stage - 1];
     int mc = (p->mass_conserve >> (stage - 1)) & 1;
     const double *guide = stage == 1 ? y : pilot;
+    if (stage == 1) or_moment_tables(p->match_metric);  /* before any parallel region */
     int64_t R = or_schedule(p, NULL, 0);
     int64_t *refs = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
     or_schedule(p, refs, R);
@@ -701,6 +934,7 @@ int or_stage_points(const or_params *p, const double *y, const double *pilot, in
     int64_t P = prod_patch(p);
     int M = p->group_max[stage - 1];
     const double *guide = stage == 1 ? y : pilot;
+    if (stage == 1) or_moment_tables(p->match_metric);  /* before any parallel region */
     int64_t R = or_schedule(p, NULL, 0);
     int64_t *refs = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
     or_schedule(p, refs, R);
