@@ -163,14 +163,14 @@ def oracle_sample(name: str, jobs):
         "a 32^3 crop of the volume"
 
 
-def time_oracle(jobs, min_seconds: float, max_reps: int = 1000):
+def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd", "fixed")):
     import oracle
     oracle.build()
     vox, t0, reps = 0, time.perf_counter(), 0
     while True:
         for j in jobs:
             p = oracle.params(j.y.shape, j.patch, j.step, j.search, j.noise, j.group_size, j.stages,
-                              j.mass_conserve)
+                              j.mass_conserve, match_metric=matching[0], match_policy=matching[1])
             oracle.denoise(p, j.y)
             vox += j.y.size
         reps += 1
@@ -301,6 +301,11 @@ def main():
     ap.add_argument("--edge", type=int, default=128, help="volume edge of the 3-D workload (c4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's tiles")
+    ap.add_argument("--match-metric", default="ssd", choices=["ssd", "poisson_deviance", "pearson", "anscombe_ssd"],
+                    help="stage-1 matching distance (Sec. 4.2)")
+    ap.add_argument("--match-policy", default="fixed",
+                    choices=["fixed", "reference_finite_count", "candidate_standardized"],
+                    help="stage-1 acceptance policy (Sec. 4.3)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -315,11 +320,12 @@ def main():
         jobs, desc = workload(args.workload, 0, args.edge)
         sample, sdesc = oracle_sample(args.workload, jobs)
         vox = sum(j.y.size for j in sample)
+        matching = (args.match_metric, args.match_policy)
         for _ in range(args.warmup):
-            time_oracle(sample, 0.0, 1)
+            time_oracle(sample, 0.0, 1, matching)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            time_oracle(sample, 0.0, 1)
+            time_oracle(sample, 0.0, 1, matching)
         el = time.perf_counter() - t0
         import oracle
         val = vox * args.steps / el
@@ -361,14 +367,16 @@ def main():
     cfgs = [j.cfg for j in jobs]
     vox_step = sum(j.y.size for j in jobs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    pmetric = args.match_metric != "ssd"
+    prm = bm.params(match_metric=args.match_metric, match_policy=args.match_policy) if pmetric else None
 
     def step(yy, oo):
         if len(jobs) == 1:
             c = cfgs[0]
             ctx.bmnd_denoise(yy[0], oo[0], c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
-                             c["stages"], c["mass_conserve"], stream=stream)
+                             c["stages"], c["mass_conserve"], prm, stream=stream)
         else:
-            ctx.bmnd_denoise_batch(yy, oo, cfgs, stream=stream)
+            ctx.bmnd_denoise_batch(yy, oo, cfgs, prm, stream=stream)
 
     # algorithmic work per stage launch (outside any timing)
     flops = {1: 0.0, 2: 0.0}
@@ -376,10 +384,10 @@ def main():
     pilots = []
     for j, y in zip(jobs, ys):
         c = j.cfg
-        o, _, cnt1 = ctx.bmnd_match(y, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1)
+        o, _, cnt1 = ctx.bmnd_match(y, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1, prm)
         pilot = torch.empty_like(y)
         ctx.bmnd_stage(y, None, pilot, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1,
-                       c["mass_conserve"] & 1)
+                       c["mass_conserve"] & 1, prm)
         _, _, cnt2 = ctx.bmnd_match(pilot, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][1], 2)
         ncand = window_counts(o.cpu().numpy(), j.y.shape, c["patch"], c["search"])
         pois = c["noise"][0] == "poisson"
@@ -404,7 +412,8 @@ def main():
                    tuple(c["group_size"]), c["stages"], c["mass_conserve"])
             if key not in tuned:
                 tuned[key] = ctx.bmnd_autotune(y, o, c["noise"], c["patch"], c["step"], c["search"],
-                                               c["group_size"], c["stages"], c["mass_conserve"], stream=stream)
+                                               c["group_size"], c["stages"], c["mass_conserve"], prm,
+                                               stream=stream)
     torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -421,7 +430,7 @@ def main():
             for j, y, pl in zip(jobs, ys, pilots):
                 c = j.cfg
                 ctx.bmnd_match(y if s_ == 1 else pl, c["noise"], c["patch"], c["step"], c["search"],
-                               c["group_size"][s_ - 1], s_)
+                               c["group_size"][s_ - 1], s_, prm)
         n_m, ms_m = ctx.bmnd_kernel_stats(reset=True)["match"]
         match_frac[s_] = (mflops[s_] * reps / (ms_m / 1e3) / 1e12) if ms_m > 0 else None
     ctx.bmnd_set_profiling(False)
@@ -459,7 +468,7 @@ def main():
             evp[k][0].record(stream)
             for y, o, c in zip(ys, outs, cfgs):
                 ctx.bmnd_denoise(y, o, c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
-                                 c["stages"], c["mass_conserve"], stream=stream)
+                                 c["stages"], c["mass_conserve"], prm, stream=stream)
             evp[k][1].record(stream)
         torch.cuda.synchronize()
         plain_ms = sum(a.elapsed_time(b) for a, b in evp)
@@ -527,13 +536,23 @@ def main():
                          "stage1_frac": match_frac[1] / peak if match_frac[1] else None,
                          "stage2_frac": match_frac[2] / peak if match_frac[2] else None}},
     }
+    if pmetric:
+        # the FLOP model above is the SSD path's; the Poisson distances spend
+        # divisions, logarithms and square roots per entry pair that it does
+        # not count, so no fraction is claimed for them
+        line["config"]["matching"] = {"metric": args.match_metric, "policy": args.match_policy}
+        line["roofline"] = {"kernel": "k_stage (generic, Poisson distances)", "bound": "alu", "achieved": None,
+                            "peak": peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                            "stage_kernel_ms_per_step": stage_ms / args.steps,
+                            "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
+                            "share_of_step": stage_ms / step_ms_total if step_ms_total else None}
     if plain_ms is not None:
         line["plain"] = {"value": vox_step * args.steps / (plain_ms / 1e3), "unit": UNIT,
                          "ms_per_step": plain_ms / args.steps,
                          "path": "one bmnd_denoise call per array, same stream, same timing"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, sdesc = oracle_sample(args.workload, jobs)
-        v, el, reps, cores = time_oracle(sample, 10.0)
+        v, el, reps, cores = time_oracle(sample, 10.0, matching=(args.match_metric, args.match_policy))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%s, both stages, %d repetition(s), %.1f s" % (sdesc, reps, el)}
     if rank == 0:

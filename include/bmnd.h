@@ -65,6 +65,12 @@ enum { BMND_POWER_CLASSIC = 0, BMND_POWER_NOISE_FLOOR = 1, BMND_POWER_VARIANCE_S
 enum { BMND_GROUP_HAAR = 0, BMND_GROUP_DCT = 1 };
 enum { BMND_WEIGHT_CLASSIC = 0, BMND_WEIGHT_VARIANCE = 1, BMND_WEIGHT_RISK = 2 };
 enum { BMND_SCOPE_PATCH = 0, BMND_SCOPE_GROUP = 1 };
+/* Stage-1 matching distance (Sec. 4.2) and acceptance policy (Sec. 4.3). */
+enum { BMND_METRIC_SSD = 0, BMND_METRIC_DEVIANCE = 1, BMND_METRIC_PEARSON = 2, BMND_METRIC_ANSCOMBE = 3 };
+enum { BMND_POLICY_FIXED = 0, BMND_POLICY_REFERENCE = 1, BMND_POLICY_STANDARDIZED = 2 };
+/* The finite-count moment tables cover pooled counts 0..BMND_MOMENT_NMAX; a
+ * pooled count above it uses the moments at BMND_MOMENT_NMAX. */
+#define BMND_MOMENT_NMAX 4096
 
 /* Algorithm profile.  bmnd_default_params() fills the standard configuration
  * of App. A ("Standard Configuration"):
@@ -78,7 +84,31 @@ enum { BMND_SCOPE_PATCH = 0, BMND_SCOPE_GROUP = 1 };
  *     Sec. 4.1); power_mode classic (Def. "Pilot-power modes");
  *   group_transform Haar; min_group 2; weight_model variance, weight_scope
  *     patch (Defs. "Coefficient-domain hard-thresholding / Wiener weighting
- *     models"). */
+ *     models").
+ *   match_metric SSD (App. A); match_policy fixed; match_t 3.0; beta_s 0.1
+ *     and kappa_s 1.0 (Sec. 9.4).
+ *
+ * Poisson-aware stage-1 matching (Secs. 4.2-4.3; scaled-Poisson noise only,
+ * BMND_EINVAL otherwise).  With match_metric != SSD, stage 1 ranks the
+ * candidates of a reference p by one of the distances built from the raw
+ * counts r_i = [p_i / s_P]_+, c_i = [q_i / s_P]_+ (Eq. raw-counts):
+ * P d_m = sum_i phi_m(r_i, c_i) with phi the Poisson deviance (Eq. deviance),
+ * the Pearson statistic (Eq. pearson) or half the squared Anscombe difference
+ * (Eq. anscombe-distance); gamma_ht is not used.  Acceptance (then the group
+ * rules of App. A as for SSD):
+ *   fixed:        d_m < tau_ht, or, with tau_ht <= 0, d_m < 1 + t sqrt(2/P)
+ *                 (the high-count null, mean 1 and variance 2 per entry,
+ *                 Thm. "Common high-count limit");
+ *   reference:    d_m < T_ref(p; t) of Eq. (reference-threshold), with the
+ *                 exact moments mu_m, v_m of Prop. "Universal finite-count
+ *                 moments" at the pooled-count estimate 2 r_i rounded to the
+ *                 nearest integer, plus beta_s r-bar^kappa_s;
+ *   standardized: candidates ranked and accepted by Z_m < t of Eq.
+ *                 (standardized-distance), n_i = r_i + c_i rounded.
+ * Stage 2 keeps plain SSD on the pilot with tau_wie (App. B).  Scores and
+ * thresholds are formed in float32 with every operation rounded once (the
+ * logarithm by the artanh series), so that equal inputs give equal groups
+ * on every run. */
 typedef struct {
     double lambda_ht;
     double gamma_ht;
@@ -95,9 +125,23 @@ typedef struct {
     int min_group;
     int weight_model;
     int weight_scope;
+    int match_metric;
+    int match_policy;
+    double match_t;
+    double beta_s;
+    double kappa_s;
 } bmnd_params;
 
 void bmnd_default_params(bmnd_params *p);
+
+/* Finite-count null moments of a Poisson matching distance (Prop. "Universal
+ * finite-count moments"; Prop. "Exact Pearson moments" for Pearson): writes
+ * mu_m(n) and v_m(n), n = 0..count-1, rounded to float32, into the HOST
+ * arrays mu[count] and v[count] -- the tables stage-1 matching reads.
+ * metric is BMND_METRIC_DEVIANCE, _PEARSON or _ANSCOMBE; 1 <= count <=
+ * BMND_MOMENT_NMAX + 1.  Host computation only (no device, no context).
+ * Errors: BMND_EINVAL for a bad metric, count or null pointer. */
+bmnd_status bmnd_match_moments(int metric, int count, float *mu, float *v);
 
 /* Create a context on CUDA device `device`.  `scratch_budget_bytes` caps the
  * device scratch the context may hold (0 = no cap).  On success *ctx owns

@@ -24,6 +24,9 @@ POWER_MODES = {"classic": 0, "noise_floor": 1, "variance_scaled": 2}
 GROUP_TRANSFORMS = {"haar": 0, "dct": 1}
 WEIGHT_MODELS = {"classic": 0, "variance": 1, "risk": 2}
 WEIGHT_SCOPES = {"patch": 0, "group": 1}
+MATCH_METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
+MATCH_POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
+MOMENT_NMAX = 4096
 
 
 class BmndError(RuntimeError):
@@ -43,7 +46,9 @@ class bmnd_params(ctypes.Structure):
                 ("kaiser_beta", ctypes.c_double), ("shift_density", ctypes.c_double),
                 ("passes", ctypes.c_int), ("schedule", ctypes.c_int), ("power_mode", ctypes.c_int),
                 ("group_transform", ctypes.c_int), ("min_group", ctypes.c_int),
-                ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int)]
+                ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int),
+                ("match_metric", ctypes.c_int), ("match_policy", ctypes.c_int),
+                ("match_t", ctypes.c_double), ("beta_s", ctypes.c_double), ("kappa_s", ctypes.c_double)]
 
 
 class bmnd_job(ctypes.Structure):
@@ -69,7 +74,8 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
-           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune"]
+           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune",
+           "bmnd_match_moments"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
@@ -114,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.bmnd_graph_launch.argtypes = [vp, vp]
     lib.bmnd_autotune.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp, ip]
     lib.bmnd_graph_destroy.argtypes = [vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.bmnd_match_moments.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -131,12 +139,27 @@ def params(**kw) -> bmnd_params:
     p = bmnd_params()
     load().bmnd_default_params(ctypes.byref(p))
     maps = dict(schedule=SCHEDULES, power_mode=POWER_MODES, group_transform=GROUP_TRANSFORMS,
-                weight_model=WEIGHT_MODELS, weight_scope=WEIGHT_SCOPES)
+                weight_model=WEIGHT_MODELS, weight_scope=WEIGHT_SCOPES, match_metric=MATCH_METRICS,
+                match_policy=MATCH_POLICIES)
     for k, v in kw.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]
         setattr(p, k, v)
     return p
+
+
+def bmnd_match_moments(metric, count: int = MOMENT_NMAX + 1):
+    """Host-computed finite-count moment tables (mu, v), n = 0..count-1, of a
+    Poisson matching distance (name or BMND_METRIC_* value), as float32."""
+    import numpy as np
+    m = MATCH_METRICS[metric] if isinstance(metric, str) else int(metric)
+    mu = np.zeros(count, np.float32)
+    v = np.zeros(count, np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    rc = load().bmnd_match_moments(m, int(count), mu.ctypes.data_as(fp), v.ctypes.data_as(fp))
+    if rc != 0:
+        raise BmndError(rc, "bmnd_match_moments(%r, %d)" % (metric, count))
+    return mu, v
 
 
 def noise(spec) -> bmnd_noise:

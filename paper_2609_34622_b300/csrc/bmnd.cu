@@ -57,6 +57,9 @@ struct bmnd_ctx {
   // overrides the planner while the tuner times a candidate
   std::map<std::string, std::vector<int>> tuned;
   const std::vector<int> *force_core = nullptr;
+  // finite-count moment tables (mu, v) of the Poisson matching distances,
+  // n = 0..BMND_MOMENT_NMAX, built on first use
+  float2 *mom[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -166,6 +169,7 @@ struct Plan {
   int64_t nflags;
   int Mmax;
   int gtrans;            // group transform (Haar / DCT)
+  int metric;            // stage-1 matching distance (BMND_METRIC_*)
   int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
@@ -261,10 +265,70 @@ std::string tune_key(int ndim, const int64_t *shape, const int *patch, const int
     snprintf(b, sizeof(b), "%lld/%d/%d/%d;", (long long)shape[d], patch[d], step[d], search[d]);
     k += b;
   }
-  snprintf(b, sizeof(b), "g%d,%d s%d m%d t%d sc%d p%d w%d,%d", group_size[0], stages == 2 ? group_size[1] : 0,
-           stages, mass_conserve, pr.group_transform, pr.schedule, pr.passes, pr.weight_model, pr.weight_scope);
+  snprintf(b, sizeof(b), "g%d,%d s%d m%d t%d sc%d p%d w%d,%d d%d", group_size[0], stages == 2 ? group_size[1] : 0,
+           stages, mass_conserve, pr.group_transform, pr.schedule, pr.passes, pr.weight_model, pr.weight_scope,
+           pr.match_metric);
   k += b;
   return k;
+}
+
+// Per-entry contribution phi_m(r, c) of a Poisson matching distance
+// (Eq. varphi), double precision: deviance (0 log 0 = 0), Pearson and half
+// the squared Anscombe difference; a zero pooled count contributes 0.
+double contribution(int metric, double r, double c) {
+  const double n = r + c;
+  if (metric == BMND_METRIC_DEVIANCE) {
+    if (n <= 0) return 0.0;
+    return 2.0 * ((r > 0 ? r * std::log(2.0 * r / n) : 0.0) + (c > 0 ? c * std::log(2.0 * c / n) : 0.0));
+  }
+  if (metric == BMND_METRIC_PEARSON) return n > 0 ? (r - c) * (r - c) / n : 0.0;
+  const double d = 2.0 * std::sqrt(c + 0.375) - 2.0 * std::sqrt(r + 0.375);
+  return 0.5 * d * d;
+}
+
+// Finite-count null moments (Prop. "Universal finite-count moments") for
+// n = 0..count-1.  The Binomial(n, 1/2) weights of row n come from row n-1 by
+// Pascal's rule, w_n(x) = (w_{n-1}(x) + w_{n-1}(x-1)) / 2.  n = 0 has the
+// single allocation (0, 0); at n = 1 both allocations contribute equally, so
+// v = 0 exactly.  A variance that rounding makes negative becomes 0.
+void moment_table(int metric, int count, std::vector<float2> &out) {
+  out.assign(count, make_float2(0.f, 0.f));
+  std::vector<double> w(count + 1, 0.0);
+  w[0] = 1.0;
+  for (int n = 1; n < count; ++n) {
+    for (int x = n; x >= 1; --x) w[x] = 0.5 * (w[x] + w[x - 1]);
+    w[0] *= 0.5;
+    if (n == 1) {
+      out[1] = make_float2((float)contribution(metric, 1.0, 0.0), 0.f);
+      continue;
+    }
+    double m1 = 0, m2 = 0;
+    for (int x = 0; x <= n; ++x) {
+      if (w[x] == 0.0) continue;
+      const double f = contribution(metric, (double)x, (double)(n - x));
+      m1 += w[x] * f;
+      m2 += w[x] * f * f;
+    }
+    out[n] = make_float2((float)m1, (float)std::max(m2 - m1 * m1, 0.0));
+  }
+}
+
+bmnd_status ensure_moments(bmnd_ctx *ctx, int metric) {
+  if (ctx->mom[metric]) return BMND_OK;
+  std::vector<float2> h;
+  moment_table(metric, BMND_MOMENT_NMAX + 1, h);
+  float2 *d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BMND_ENOMEM, "cudaMalloc of the moment table failed");
+  }
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d);
+    return fail(ctx, BMND_ECUDA, "upload of the moment table failed");
+  }
+  ctx->mom[metric] = d;
+  return BMND_OK;
 }
 
 bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
@@ -301,6 +365,10 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   if (pr.weight_model < 0 || pr.weight_model > 2 || pr.weight_scope < 0 || pr.weight_scope > 1)
     return fail(ctx, BMND_EINVAL, "unknown weight model/scope");
   if (pr.power_mode < 0 || pr.power_mode > 2) return fail(ctx, BMND_EINVAL, "unknown power mode");
+  if (pr.match_metric < 0 || pr.match_metric > 3) return fail(ctx, BMND_EINVAL, "unknown matching distance");
+  if (pr.match_policy < 0 || pr.match_policy > 2) return fail(ctx, BMND_EINVAL, "unknown matching policy");
+  if (pr.match_metric != BMND_METRIC_SSD && (!(pr.match_t >= 0) || !(pr.beta_s >= 0) || !(pr.kappa_s > 0)))
+    return fail(ctx, BMND_EINVAL, "match_t and beta_s must be >= 0 and kappa_s > 0");
   if (!(pr.shift_density >= 0) || !(pr.s_v >= 0) || !(pr.lambda_ht >= 0))
     return fail(ctx, BMND_EINVAL, "negative shift_density, s_v or lambda_ht");
   // kernel axes: those with length > 1 (at least one)
@@ -337,6 +405,12 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   // shared memory on larger tiles
   g.lean = D >= 3 ? 1 : 0;
   pl.gtrans = pr.group_transform;
+  pl.metric = pr.match_metric;
+  if (pl.metric != BMND_METRIC_SSD) {
+    bmnd_status rc = ensure_moments(ctx, pl.metric);
+    if (rc != BMND_OK) return rc;
+    g.mom = ctx->mom[pl.metric];
+  }
   if (cube_side(D, g.j, pl.gtrans) && g.P <= 32) {
     // specialized kernels with members in registers: unpadded rows, odd
     // member stride (whole members and whole entry columns are read)
@@ -490,10 +564,28 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.poisson = nz.kind == BMND_NOISE_POISSON;
   double gamma = stage == 1 ? pr.gamma_ht : pr.gamma_wie;
   g.gamma = (float)gamma;
-  g.bias_on = g.poisson && gamma > 0;
+  // Poisson matching distances in stage 1 only (App. B: the Wiener stage
+  // matches the pilot by SSD with a fixed threshold)
+  g.metric = stage == 1 ? pr.match_metric : BMND_METRIC_SSD;
+  g.policy = pr.match_policy;
+  g.bias_on = g.poisson && gamma > 0 && g.metric == BMND_METRIC_SSD;
   double tau = stage == 1 ? pr.tau_ht : pr.tau_wie;
   if (tau <= 0) tau = (stage == 1 ? 3000.0 : 400.0) * g.P / (255.0 * 255.0);
   g.tau = (float)tau;
+  if (g.metric != BMND_METRIC_SSD) {
+    // thresholds in sum units, P d_m (fixed: tau_ht or the high-count null
+    // 1 + t sqrt(2 / P); standardized: t; reference: per reference patch)
+    if (g.policy == BMND_POLICY_FIXED) {
+      double tf = pr.tau_ht > 0 ? pr.tau_ht : 1.0 + pr.match_t * std::sqrt(2.0 / g.P);
+      g.tau = (float)(tf * g.P);
+    } else if (g.policy == BMND_POLICY_STANDARDIZED) {
+      g.tau = (float)pr.match_t;
+    }
+    g.mt = (float)pr.match_t;
+    g.beta_p = (float)(pr.beta_s * g.P);
+    g.kappa = (float)pr.kappa_s;
+    g.inv_sp = (float)(1.0 / nz.poisson_scale);
+  }
   g.lambda = (float)pr.lambda_ht;
   g.s_v = (float)pr.s_v;
   g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
@@ -503,6 +595,10 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
 
 // Patch side of the specialized stage kernel for a plan (0: generic).
 int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans); }
+
+// Kernel stage of a plan's stage s: 3 selects the stage-1 kernels with a
+// Poisson matching distance.
+int kernel_stage(int metric, int s) { return s == 1 && metric != BMND_METRIC_SSD ? 3 : s; }
 
 // Candidates per lane of the matching loop for the plan's stage kernel.
 int pick_kb(const Plan &pl) {
@@ -585,7 +681,7 @@ struct JobIO {
   int mass_conserve;
 };
 
-bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz) {
+bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz, const bmnd_params *pr = nullptr) {
   if (nz.kind == BMND_NOISE_GAUSSIAN) {
     if (!(nz.sigma >= 0)) return fail(ctx, BMND_EINVAL, "Gaussian sigma must be >= 0");
   } else if (nz.kind == BMND_NOISE_POISSON) {
@@ -593,6 +689,9 @@ bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz) {
   } else {
     return fail(ctx, BMND_EINVAL, "unknown noise kind %d", nz.kind);
   }
+  // the Poisson matching distances are defined on raw counts y / s_P
+  if (pr && pr->match_metric != BMND_METRIC_SSD && nz.kind != BMND_NOISE_POISSON)
+    return fail(ctx, BMND_EINVAL, "Poisson matching distances need the scaled-Poisson noise model");
   return BMND_OK;
 }
 
@@ -607,6 +706,7 @@ struct JobTables {
   int smax[2] = {0, 0}, smax2[2] = {0, 0};
   bool any_mc[2] = {false, false};
   int kjL = 0, kkb = 4;
+  int kmetric = 0;        // stage-1 matching distance shared by the jobs
 };
 
 void build_tables(const std::vector<Plan> &plans, const std::vector<JobIO> &io, const bmnd_params &pr,
@@ -657,6 +757,7 @@ void build_tables(const std::vector<Plan> &plans, const std::vector<JobIO> &io, 
   }
   t.kjL = kernel_jl(plans[0]);
   t.kkb = pick_kb(plans[0]);
+  t.kmetric = plans[0].metric;
   for (int i = 1; i < nj; ++i)
     if (kernel_jl(plans[i]) != t.kjL) { t.kjL = 0; t.kkb = 4; }
 }
@@ -686,7 +787,8 @@ bmnd_status record_launches(bmnd_ctx *ctx, const std::vector<Plan> &plans, const
     bmnd_status rc;
     {
       ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
-      rc = launch_stage(ctx, D, t.kjL, t.kkb, s, dj, nj, t.tiles, 0, t.smax[s - 1], st, counter);
+      rc = launch_stage(ctx, D, t.kjL, t.kkb, kernel_stage(t.kmetric, s), dj, nj, t.tiles, 0, t.smax[s - 1], st,
+                        counter);
     }
     if (rc != BMND_OK) return rc;
     {
@@ -697,7 +799,8 @@ bmnd_status record_launches(bmnd_ctx *ctx, const std::vector<Plan> &plans, const
     if (t.any_mc[s - 1]) {
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
-        rc = launch_stage(ctx, D, t.kjL, t.kkb, s, dj, nj, t.tiles, 2, t.smax2[s - 1], st, counter);
+        rc = launch_stage(ctx, D, t.kjL, t.kkb, kernel_stage(t.kmetric, s), dj, nj, t.tiles, 2, t.smax2[s - 1], st,
+                          counter);
       }
       if (rc != BMND_OK) return rc;
       {
@@ -795,6 +898,11 @@ void bmnd_default_params(bmnd_params *p) {
   p->min_group = 2;
   p->weight_model = BMND_WEIGHT_VARIANCE;
   p->weight_scope = BMND_SCOPE_PATCH;
+  p->match_metric = BMND_METRIC_SSD;
+  p->match_policy = BMND_POLICY_FIXED;
+  p->match_t = 3.0;
+  p->beta_s = 0.1;
+  p->kappa_s = 1.0;
 }
 
 bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {
@@ -887,11 +995,26 @@ bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   if (ctx->djobs) cudaFree(ctx->djobs);
   if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
   if (ctx->staged) cudaEventDestroy(ctx->staged);
+  for (auto m : ctx->mom)
+    if (m) cudaFree(m);
   delete ctx;
   return BMND_OK;
 }
 
 const char *bmnd_last_error(const bmnd_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+bmnd_status bmnd_match_moments(int metric, int count, float *mu, float *v) {
+  if (metric < BMND_METRIC_DEVIANCE || metric > BMND_METRIC_ANSCOMBE || count < 1 || count > BMND_MOMENT_NMAX + 1 ||
+      !mu || !v)
+    return BMND_EINVAL;
+  std::vector<float2> h;
+  moment_table(metric, count, h);
+  for (int n = 0; n < count; ++n) {
+    mu[n] = h[n].x;
+    v[n] = h[n].y;
+  }
+  return BMND_OK;
+}
 
 bmnd_status bmnd_denoise_ex(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape,
                             bmnd_noise noise, const int *patch, const int *step, const int *search,
@@ -903,7 +1026,7 @@ bmnd_status bmnd_denoise_ex(bmnd_ctx *ctx, const float *y, int ndim, const int64
   if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
   bmnd_params pr;
   if (params) pr = *params; else bmnd_default_params(&pr);
-  bmnd_status rc = check_noise(ctx, noise);
+  bmnd_status rc = check_noise(ctx, noise, &pr);
   if (rc != BMND_OK) return rc;
   if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
   CU(cudaSetDevice(ctx->device));
@@ -934,7 +1057,7 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
   if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
   bmnd_params pr;
   if (params) pr = *params; else bmnd_default_params(&pr);
-  bmnd_status rc = check_noise(ctx, noise);
+  bmnd_status rc = check_noise(ctx, noise, &pr);
   if (rc != BMND_OK) return rc;
   if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
   CU(cudaSetDevice(ctx->device));
@@ -1033,7 +1156,7 @@ bmnd_status bmnd_graph_create(bmnd_ctx *ctx, const float *y, int ndim, const int
   if (!group_size) return fail(ctx, BMND_EINVAL, "null group_size");
   bmnd_params pr;
   if (params) pr = *params; else bmnd_default_params(&pr);
-  bmnd_status rc = check_noise(ctx, noise);
+  bmnd_status rc = check_noise(ctx, noise, &pr);
   if (rc != BMND_OK) return rc;
   if (mass_conserve < 0 || mass_conserve > 3) return fail(ctx, BMND_EINVAL, "mass_conserve must be in [0, 3]");
   CU(cudaSetDevice(ctx->device));
@@ -1115,7 +1238,7 @@ bmnd_status bmnd_stage(bmnd_ctx *ctx, const float *y, const float *pilot, int nd
   if (stage == 2 && !pilot) return fail(ctx, BMND_EINVAL, "stage 2 needs a pilot");
   bmnd_params pr;
   if (params) pr = *params; else bmnd_default_params(&pr);
-  bmnd_status rc = check_noise(ctx, noise);
+  bmnd_status rc = check_noise(ctx, noise, &pr);
   if (rc != BMND_OK) return rc;
   CU(cudaSetDevice(ctx->device));
   int gs[2] = {group_max, group_max};
@@ -1144,7 +1267,7 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   bmnd_params pr;
   if (params) pr = *params; else bmnd_default_params(&pr);
   if (do_match) {
-    bmnd_status rc = check_noise(ctx, noise);
+    bmnd_status rc = check_noise(ctx, noise, &pr);
     if (rc != BMND_OK) return rc;
   }
   static const int ones[BMND_MAX_NDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
@@ -1180,7 +1303,8 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
   if (do_match) {
     int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
     ProfScope ps(ctx, BMND_KERNEL_MATCH, st);
-    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), stage == 2 ? 2 : 1, ctx->djobs, 1, pl.g.ntiles, 1, sm, st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), stage == 2 ? 2 : kernel_stage(pl.metric, 1), ctx->djobs,
+                      1, pl.g.ntiles, 1, sm, st);
     if (rc != BMND_OK) return rc;
   }
   std::vector<int> cnt(pl.g.ntiles);
@@ -1231,7 +1355,7 @@ bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
   for (int i = 0; i < n_jobs; ++i) {
     const bmnd_job &jb = jobs[i];
     if (!jb.y || !jb.out) return fail(ctx, BMND_EINVAL, "job %d: null y or out", i);
-    bmnd_status rc = check_noise(ctx, jb.noise);
+    bmnd_status rc = check_noise(ctx, jb.noise, &pr);
     if (rc != BMND_OK) return rc;
     if (jb.stages != stages) return fail(ctx, BMND_EUNSUPPORTED, "job %d: all jobs must use the same stage count", i);
     if (jb.mass_conserve < 0 || jb.mass_conserve > 3) return fail(ctx, BMND_EINVAL, "job %d: bad mass_conserve", i);

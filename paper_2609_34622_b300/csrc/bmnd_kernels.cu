@@ -567,6 +567,162 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
 }
 
 // ---------------------------------------------------------------------------
+// Poisson matching distances (Sec. 4.2) and their finite-count calibration
+// (Sec. 4.3).  Scores and thresholds are float32 with every operation rounded
+// once, in the order written (explicit intrinsics, no contraction), so the
+// groups they decide are the same on every run and build.
+// ---------------------------------------------------------------------------
+
+// ln x for x > 0 by the artanh series: x = 2^e m with m in [1/sqrt 2, sqrt 2],
+// s = (m - 1) / (m + 1) (|s| <= 0.172), ln m = 2 (s + s^3/3 + ... + s^9/9)
+// (the omitted terms are below 1e-9 relative), plus e ln 2 with ln 2 split
+// into a 16-bit head (e times it is exact) and a float tail.
+__device__ __forceinline__ float series_log(float x) {
+  int e = 0;
+  if (x < FLT_MIN) {
+    x = __fmul_rn(x, 0x1p23f);
+    e = -23;
+  }
+  const unsigned b = __float_as_uint(x);
+  e += (int)((b >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(m, 1.f), __fadd_rn(m, 1.f));
+  const float s2 = __fmul_rn(s, s);
+  float q = __fmaf_rn(s2, 0x1.c71c72p-3f, 0x1.24924ap-2f);  // 2/9, 2/7
+  q = __fmaf_rn(s2, q, 0x1.99999ap-2f);                      // 2/5
+  q = __fmaf_rn(s2, q, 0x1.555556p-1f);                      // 2/3
+  q = __fmaf_rn(s2, q, 2.f);
+  const float lm = __fmul_rn(s, q);
+  const float fe = (float)e;
+  return __fmaf_rn(fe, 0x1.62e4p-1f, __fmaf_rn(fe, 0x1.7f7d1cp-20f, lm));
+}
+
+// Per-entry contribution phi_m(r, c) of Eq. (varphi): 1 Poisson deviance
+// (Eq. deviance, 0 log 0 = 0), 2 Pearson (Eq. pearson), 3 half the squared
+// Anscombe difference (Eq. anscombe-distance); a zero total contributes 0.
+template <int METRIC>
+__device__ __forceinline__ float poisson_phi(float r, float c) {
+  const float n = __fadd_rn(r, c);
+  if (METRIC == 1) {
+    if (!(n > 0.f)) return 0.f;
+    const float a = r > 0.f ? __fmul_rn(r, series_log(__fdiv_rn(__fmul_rn(2.f, r), n))) : 0.f;
+    const float b = c > 0.f ? __fmul_rn(c, series_log(__fdiv_rn(__fmul_rn(2.f, c), n))) : 0.f;
+    return __fmul_rn(2.f, __fadd_rn(a, b));
+  } else if (METRIC == 2) {
+    if (!(n > 0.f)) return 0.f;
+    const float d = __fsub_rn(r, c);
+    return __fdiv_rn(__fmul_rn(d, d), n);
+  } else {
+    const float d = __fsub_rn(__fmul_rn(2.f, __fsqrt_rn(__fadd_rn(c, 0.375f))),
+                              __fmul_rn(2.f, __fsqrt_rn(__fadd_rn(r, 0.375f))));
+    return __fmul_rn(0.5f, __fmul_rn(d, d));
+  }
+}
+
+// Moment-table index of a pooled count: nearest integer (ties to even),
+// capped at MOMENT_NMAX.
+__device__ __forceinline__ int count_index(float x) { return (int)rintf(fminf(x, (float)MOMENT_NMAX)); }
+
+// Raw count [v / s_P]_+ of Eq. (raw-counts), as v times float(1 / s_P).
+__device__ __forceinline__ float raw_count(float v, float inv) { return fmaxf(__fmul_rn(v, inv), 0.f); }
+
+// x^kappa: the exponents of the paper's sensitivity grid (0.25, 0.5, 1, 2,
+// 3, 4) by square roots and products, any other by powf.
+__device__ __forceinline__ float pow_kappa(float x, float k) {
+  if (k == 1.f) return x;
+  if (k == 0.5f) return __fsqrt_rn(x);
+  if (k == 0.25f) return __fsqrt_rn(__fsqrt_rn(x));
+  if (k == 2.f) return __fmul_rn(x, x);
+  if (k == 3.f) return __fmul_rn(__fmul_rn(x, x), x);
+  if (k == 4.f) {
+    const float x2 = __fmul_rn(x, x);
+    return __fmul_rn(x2, x2);
+  }
+  return powf(x, k);
+}
+
+// Scores of the KB candidates q + b (b < KB, consecutive on the last axis)
+// against the reference p, both in the staged guide with patch rows at
+// rowoff: P d_m = sum_i phi_m(r_i, c_i) over the entries in C order, or,
+// standardized, Z_m of Eq. (standardized-distance) with the moments at
+// n_i = r_i + c_i (0 when their variances sum to 0).  The KB candidates are
+// interleaved for instruction-level parallelism; each one's sum keeps the
+// entry order.  Candidates past the window read the region's padding, as the
+// SSD loop does; their scores are discarded (every table index stays in
+// [0, MOMENT_NMAX] whatever they read).
+template <int METRIC, bool STD, int KB>
+__device__ __forceinline__ void metric_block(const DGeom &g, const float *p, const float *q, const int *rowoff,
+                                             float (&acc)[KB]) {
+  const float inv = g.inv_sp;
+  float ms[KB], vs[KB];
+#pragma unroll
+  for (int b = 0; b < KB; ++b) { acc[b] = 0.f; ms[b] = 0.f; vs[b] = 0.f; }
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = p + rowoff[r], *qr = q + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const float rv = raw_count(pr[i], inv);
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const float cv = raw_count(qr[i + b], inv);
+        acc[b] = __fadd_rn(acc[b], poisson_phi<METRIC>(rv, cv));
+        if (STD) {
+          const float2 mv = __ldg(&g.mom[count_index(__fadd_rn(rv, cv))]);
+          ms[b] = __fadd_rn(ms[b], mv.x);
+          vs[b] = __fadd_rn(vs[b], mv.y);
+        }
+      }
+    }
+  }
+  if (STD) {
+#pragma unroll
+    for (int b = 0; b < KB; ++b)
+      acc[b] = vs[b] > 0.f ? __fdiv_rn(__fsub_rn(acc[b], ms[b]), __fsqrt_rn(vs[b])) : 0.f;
+  }
+}
+
+template <int KB>
+__device__ __forceinline__ void metric_scores(const DGeom &g, const float *p, const float *q, const int *rowoff,
+                                              float (&acc)[KB]) {
+  const bool st = g.policy == 2;
+  switch (g.metric) {
+    case 1:
+      if (st) metric_block<1, true, KB>(g, p, q, rowoff, acc); else metric_block<1, false, KB>(g, p, q, rowoff, acc);
+      break;
+    case 2:
+      if (st) metric_block<2, true, KB>(g, p, q, rowoff, acc); else metric_block<2, false, KB>(g, p, q, rowoff, acc);
+      break;
+    default:
+      if (st) metric_block<3, true, KB>(g, p, q, rowoff, acc); else metric_block<3, false, KB>(g, p, q, rowoff, acc);
+      break;
+  }
+}
+
+// Reference finite-count threshold in sum units, P T_ref(p; t) of Eq.
+// (reference-threshold): sum_i mu_m(2 r_i) + t sqrt(sum_i v_m(2 r_i)) +
+// beta_s P r-bar^kappa_s, from the reference patch alone.
+__device__ __noinline__ float metric_threshold(const DGeom &g, const float *p, const int *rowoff) {
+  const float inv = g.inv_sp;
+  float ms = 0.f, vs = 0.f, rs = 0.f;
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = p + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const float rv = raw_count(pr[i], inv);
+      const float2 mv = __ldg(&g.mom[count_index(__fmul_rn(2.f, rv))]);
+      ms = __fadd_rn(ms, mv.x);
+      vs = __fadd_rn(vs, mv.y);
+      rs = __fadd_rn(rs, rv);
+    }
+  }
+  const float rbar = __fdiv_rn(rs, (float)g.P);
+  const float allow = __fmul_rn(g.beta_p, pow_kappa(rbar, g.kappa));
+  return __fadd_rn(__fadd_rn(ms, __fmul_rn(g.mt, __fsqrt_rn(vs))), allow);
+}
+
+// ---------------------------------------------------------------------------
 // block matching of one reference (Sec. 4.2 / 4.4, App. A group rules)
 // ---------------------------------------------------------------------------
 
@@ -600,7 +756,12 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
       ws *= W[d];
     }
   }
-  const float gam = g.gamma, tau = g.tau;
+  const float gam = g.gamma;
+  // Poisson matching distances in stage 1 (Secs. 4.2-4.3): the generic
+  // kernels, or the cubic-patch kernels instantiated with ST = 3
+  const bool pmetric = (JL == 0 || ST == 3) && ST != 2 && g.metric != 0;
+  float tau = g.tau;
+  if (pmetric && g.policy == 1) tau = metric_threshold(g, S + rbase, rowoff);
   const float gbias = g.poisson ? 0.f : __fmul_rn(__fmul_rn(2.f, (float)g.P), g.var_g);
   float lk = FLT_MAX;
   int li = INT_MAX;
@@ -634,7 +795,8 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
 #pragma unroll
       for (int b = 0; b < KB; ++b) { acc[b] = 0.f; bs[b] = 0.f; }
       const int jl = JL > 0 ? JL : g.jL;
-      for (int r = 0; r < g.rows; ++r) {
+      if (pmetric) metric_scores<KB>(g, S + rbase, S + cbase, rowoff, acc);
+      for (int r = 0; r < (pmetric ? 0 : g.rows); ++r) {
         const float *prow = S + rbase + rowoff[r];
         const float *qrow = S + cbase + rowoff[r];
         if (JL > 0) {
@@ -717,7 +879,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
         bool ok = b < kb && (widx0 + b) != ridx;
         // rounded exactly as written: no contraction of gam * B into the subtraction
         float B = g.poisson ? __fmul_rn(g.s_p, bs[b]) : gbias;
-        float sc = gam > 0.f ? __fsub_rn(acc[b], __fmul_rn(gam, B)) : acc[b];
+        float sc = gam > 0.f && !pmetric ? __fsub_rn(acc[b], __fmul_rn(gam, B)) : acc[b];
         if (ok) {
           key[b] = sc;
           idx[b] = widx0 + b;
@@ -1868,17 +2030,21 @@ typedef void (*stage_fn)(const DJob *, int, int, int, const float *, int *);
 template <int D, int JL, int KB, int ST = 0>
 stage_fn stage_ptr(int minb) { return minb >= 2 ? &k_stage<D, JL, KB, 2, ST> : &k_stage<D, JL, KB, 1, ST>; }
 
-// The cubic-patch kernels exist per stage (1 or 2), which keeps each
-// launch's code to the stage it runs; all jobs of such a launch share it.
+// The cubic-patch kernels exist per stage (1 or 2, and 3: stage 1 with a
+// Poisson matching distance), which keeps each launch's code to the stage it
+// runs -- the SSD kernels carry no Poisson code; all jobs of such a launch
+// share it.
 template <int D, int JL, int KB>
 stage_fn stage_ptr_st(int minb, int stage) {
-  return stage == 1 ? stage_ptr<D, JL, KB, 1>(minb) : stage_ptr<D, JL, KB, 2>(minb);
+  return stage == 1 ? stage_ptr<D, JL, KB, 1>(minb)
+                    : (stage == 2 ? stage_ptr<D, JL, KB, 2>(minb) : stage_ptr<D, JL, KB, 3>(minb));
 }
 
 // Stage kernel for a geometry: D kernel axes, jL > 0 the side of a cubic
 // patch (compile-time shape) or 0 for any shape, candidates per lane kb, the
-// stage of every job in the launch (1 or 2; the generic kernels read it from
-// each job), and the register budget: minb = 2 limits registers
+// stage of every job in the launch (1 or 2, 3 for stage 1 with a Poisson
+// matching distance; the generic kernels read both from each job), and the
+// register budget: minb = 2 limits registers
 // so that two CTAs share an SM (used when their shared memory fits), minb = 1
 // gives the kernel the whole register file.
 stage_fn select_stage_kernel(int D, int jL, int kb, int minb, int stage) {

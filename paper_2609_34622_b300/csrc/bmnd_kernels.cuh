@@ -86,7 +86,18 @@ struct DGeom {
   // reads y (stage 2) and eta (second mass-conservation sweep) from global
   // memory, which leaves room for larger tiles when D >= 3
   int lean;
+  // Poisson matching distance of this stage (0 SSD, 1 deviance, 2 Pearson,
+  // 3 Anscombe-SSD) and acceptance policy (0 fixed, 1 reference finite-count,
+  // 2 candidate-standardized); tau is then in sum units (P d_m) for the fixed
+  // policy and t for the standardized one.  mt = t, beta_p = beta_s P,
+  // kappa = kappa_s, inv_sp = float(1 / s_P); mom[n] = (mu_m(n), v_m(n)),
+  // n = 0..MOMENT_NMAX.  Only the generic (JL = 0) kernels read these.
+  int metric, policy;
+  float mt, beta_p, kappa, inv_sp;
+  const float2 *mom;
 };
+
+constexpr int MOMENT_NMAX = 4096;
 
 struct DJob {
   DGeom g;
