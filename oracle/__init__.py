@@ -62,6 +62,7 @@ class _Params(ctypes.Structure):
         ("match_t", ctypes.c_double),
         ("beta_s", ctypes.c_double),
         ("kappa_s", ctypes.c_double),
+        ("ht_rule", ctypes.c_int),
     ]
 
 
@@ -72,6 +73,7 @@ WEIGHT_MODELS = {"classic": 0, "variance": 1, "risk": 2}
 WEIGHT_SCOPES = {"patch": 0, "group": 1}
 METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
 POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
+HT_RULES = {"hard": 0, "soft": 1}
 NMAX = 4096  # moment tables cover pooled counts 0..NMAX (larger counts use NMAX)
 
 _lib = None
@@ -160,6 +162,8 @@ def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 3
     p.match_t = kw.pop("match_t", 3.0)
     p.beta_s = kw.pop("beta_s", 0.1)
     p.kappa_s = kw.pop("kappa_s", 1.0)
+    # stage-1 thresholding rule (Def. "Coefficient thresholding"; hard in App. A)
+    p.ht_rule = HT_RULES[kw.pop("ht_rule", "hard")]
     if kw:
         raise TypeError("unknown oracle parameters: %s" % sorted(kw))
     return p

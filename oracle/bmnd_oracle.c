@@ -85,6 +85,8 @@ typedef struct or_params {
     double match_t;        /* threshold multiplier t                           */
     double beta_s;         /* structural allowance beta_s (0.1 in App. B)      */
     double kappa_s;        /* its intensity exponent kappa_s (1 in App. B)     */
+    int ht_rule;           /* stage-1 rule: 0 hard (Eq. hard-threshold),       */
+                           /* 1 soft (Eq. soft-threshold)                      */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -730,13 +732,26 @@ static void filter_group(const or_params *p, int stage, const double *y,
         for (int l = 0; l < n; ++l)
             for (int64_t q = 0; q < P; ++q) {
                 int64_t k = l * P + q;
-                /* READING: count data make exact ties |Y_k| = lambda sigma_k
-                 * common; the strict inequality zeroes them.  To resolve them
-                 * that way in any floating-point precision, a coefficient is
-                 * kept only if it exceeds the threshold by a relative 1e-4. */
-                double a = fabs(Y[k]) > p->lambda_ht * sqrt(S2[k]) * (1.0 + 1e-4) ? 1.0 : 0.0;
+                double a;
+                if (p->ht_rule == 1) {
+                    /* Eq. (soft-threshold): C = sgn(Y) [|Y| - lambda sigma]_+,
+                     * i.e. attenuation a = [|Y| - lambda sigma]_+ / |Y|
+                     * (Y = 0 gives C = 0: a = 0); continuous at the
+                     * threshold, so it needs no tie guard */
+                    double ay = fabs(Y[k]), t = p->lambda_ht * sqrt(S2[k]);
+                    a = ay > t ? (ay - t) / ay : 0.0;
+                } else {
+                    /* READING: count data make exact ties |Y_k| = lambda
+                     * sigma_k common; the strict inequality zeroes them.  To
+                     * resolve them that way in any floating-point precision,
+                     * a coefficient is kept only if it exceeds the threshold
+                     * by a relative 1e-4. */
+                    a = fabs(Y[k]) > p->lambda_ht * sqrt(S2[k]) * (1.0 + 1e-4) ? 1.0 : 0.0;
+                }
                 G->C[k] = a * Y[k];
-                r[l] += p->weight_model == 0 ? a : a * S2[k];
+                /* Def. "Coefficient-domain hard-thresholding weighting
+                 * models": classic |a|^2, variance |a|^2 sigma^2 */
+                r[l] += p->weight_model == 0 ? a * a : a * a * S2[k];
             }
     } else {
         for (int m = 0; m < n; ++m)

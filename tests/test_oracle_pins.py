@@ -442,3 +442,77 @@ def test_wiener_risk_weight_minimum_risk(oracle):
     gam = _full_T(oracle, 4, patch) @ pilot.ravel()[np.array([[m + o for o in offs] for m in members]).ravel()]
     G = gam ** 2 / (gam ** 2 + sig ** 2)
     np.testing.assert_allclose(g["w"], 1.0 / np.sum(G * sig ** 2), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# soft thresholding (Def. "Coefficient thresholding", Eq. soft-threshold)
+# ---------------------------------------------------------------------------
+
+def _soft_params(oracle, noise, **kw):
+    return oracle.params((16, 16), (4, 4), (2, 2), (7, 7), noise, (8, 8), ht_rule="soft", **kw)
+
+
+def test_soft_threshold_coefficients(oracle):
+    """Eq. (soft-threshold): C_k = sgn(Y_k) [|Y_k| - lambda sigma_k]_+, written
+    here with numpy from the group's coefficients and variances."""
+    _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    p = _soft_params(oracle, ("poisson", 0.1))
+    y = rng.poisson(x / 0.1) * 0.1
+    g = oracle.filter_group(p, 1, y, None, members)
+    want = np.sign(g["Y"]) * np.maximum(np.abs(g["Y"]) - 3.0 * np.sqrt(g["var"]), 0.0)
+    np.testing.assert_allclose(g["C"], want, rtol=1e-13, atol=1e-15)
+    assert np.count_nonzero(g["C"]) > 0 and np.count_nonzero(g["C"]) < g["C"].size
+
+
+def test_soft_threshold_weights_are_synthesized_noise(oracle):
+    """Def. "Coefficient-domain hard-thresholding weighting models" with the
+    soft attenuation a_k = C_k / Y_k (variance model, patch scope, white
+    noise): R_j = sum_l |V_jl|^2 sum_q |a_lq|^2 sigma^2 equals the trace of the
+    noise covariance of synthesized patch j, U A sigma^2 I A U^T, full matrices."""
+    sig = 0.2
+    _, x, members, rng = _group_setup(oracle, ("gaussian", sig))
+    p = _soft_params(oracle, ("gaussian", sig))
+    y = x + rng.normal(0, sig, x.shape)
+    g = oracle.filter_group(p, 1, y, None, members)
+    Y, C = g["Y"].ravel(), g["C"].ravel()
+    a = np.where(Y != 0, C / np.where(Y != 0, Y, 1.0), 0.0)
+    assert np.any((a > 0) & (a < 1))
+    U = _full_T(oracle, 4, (4, 4)).T
+    cov = U @ np.diag(a) @ (sig ** 2 * np.eye(64)) @ np.diag(a) @ U.T
+    R = np.array([np.trace(cov[j * 16:(j + 1) * 16, j * 16:(j + 1) * 16]) for j in range(4)])
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-12)
+
+
+def test_soft_classic_group_weight(oracle):
+    """Classic group-scope surrogate under soft attenuation: R = sum_k |a_k|^2."""
+    _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    p = _soft_params(oracle, ("poisson", 0.1), weight_model="classic", weight_scope="group")
+    y = rng.poisson(x / 0.1) * 0.1
+    g = oracle.filter_group(p, 1, y, None, members)
+    Y, C = g["Y"].ravel(), g["C"].ravel()
+    a = np.where(Y != 0, C / np.where(Y != 0, Y, 1.0), 0.0)
+    np.testing.assert_allclose(g["w"], 1.0 / np.sum(a * a), rtol=1e-12)
+
+
+def test_soft_identity_at_zero_threshold(oracle):
+    """lambda_HT = 0: the soft rule keeps every coefficient unchanged, so the
+    first stage returns the observation (as the hard rule does)."""
+    rng = np.random.default_rng(5)
+    y = rng.uniform(0, 1, size=(24, 20))
+    p = oracle.params(y.shape, (4, 4), (2, 2), (7, 7), ("gaussian", 0.0), (8, 16), lambda_ht=0.0, ht_rule="soft")
+    out, pilot = oracle.denoise(p, y)
+    np.testing.assert_allclose(pilot, y, atol=1e-12)
+
+
+def test_soft_shrinks_at_least_as_much_as_hard(oracle):
+    """|C_soft| <= |C_hard| coefficient by coefficient, and they share their
+    zero set up to the hard rule's 1e-4 tie guard."""
+    _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    y = rng.poisson(x / 0.1) * 0.1
+    gh = oracle.filter_group(oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8)),
+                             1, y, None, members)
+    gs = oracle.filter_group(_soft_params(oracle, ("poisson", 0.1)), 1, y, None, members)
+    assert np.all(np.abs(gs["C"]) <= np.abs(gh["C"]) + 1e-15)
+    thr = 3.0 * np.sqrt(gh["var"])
+    clear = np.abs(np.abs(gh["Y"]) - thr) > 1e-3 * thr
+    np.testing.assert_array_equal((gs["C"] != 0)[clear], (gh["C"] != 0)[clear])
