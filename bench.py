@@ -163,14 +163,14 @@ def oracle_sample(name: str, jobs):
         "a 32^3 crop of the volume"
 
 
-def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd", "fixed")):
+def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd", "fixed"), ht_rule="hard"):
     import oracle
     oracle.build()
     vox, t0, reps = 0, time.perf_counter(), 0
     while True:
         for j in jobs:
             p = oracle.params(j.y.shape, j.patch, j.step, j.search, j.noise, j.group_size, j.stages,
-                              j.mass_conserve, match_metric=matching[0], match_policy=matching[1])
+                              j.mass_conserve, match_metric=matching[0], match_policy=matching[1], ht_rule=ht_rule)
             oracle.denoise(p, j.y)
             vox += j.y.size
         reps += 1
@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--match-policy", default="fixed",
                     choices=["fixed", "reference_finite_count", "candidate_standardized"],
                     help="stage-1 acceptance policy (Sec. 4.3)")
+    ap.add_argument("--ht-rule", default="hard", choices=["hard", "soft"],
+                    help="stage-1 thresholding rule (Def. \"Coefficient thresholding\")")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -322,10 +324,10 @@ def main():
         vox = sum(j.y.size for j in sample)
         matching = (args.match_metric, args.match_policy)
         for _ in range(args.warmup):
-            time_oracle(sample, 0.0, 1, matching)
+            time_oracle(sample, 0.0, 1, matching, args.ht_rule)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            time_oracle(sample, 0.0, 1, matching)
+            time_oracle(sample, 0.0, 1, matching, args.ht_rule)
         el = time.perf_counter() - t0
         import oracle
         val = vox * args.steps / el
@@ -368,7 +370,8 @@ def main():
     vox_step = sum(j.y.size for j in jobs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     pmetric = args.match_metric != "ssd"
-    prm = bm.params(match_metric=args.match_metric, match_policy=args.match_policy) if pmetric else None
+    prm = (bm.params(match_metric=args.match_metric, match_policy=args.match_policy, ht_rule=args.ht_rule)
+           if pmetric or args.ht_rule != "hard" else None)
 
     def step(yy, oo):
         if len(jobs) == 1:
@@ -536,6 +539,8 @@ def main():
                          "stage1_frac": match_frac[1] / peak if match_frac[1] else None,
                          "stage2_frac": match_frac[2] / peak if match_frac[2] else None}},
     }
+    if args.ht_rule != "hard":
+        line["config"]["ht_rule"] = args.ht_rule
     if pmetric:
         # the FLOP model above is the SSD path's; the Poisson distances spend
         # divisions, logarithms and square roots per entry pair that it does
@@ -552,7 +557,8 @@ def main():
                          "path": "one bmnd_denoise call per array, same stream, same timing"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, sdesc = oracle_sample(args.workload, jobs)
-        v, el, reps, cores = time_oracle(sample, 10.0, matching=(args.match_metric, args.match_policy))
+        v, el, reps, cores = time_oracle(sample, 10.0, matching=(args.match_metric, args.match_policy),
+                                         ht_rule=args.ht_rule)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%s, both stages, %d repetition(s), %.1f s" % (sdesc, reps, el)}
     if rank == 0:

@@ -68,6 +68,8 @@ enum { BMND_SCOPE_PATCH = 0, BMND_SCOPE_GROUP = 1 };
 /* Stage-1 matching distance (Sec. 4.2) and acceptance policy (Sec. 4.3). */
 enum { BMND_METRIC_SSD = 0, BMND_METRIC_DEVIANCE = 1, BMND_METRIC_PEARSON = 2, BMND_METRIC_ANSCOMBE = 3 };
 enum { BMND_POLICY_FIXED = 0, BMND_POLICY_REFERENCE = 1, BMND_POLICY_STANDARDIZED = 2 };
+/* Stage-1 thresholding rule (Def. "Coefficient thresholding"). */
+enum { BMND_HT_HARD = 0, BMND_HT_SOFT = 1 };
 /* The finite-count moment tables cover pooled counts 0..BMND_MOMENT_NMAX; a
  * pooled count above it uses the moments at BMND_MOMENT_NMAX. */
 #define BMND_MOMENT_NMAX 4096
@@ -86,7 +88,12 @@ enum { BMND_POLICY_FIXED = 0, BMND_POLICY_REFERENCE = 1, BMND_POLICY_STANDARDIZE
  *     patch (Defs. "Coefficient-domain hard-thresholding / Wiener weighting
  *     models").
  *   match_metric SSD (App. A); match_policy fixed; match_t 3.0; beta_s 0.1
- *     and kappa_s 1.0 (Sec. 9.4).
+ *     and kappa_s 1.0 (Sec. 9.4); ht_rule hard (App. A).
+ *
+ * ht_rule = BMND_HT_SOFT replaces the stage-1 hard threshold by the soft one
+ * of Eq. (soft-threshold), C_k = sgn(Y_k) [|Y_k| - lambda_ht sigma_k]_+: the
+ * attenuation a_k = C_k / Y_k then enters the hard-thresholding weighting
+ * models as |a_k|^2 (classic) or |a_k|^2 sigma_k^2 (variance).
  *
  * Poisson-aware stage-1 matching (Secs. 4.2-4.3; scaled-Poisson noise only,
  * BMND_EINVAL otherwise).  With match_metric != SSD, stage 1 ranks the
@@ -130,6 +137,7 @@ typedef struct {
     double match_t;
     double beta_s;
     double kappa_s;
+    int ht_rule;
 } bmnd_params;
 
 void bmnd_default_params(bmnd_params *p);

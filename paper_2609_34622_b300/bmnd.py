@@ -27,6 +27,7 @@ WEIGHT_SCOPES = {"patch": 0, "group": 1}
 MATCH_METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
 MATCH_POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
 MOMENT_NMAX = 4096
+HT_RULES = {"hard": 0, "soft": 1}
 
 
 class BmndError(RuntimeError):
@@ -48,7 +49,8 @@ class bmnd_params(ctypes.Structure):
                 ("group_transform", ctypes.c_int), ("min_group", ctypes.c_int),
                 ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int),
                 ("match_metric", ctypes.c_int), ("match_policy", ctypes.c_int),
-                ("match_t", ctypes.c_double), ("beta_s", ctypes.c_double), ("kappa_s", ctypes.c_double)]
+                ("match_t", ctypes.c_double), ("beta_s", ctypes.c_double), ("kappa_s", ctypes.c_double),
+                ("ht_rule", ctypes.c_int)]
 
 
 class bmnd_job(ctypes.Structure):
@@ -140,7 +142,7 @@ def params(**kw) -> bmnd_params:
     load().bmnd_default_params(ctypes.byref(p))
     maps = dict(schedule=SCHEDULES, power_mode=POWER_MODES, group_transform=GROUP_TRANSFORMS,
                 weight_model=WEIGHT_MODELS, weight_scope=WEIGHT_SCOPES, match_metric=MATCH_METRICS,
-                match_policy=MATCH_POLICIES)
+                match_policy=MATCH_POLICIES, ht_rule=HT_RULES)
     for k, v in kw.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]

@@ -365,6 +365,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   if (pr.weight_model < 0 || pr.weight_model > 2 || pr.weight_scope < 0 || pr.weight_scope > 1)
     return fail(ctx, BMND_EINVAL, "unknown weight model/scope");
   if (pr.power_mode < 0 || pr.power_mode > 2) return fail(ctx, BMND_EINVAL, "unknown power mode");
+  if (pr.ht_rule < 0 || pr.ht_rule > 1) return fail(ctx, BMND_EINVAL, "unknown thresholding rule");
   if (pr.match_metric < 0 || pr.match_metric > 3) return fail(ctx, BMND_EINVAL, "unknown matching distance");
   if (pr.match_policy < 0 || pr.match_policy > 2) return fail(ctx, BMND_EINVAL, "unknown matching policy");
   if (pr.match_metric != BMND_METRIC_SSD && (!(pr.match_t >= 0) || !(pr.beta_s >= 0) || !(pr.kappa_s > 0)))
@@ -587,6 +588,7 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
     g.inv_sp = (float)(1.0 / nz.poisson_scale);
   }
   g.lambda = (float)pr.lambda_ht;
+  g.soft = stage == 1 && pr.ht_rule == BMND_HT_SOFT;
   g.s_v = (float)pr.s_v;
   g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
   g.s_p = (float)(g.poisson ? nz.poisson_scale : 1.0);
@@ -903,6 +905,7 @@ void bmnd_default_params(bmnd_params *p) {
   p->match_t = 3.0;
   p->beta_s = 0.1;
   p->kappa_s = 1.0;
+  p->ht_rule = BMND_HT_HARD;
 }
 
 bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {

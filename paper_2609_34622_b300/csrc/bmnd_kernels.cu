@@ -1113,7 +1113,15 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         const float s2 = g.poisson ? bufA[a] : g.var_g;
         const float X = bufB[a];
         float wterm;
-        if (!stage2) {
+        if (!stage2 && g.soft) {
+          // Eq. (soft-threshold) as an attenuation att = [|X| - lambda
+          // sigma]_+ / |X|; weight terms |att|^2 (times sigma^2)
+          const float ax = fabsf(X);
+          const float t = g.lambda * sqrtf(s2);
+          const float att = ax > t ? (ax - t) / ax : 0.f;
+          bufB[a] = att * X;
+          wterm = att * att * (g.wmodel == 0 ? 1.f : s2);
+        } else if (!stage2) {
           // |X| > lambda sigma with a relative guard of 1e-4 (exact ties,
           // common with count data, are zeroed whatever the rounding)
           const bool keep = X * X > lam2 * s2;
@@ -1235,13 +1243,25 @@ __device__ __forceinline__ void col_hard_threshold(const DGeom &g, float *bufA, 
 #pragma unroll
     for (int m = 0; m < N; ++m) S[m] = g.var_g;
   }
+  if (g.soft) {
+    // Eq. (soft-threshold) as an attenuation att = [|X| - lambda sigma]_+ /
+    // |X|; weight terms |att|^2 (times sigma^2)
 #pragma unroll
-  for (int m = 0; m < N; ++m) {
-    // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
-    // with count data, are zeroed whatever the rounding)
-    const bool keep = X[m] * X[m] > lam2 * S[m];
-    bufA[m * MS + v] = keep ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
-    X[m] = keep ? X[m] : 0.f;
+    for (int m = 0; m < N; ++m) {
+      const float ax = fabsf(X[m]), t = g.lambda * sqrtf(S[m]);
+      const float att = ax > t ? (ax - t) / ax : 0.f;
+      bufA[m * MS + v] = att * att * (g.wmodel == 0 ? 1.f : S[m]);
+      X[m] = att * X[m];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
+      // with count data, are zeroed whatever the rounding)
+      const bool keep = X[m] * X[m] > lam2 * S[m];
+      bufA[m * MS + v] = keep ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
+      X[m] = keep ? X[m] : 0.f;
+    }
   }
   haar_inv_levels<N, 2>(X);
   col_store<N, MS>(bufB, v, X);

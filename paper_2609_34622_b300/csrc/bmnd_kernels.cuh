@@ -93,6 +93,7 @@ struct DGeom {
   // kappa = kappa_s, inv_sp = float(1 / s_P); mom[n] = (mu_m(n), v_m(n)),
   // n = 0..MOMENT_NMAX.  Only the generic (JL = 0) kernels read these.
   int metric, policy;
+  int soft;     // stage-1 soft thresholding (Eq. soft-threshold) instead of hard
   float mt, beta_p, kappa, inv_sp;
   const float2 *mom;
 };
