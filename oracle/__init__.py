@@ -63,6 +63,7 @@ class _Params(ctypes.Structure):
         ("beta_s", ctypes.c_double),
         ("kappa_s", ctypes.c_double),
         ("ht_rule", ctypes.c_int),
+        ("weight_domain", ctypes.c_int),
     ]
 
 
@@ -74,6 +75,7 @@ WEIGHT_SCOPES = {"patch": 0, "group": 1}
 METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
 POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
 HT_RULES = {"hard": 0, "soft": 1}
+WEIGHT_DOMAINS = {"coefficient": 0, "windowed_synthesis": 1}
 NMAX = 4096  # moment tables cover pooled counts 0..NMAX (larger counts use NMAX)
 
 _lib = None
@@ -164,6 +166,8 @@ def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 3
     p.kappa_s = kw.pop("kappa_s", 1.0)
     # stage-1 thresholding rule (Def. "Coefficient thresholding"; hard in App. A)
     p.ht_rule = HT_RULES[kw.pop("ht_rule", "hard")]
+    # aggregation-weight domain (Sec. 7; coefficient domain in App. A)
+    p.weight_domain = WEIGHT_DOMAINS[kw.pop("weight_domain", "coefficient")]
     if kw:
         raise TypeError("unknown oracle parameters: %s" % sorted(kw))
     return p

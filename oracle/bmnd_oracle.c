@@ -87,6 +87,8 @@ typedef struct or_params {
     double kappa_s;        /* its intensity exponent kappa_s (1 in App. B)     */
     int ht_rule;           /* stage-1 rule: 0 hard (Eq. hard-threshold),       */
                            /* 1 soft (Eq. soft-threshold)                      */
+    int weight_domain;     /* 0 coefficient domain, 1 windowed synthesized     */
+                           /* domain (Sec. 7.3), both stages                   */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -699,6 +701,41 @@ typedef struct {
     double w[64];   /* aggregation weights per patch                  */
 } or_group;
 
+/* Diagonal of the windowed synthesis metric (Def. "Windowed synthesis
+ * metrics", Eq. patch-synthesis-metric) for the separable group transform
+ * U = V (x) U_s, with V the group-axis inverse and U_s the spatial inverse
+ * (the Kronecker product of the axis DCT^T), and W_p the Kaiser window of
+ * the overlap-add: (H_{g,j})_{kk} = |V_jl|^2 omq[q] for k = (l, q), with
+ *   omq[q] = sum_p |(U_s)_pq|^2 w_p^2
+ * over the P entries p of a patch, written here as that full sum (the
+ * entries of U_s formed as products of the axis DCT entries). */
+static void synthesis_window_energy(const or_params *p, double *omq)
+{
+    int64_t P = prod_patch(p);
+    double C[OR_MAXD][1024], k1[OR_MAXD][256];
+    for (int d = 0; d < p->ndim; ++d) {
+        or_dct_matrix(p->patch[d], C[d]);
+        or_kaiser(p->patch[d], p->kaiser_beta, k1[d]);
+    }
+    for (int64_t q = 0; q < P; ++q) {
+        double e = 0.0;
+        for (int64_t i = 0; i < P; ++i) {
+            /* (U_s)_iq = prod_d DCT_d[q_d][i_d]; w_i = prod_d kaiser_d[i_d] */
+            int64_t ri = i, rq = q;
+            double u = 1.0, w = 1.0;
+            for (int d = p->ndim - 1; d >= 0; --d) {
+                int id = (int)(ri % p->patch[d]), qd = (int)(rq % p->patch[d]);
+                ri /= p->patch[d];
+                rq /= p->patch[d];
+                u *= C[d][qd * p->patch[d] + id];
+                w *= k1[d][id];
+            }
+            e += u * u * w * w;
+        }
+        omq[q] = e;
+    }
+}
+
 /* Filter one group.  stage 1: hard thresholding of Y = T y_g against
  * sigma_k from the variance map (Poisson: m_v = s_P [y]_+ with the plug-in
  * surrogate X^ = y, READING; Gaussian: sigma^2).  stage 2: Wiener shrinkage of
@@ -726,6 +763,14 @@ static void filter_group(const or_params *p, int stage, const double *y,
         }
     apply_T(&f, Y, 0, tmp);   /* Y = T y_g */
     apply_T(&f, S2, 2, tmp);  /* sigma_k^2 = sum_i T_ki^2 m_v(u_i) */
+    /* Def. "Windowed synthesized-domain weighting models" with diagonal F_g
+     * and noise model: tr(H F Sigma F^H) = sum_k H_kk |F_k|^2 sigma_k^2 (and
+     * the risk term likewise), so every coefficient's weight term takes the
+     * factor omq[q] of the metric's diagonal; the coefficient domain is
+     * omq = 1 (H = I) */
+    double omq[1024];
+    if (p->weight_domain == 1) synthesis_window_energy(p, omq);
+    else for (int64_t q = 0; q < P; ++q) omq[q] = 1.0;
     double r[64];
     for (int l = 0; l < n; ++l) r[l] = 0.0;
     if (stage == 1) {
@@ -751,7 +796,7 @@ static void filter_group(const or_params *p, int stage, const double *y,
                 G->C[k] = a * Y[k];
                 /* Def. "Coefficient-domain hard-thresholding weighting
                  * models": classic |a|^2, variance |a|^2 sigma^2 */
-                r[l] += p->weight_model == 0 ? a * a : a * a * S2[k];
+                r[l] += omq[q] * (p->weight_model == 0 ? a * a : a * a * S2[k]);
             }
     } else {
         for (int m = 0; m < n; ++m)
@@ -765,9 +810,9 @@ static void filter_group(const or_params *p, int stage, const double *y,
                 double den = S + p->s_v * S2[k];
                 double gain = den > 0.0 ? S / den : 0.0;   /* READING: 0/0 -> 0 */
                 G->C[k] = gain * Y[k];
-                if (p->weight_model == 0) r[l] += gain * gain;
-                else if (p->weight_model == 1) r[l] += gain * gain * S2[k];
-                else r[l] += gain * gain * S2[k] + (1.0 - gain) * (1.0 - gain) * S;
+                if (p->weight_model == 0) r[l] += omq[q] * (gain * gain);
+                else if (p->weight_model == 1) r[l] += omq[q] * (gain * gain * S2[k]);
+                else r[l] += omq[q] * (gain * gain * S2[k] + (1.0 - gain) * (1.0 - gain) * S);
             }
     }
     /* weights: patch scope R_j = sum_l |V_jl|^2 r_l with V the inverse of the

@@ -516,3 +516,89 @@ def test_soft_shrinks_at_least_as_much_as_hard(oracle):
     thr = 3.0 * np.sqrt(gh["var"])
     clear = np.abs(np.abs(gh["Y"]) - thr) > 1e-3 * thr
     np.testing.assert_array_equal((gs["C"] != 0)[clear], (gh["C"] != 0)[clear])
+
+
+# ---------------------------------------------------------------------------
+# windowed synthesized-domain weights (Sec. 7.3)
+# ---------------------------------------------------------------------------
+
+def _windowed_R(oracle, g, members, F, S2, extra=None, scope="patch"):
+    """tr(H F Sigma F^H) (+ extra) with H = U^H Q_j^H W_p^H W_p Q_j U built from
+    full matrices (Def. "Windowed synthesis metrics", Def. "Windowed
+    synthesized-domain weighting models"): U = T^T (scipy DCT, hand Haar),
+    W_p the Kaiser window (numpy, beta = 2)."""
+    n, P = 4, 16
+    U = _full_T(oracle, n, (4, 4)).T
+    w1 = np.kaiser(4, 2.0)
+    wp = np.outer(w1, w1).ravel()
+    M = np.diag(F) @ np.diag(S2) @ np.diag(F)
+    if extra is not None:
+        M = M + extra
+    R = []
+    for j in range(n):
+        Q = np.zeros((P, n * P))
+        Q[:, j * P:(j + 1) * P] = np.eye(P)
+        L = np.diag(wp) @ Q @ U
+        R.append(np.trace(L.T @ L @ M))
+    R = np.array(R)
+    return R if scope == "patch" else np.full(n, R.sum())
+
+
+@pytest.mark.parametrize("scope", ["patch", "group"])
+@pytest.mark.parametrize("rule", ["hard", "soft"])
+def test_windowed_ht_weights_full_matrices(oracle, scope, rule):
+    """Hard or soft thresholding, variance model: R = tr(H A Sigma A^H)."""
+    _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    p = oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8), ht_rule=rule,
+                      weight_domain="windowed_synthesis", weight_scope=scope)
+    y = rng.poisson(x / 0.1) * 0.1
+    g = oracle.filter_group(p, 1, y, None, members)
+    Y, C, S2 = g["Y"].ravel(), g["C"].ravel(), g["var"].ravel()
+    a = np.where(Y != 0, C / np.where(Y != 0, Y, 1.0), 0.0)
+    R = _windowed_R(oracle, g, members, a, S2, scope=scope)
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-11)
+
+
+@pytest.mark.parametrize("model", ["classic", "variance", "risk"])
+def test_windowed_wiener_weights_full_matrices(oracle, model):
+    """Wiener stage: classic tr(H D D^H), variance tr(H D Sigma D^H), risk adds
+    tr(H (D - I) diag(S) (D - I)^H) with S = [Gamma^2 - a sigma^2]_+ (classic
+    pilot power, a = 0)."""
+    sig = 0.15
+    shape = (16, 16)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.1, 1.0, size=shape)
+    y = x + rng.normal(0, sig, shape)
+    pilot = x + rng.normal(0, 0.05, shape)
+    p = oracle.params(shape, (4, 4), (2, 2), (7, 7), ("gaussian", sig), (8, 8), weight_model=model,
+                      weight_domain="windowed_synthesis")
+    members = np.array([np.ravel_multi_index(c, shape) for c in [(3, 3), (5, 4), (0, 9), (10, 2)]])
+    g = oracle.filter_group(p, 2, y, pilot, members)
+    offs = [np.ravel_multi_index((i, j), shape) for i in range(4) for j in range(4)]
+    T = _full_T(oracle, 4, (4, 4))
+    gam = T @ pilot.ravel()[np.array([[m + o for o in offs] for m in members]).ravel()]
+    s2 = np.full(64, sig ** 2)
+    S = np.maximum(gam ** 2, 0.0)
+    G = S / (S + 0.4 * s2)
+    np.testing.assert_allclose(g["C"].ravel(), G * g["Y"].ravel(), atol=1e-12)
+    if model == "classic":
+        R = _windowed_R(oracle, g, members, G, np.ones(64))
+    elif model == "variance":
+        R = _windowed_R(oracle, g, members, G, s2)
+    else:
+        R = _windowed_R(oracle, g, members, G, s2, extra=np.diag((G - 1) ** 2 * S))
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-11)
+
+
+def test_windowed_equals_coefficient_domain_with_flat_window(oracle):
+    """With a constant window (Kaiser beta = 0) and a unitary U, H = I and the
+    windowed models reduce to the coefficient-domain ones (the remark closing
+    Sec. 7.3)."""
+    _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
+    y = rng.poisson(x / 0.1) * 0.1
+    kw = dict(kaiser_beta=0.0)
+    pc = oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8), **kw)
+    pw = oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8),
+                       weight_domain="windowed_synthesis", **kw)
+    np.testing.assert_allclose(oracle.filter_group(pw, 1, y, None, members)["w"],
+                               oracle.filter_group(pc, 1, y, None, members)["w"], rtol=1e-12)
