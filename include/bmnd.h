@@ -70,6 +70,8 @@ enum { BMND_METRIC_SSD = 0, BMND_METRIC_DEVIANCE = 1, BMND_METRIC_PEARSON = 2, B
 enum { BMND_POLICY_FIXED = 0, BMND_POLICY_REFERENCE = 1, BMND_POLICY_STANDARDIZED = 2 };
 /* Stage-1 thresholding rule (Def. "Coefficient thresholding"). */
 enum { BMND_HT_HARD = 0, BMND_HT_SOFT = 1 };
+/* Aggregation-weight domain (Sec. 7.3). */
+enum { BMND_DOMAIN_COEFFICIENT = 0, BMND_DOMAIN_WINDOWED = 1 };
 /* The finite-count moment tables cover pooled counts 0..BMND_MOMENT_NMAX; a
  * pooled count above it uses the moments at BMND_MOMENT_NMAX. */
 #define BMND_MOMENT_NMAX 4096
@@ -88,7 +90,16 @@ enum { BMND_HT_HARD = 0, BMND_HT_SOFT = 1 };
  *     patch (Defs. "Coefficient-domain hard-thresholding / Wiener weighting
  *     models").
  *   match_metric SSD (App. A); match_policy fixed; match_t 3.0; beta_s 0.1
- *     and kappa_s 1.0 (Sec. 9.4); ht_rule hard (App. A).
+ *     and kappa_s 1.0 (Sec. 9.4); ht_rule hard (App. A); weight_domain
+ *     coefficient (App. A).
+ *
+ * weight_domain = BMND_DOMAIN_WINDOWED measures the weighting models of both
+ * stages in the windowed synthesized domain (Def. "Windowed synthesized-
+ * domain weighting models"): with the diagonal filters and noise model here,
+ * tr(H F Sigma F^H) weights each coefficient's term by the diagonal of the
+ * windowed synthesis metric H (Def. "Windowed synthesis metrics"), i.e. by
+ * sum_p |U_pq|^2 w_p^2 over the spatial inverse transform U and the Kaiser
+ * aggregation window w of a patch.
  *
  * ht_rule = BMND_HT_SOFT replaces the stage-1 hard threshold by the soft one
  * of Eq. (soft-threshold), C_k = sgn(Y_k) [|Y_k| - lambda_ht sigma_k]_+: the
@@ -138,6 +149,7 @@ typedef struct {
     double beta_s;
     double kappa_s;
     int ht_rule;
+    int weight_domain;
 } bmnd_params;
 
 void bmnd_default_params(bmnd_params *p);

@@ -366,6 +366,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     return fail(ctx, BMND_EINVAL, "unknown weight model/scope");
   if (pr.power_mode < 0 || pr.power_mode > 2) return fail(ctx, BMND_EINVAL, "unknown power mode");
   if (pr.ht_rule < 0 || pr.ht_rule > 1) return fail(ctx, BMND_EINVAL, "unknown thresholding rule");
+  if (pr.weight_domain < 0 || pr.weight_domain > 1) return fail(ctx, BMND_EINVAL, "unknown weight domain");
   if (pr.match_metric < 0 || pr.match_metric > 3) return fail(ctx, BMND_EINVAL, "unknown matching distance");
   if (pr.match_policy < 0 || pr.match_policy > 2) return fail(ctx, BMND_EINVAL, "unknown matching policy");
   if (pr.match_metric != BMND_METRIC_SSD && (!(pr.match_t >= 0) || !(pr.beta_s >= 0) || !(pr.kappa_s > 0)))
@@ -394,6 +395,19 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     g.ell[a] = shape[d] - patch[d];
     g.P *= patch[d];
     for (int i = 0; i < JMAX; ++i) g.kaiser[a][i] = i < patch[d] ? (float)kaiser_at(patch[d], i, pr.kaiser_beta) : 0.f;
+    // windowed synthesis metric factor of axis a (Def. "Windowed synthesis
+    // metrics"): sum_p DCT(q, p)^2 kaiser(p)^2 for the orthonormal DCT-II
+    const int J = patch[d];
+    for (int q = 0; q < JMAX; ++q) {
+      double e = 0.0;
+      if (q < J)
+        for (int i = 0; i < J; ++i) {
+          const double c = dct_entry(J, q, i);
+          const double k = kaiser_at(J, i, pr.kaiser_beta);
+          e += c * c * k * k;
+        }
+      g.wsyn[a][q] = (float)e;
+    }
   }
   {
     int64_t s = 1;
@@ -589,6 +603,7 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   }
   g.lambda = (float)pr.lambda_ht;
   g.soft = stage == 1 && pr.ht_rule == BMND_HT_SOFT;
+  g.wdomain = pr.weight_domain;
   g.s_v = (float)pr.s_v;
   g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
   g.s_p = (float)(g.poisson ? nz.poisson_scale : 1.0);
@@ -906,6 +921,7 @@ void bmnd_default_params(bmnd_params *p) {
   p->beta_s = 0.1;
   p->kappa_s = 1.0;
   p->ht_rule = BMND_HT_HARD;
+  p->weight_domain = BMND_DOMAIN_COEFFICIENT;
 }
 
 bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {

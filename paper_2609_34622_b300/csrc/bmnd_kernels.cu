@@ -973,6 +973,20 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
 // collaborative filtering of one group (Secs. 5-7)
 // ---------------------------------------------------------------------------
 
+// Diagonal factor of the windowed synthesis metric (Def. "Windowed synthesis
+// metrics") for spatial coefficient v, C order over the patch axes: the
+// separable product prod_d wsyn[d][q_d].
+__device__ __forceinline__ float syn_energy(const DGeom &g, int v) {
+  float e = 1.f;
+  for (int d = g.D - 1; d >= 0; --d) {
+    const int jd = g.j[d];
+    const int q = v % jd;
+    v /= jd;
+    e *= g.wsyn[d][q];
+  }
+  return e;
+}
+
 // Entries (m, v) of a group, m < n members, v < P patch entries, visited with
 // a lane stride of 32 and no integer division.
 #define BMND_FOR_ENTRIES(body)                         \
@@ -1135,6 +1149,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
           wterm = g.wmodel == 0 ? G * G
                                 : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
         }
+        if (g.wdomain) wterm *= syn_energy(g, v);
         bufA[a] = wterm;
       });
       __syncwarp();
@@ -1388,12 +1403,24 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
 #undef BMND_OP
   }
   __syncwarp();
-  // ---- r_l = sum_q (term) for every group-axis plane l; weights
+  // ---- r_l = sum_q (term) for every group-axis plane l (windowed
+  // synthesized domain: each term times the metric factor of its spatial
+  // coefficient, the per-axis product at compile-time coordinates); weights
   if (lane < n) {
     float r = 0.f;
     const float *row = bufA + lane * MS;
+    if (g.wdomain) {
 #pragma unroll
-    for (int v = 0; v < P; ++v) r += row[v];
+      for (int v = 0; v < P; ++v) {
+        float e = 1.f;
+#pragma unroll
+        for (int d = D - 1, rem = v; d >= 0; --d, rem /= JC) e *= g.wsyn[d][rem % JC];
+        r = fmaf(e, row[v], r);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < P; ++v) r += row[v];
+    }
     rr_s[lane] = r;
   }
   __syncwarp();

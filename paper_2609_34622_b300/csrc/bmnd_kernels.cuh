@@ -94,6 +94,11 @@ struct DGeom {
   // n = 0..MOMENT_NMAX.  Only the generic (JL = 0) kernels read these.
   int metric, policy;
   int soft;     // stage-1 soft thresholding (Eq. soft-threshold) instead of hard
+  // windowed synthesized-domain weights (Sec. 7.3): every coefficient's
+  // weight term takes prod_d wsyn[d][q_d], wsyn[d][q] = sum_p DCT_d(q, p)^2
+  // kaiser_d(p)^2 (the diagonal of the windowed synthesis metric)
+  int wdomain;
+  float wsyn[KMAXD][JMAX];
   float mt, beta_p, kappa, inv_sp;
   const float2 *mom;
 };
