@@ -103,6 +103,8 @@ def _load():
         _lib.or_bessel_i0.argtypes = [ctypes.c_double]
         _lib.or_bessel_i0.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_coverage.argtypes = [P(_Params), P(ctypes.c_int32), d]
+        _lib.or_coverage.restype = ctypes.c_int64
         _lib.or_anscombe.argtypes = [ctypes.c_double]
         _lib.or_anscombe.restype = ctypes.c_double
         _lib.or_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -191,6 +193,16 @@ def schedule(p: _Params) -> np.ndarray:
     out = np.empty(n, np.int64)
     lib.or_schedule(ctypes.byref(p), _iptr(out), n)
     return out
+
+
+def coverage(p: _Params):
+    """Reference coverage C(x) (Sec. 9.3) of the schedule p selects: returns
+    (C as an int32 array of the shape, number of references, CV(C))."""
+    shape = tuple(p.shape[a] for a in range(p.ndim))
+    cov = np.zeros(shape, np.int32)
+    cv = ctypes.c_double()
+    n = _load().or_coverage(ctypes.byref(p), cov.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(cv))
+    return cov, int(n), cv.value
 
 
 def match_ref(p: _Params, guide, stage: int, ref_lin: int):

@@ -380,6 +380,39 @@ static void patch_offsets(const or_params *p, int64_t *off)
     }
 }
 
+/* Reference coverage of a schedule (Sec. 9.3, "Shift Schedule Analysis"):
+ * C(x) = number of scheduled origins r with x in r + B (B the patch
+ * support), written into cov[prod(shape)] by a plain scatter over the
+ * references of or_schedule.  Returns the number of references and, in
+ * *cv, CV(C) = sigma_C / mu_C with the population standard deviation over
+ * all locations. */
+int64_t or_coverage(const or_params *p, int32_t *cov, double *cv)
+{
+    int64_t N = array_size(p), P = prod_patch(p);
+    int64_t R = or_schedule(p, NULL, 0);
+    int64_t *refs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(R > 0 ? R : 1));
+    or_schedule(p, refs, R);
+    int64_t st[OR_MAXD];
+    array_strides(p, st);
+    memset(cov, 0, sizeof(int32_t) * (size_t)N);
+    for (int64_t r = 0; r < R; ++r)
+        for (int64_t i = 0; i < P; ++i) {
+            int64_t rem = i, o = 0;
+            for (int d = p->ndim - 1; d >= 0; --d) {
+                o += (rem % p->patch[d]) * st[d];
+                rem /= p->patch[d];
+            }
+            cov[refs[r] + o] += 1;
+        }
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t x = 0; x < N; ++x) s1 += cov[x];
+    double mu = s1 / (double)N;
+    for (int64_t x = 0; x < N; ++x) s2 += (cov[x] - mu) * (cov[x] - mu);
+    *cv = mu > 0.0 ? sqrt(s2 / (double)N) / mu : 0.0;
+    free(refs);
+    return R;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Poisson-aware matching distances (Sec. 4.2) and their finite-count        */
 /* calibration (Sec. 4.3)                                                    */

@@ -602,3 +602,46 @@ def test_windowed_equals_coefficient_domain_with_flat_window(oracle):
                        weight_domain="windowed_synthesis", **kw)
     np.testing.assert_allclose(oracle.filter_group(pw, 1, y, None, members)["w"],
                                oracle.filter_group(pc, 1, y, None, members)["w"], rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# reference coverage of a schedule (Sec. 9.3, "Shift Schedule Analysis")
+# ---------------------------------------------------------------------------
+
+def test_coverage_off_schedule_by_hand(oracle):
+    """Def. "Off reference schedule" on 8 samples, patch 3, step 2: origins
+    0, 2, 4 and the appended l = 5; C(x) counted by hand."""
+    cov, n, cv = oracle.coverage(oracle.params((8,), (3,), (2,), (1,), schedule="off"))
+    assert n == 4
+    np.testing.assert_array_equal(cov, [1, 1, 2, 1, 2, 2, 2, 1])
+    assert cv == pytest.approx(1 / 3, rel=1e-15)
+
+
+def test_coverage_off_schedule_is_separable(oracle):
+    """The off schedule is the product of the per-axis lattices, so its 2-D
+    coverage is the outer product of the 1-D coverages."""
+    c2, n2, _ = oracle.coverage(oracle.params((23, 17), (5, 4), (3, 2), (1, 1), schedule="off"))
+    ca, na, _ = oracle.coverage(oracle.params((23,), (5,), (3,), (1,), schedule="off"))
+    cb, nb, _ = oracle.coverage(oracle.params((17,), (4,), (2,), (1,), schedule="off"))
+    assert n2 == na * nb
+    np.testing.assert_array_equal(c2, np.outer(ca, cb))
+
+
+@pytest.mark.parametrize("sched,rho,K", [("generated", 2.0, 2), ("balanced", 2.0, 2), ("sparse", 1.0, 1),
+                                         ("generated", 4.0, 1), ("balanced", 4.0, 2)])
+def test_coverage_counts_every_patch_once(oracle, sched, rho, K):
+    """Sum of C(x) = |R| P (each reference covers its P entries once); the
+    CV equals numpy's population std / mean of the map.  Two passes cover
+    every location; one pass with shifts wider than the step can leave a
+    gap before the clipped far origin l_d (Def. "Clipped reference origin"),
+    as it does here for rho = 4, K = 1 at one location."""
+    shape, patch = (41, 37), (8, 8)
+    p = oracle.params(shape, patch, (3, 3), (1, 1), schedule=sched, shift_density=rho, passes=K)
+    cov, n, cv = oracle.coverage(p)
+    assert n == len(oracle.schedule(p))
+    assert int(cov.sum()) == n * 64
+    assert cv == pytest.approx(cov.std() / cov.mean(), rel=1e-12)
+    if K == 2:
+        assert cov.min() >= 1
+    elif (sched, rho) == ("generated", 4.0):
+        assert np.argwhere(cov == 0).tolist() == [[32, 23]]
