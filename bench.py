@@ -204,6 +204,102 @@ def captured_traffic(workload: str):
     return int(m2.group(1))
 
 
+SCHEDULE_SHAPES = [(481, 321), (768, 512), (256, 256), (512, 512)]
+SCHEDULE_CONFIGS = [("off", 2.0, 1), ("generated", 0.0, 2), ("generated", 1.0, 2), ("generated", 2.0, 1),
+                    ("generated", 2.0, 2), ("generated", 4.0, 2), ("balanced", 2.0, 1), ("balanced", 2.0, 2),
+                    ("balanced", 4.0, 2), ("sparse", 2.0, 2)]
+
+
+def run_schedules(args, local: int, impl: str):
+    """Reference-count and coverage-uniformity analysis of the schedules
+    (Sec. 9.3) on image shapes of the paper's 2-D test sets (481x321,
+    768x512, 256x256, 512x512), 8x8 patches, step 3: per schedule (shift
+    density, passes), the mean count relative to the off schedule and the
+    median CV of the coverage map.  The official BM3D schedule the paper
+    normalizes by is not available, so counts are relative to the off
+    lattice.  One step = every configuration on every shape."""
+    def analyse_gpu(ctx, torch, dev):
+        import paper_2609_34622_b300.bmnd as bm
+        res = {}
+        for cfg in SCHEDULE_CONFIGS:
+            out = []
+            for sh in SCHEDULE_SHAPES:
+                prm = bm.params(schedule=cfg[0], shift_density=cfg[1], passes=cfg[2])
+                cov = torch.empty(sh, dtype=torch.int32, device=dev)
+                out.append(ctx.bmnd_coverage(sh, (8, 8), (3, 3), prm, coverage=cov))
+            res[cfg] = out
+        return res
+
+    def analyse_oracle():
+        import oracle
+        res = {}
+        for cfg in SCHEDULE_CONFIGS:
+            out = []
+            for sh in SCHEDULE_SHAPES:
+                p = oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule=cfg[0], shift_density=cfg[1], passes=cfg[2])
+                _, n, cv = oracle.coverage(p)
+                out.append((n, cv))
+            res[cfg] = out
+        return res
+
+    def table(res):
+        off = res[SCHEDULE_CONFIGS[0]]
+        return [{"schedule": c[0], "shift_density": c[1], "passes": c[2],
+                 "count_vs_off": float(np.mean([a[0] / b[0] for a, b in zip(res[c], off)])),
+                 "median_cv": float(np.median([a[1] for a in res[c]]))} for c in SCHEDULE_CONFIGS]
+
+    pix = sum(a * b for a, b in SCHEDULE_SHAPES) * len(SCHEDULE_CONFIGS)
+    desc = ("schedule analysis: %d schedules x %d shapes (%s), patch 8x8, step 3"
+            % (len(SCHEDULE_CONFIGS), len(SCHEDULE_SHAPES), ", ".join("%dx%d" % s for s in SCHEDULE_SHAPES)))
+    if impl == "reference":
+        for _ in range(args.warmup):
+            res = analyse_oracle()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = analyse_oracle()
+        el = time.perf_counter() - t0
+        import oracle
+        val = pix * args.steps / el
+        print(json.dumps({"metric": "coverage-analysed pixels/s", "value": val, "unit": "pixels/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                          "data": "synthetic", "impl": "reference", "config": {"workload": desc},
+                          "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": oracle.num_threads(),
+                                           "kind": "oracle", "sample": "the full analysis"},
+                          "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "table": table(res)}))
+        return
+    import torch
+    import paper_2609_34622_b300.bmnd as bm
+    from paper_2609_34622_b300 import build as B
+    B.build()
+    dev = torch.device("cuda", local)
+    ctx = bm.Context(local)
+    for _ in range(args.warmup):
+        res = analyse_gpu(ctx, torch, dev)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        res = analyse_gpu(ctx, torch, dev)
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    line = {"metric": "coverage-analysed pixels/s", "value": pix * args.steps / (ms / 1e3), "unit": "pixels/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "note": "each call synchronizes to return |R| and CV (analysis path, "
+                                                 "not the denoiser's hot path)"},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "gpu_launches": 2 * len(SCHEDULE_CONFIGS) * len(SCHEDULE_SHAPES) * args.steps,
+            "table": table(res)}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def run_c5(args, local: int):
     """Serving mix: 512 requests with Poisson-process arrivals at 200/s, served
     by the library's request server (memory-budgeted admission, continuous
@@ -297,7 +393,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "schedules"])
     ap.add_argument("--requests", type=int, default=512, help="serving mix size (c5)")
     ap.add_argument("--budget-gb", type=int, default=40, help="server memory budget (c5)")
     ap.add_argument("--edge", type=int, default=128, help="volume edge of the 3-D workload (c4)")
@@ -320,6 +416,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.workload == "schedules":
+        if rank == 0:
+            run_schedules(args, local, args.impl)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -234,6 +234,21 @@ bmnd_status bmnd_match(bmnd_ctx *ctx, const float *guide, int ndim, const int64_
                        int64_t *groups, int32_t *counts, int64_t cap, int64_t *n_refs,
                        void *stream);
 
+/* Reference coverage of the schedule params selects (Sec. 9.3, "Shift
+ * Schedule Analysis"): C(x), the number of scheduled reference patches that
+ * contain location x, for every x of an array of the given shape (patch,
+ * step and params->schedule / shift_density / passes as for bmnd_schedule).
+ *   coverage  DEVICE int32[prod(shape)], C-order, or NULL (map not written).
+ *   n_refs    HOST: number of distinct scheduled origins |R|.
+ *   cv        HOST: CV(C) = sigma_C / mu_C over all locations (population
+ *             standard deviation; 0 when mu_C = 0).
+ * Synchronizes `stream` to return n_refs and cv.  Errors: BMND_EINVAL for the
+ * shape / patch / step constraints of bmnd_denoise or null n_refs / cv,
+ * BMND_ENOMEM, BMND_ECUDA. */
+bmnd_status bmnd_coverage(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
+                          const bmnd_params *params, int32_t *coverage, int64_t *n_refs, double *cv,
+                          void *stream);
+
 /* One job of a batched call. */
 typedef struct {
     const float *y;

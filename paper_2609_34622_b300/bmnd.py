@@ -78,7 +78,7 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
            "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune",
-           "bmnd_match_moments"]
+           "bmnd_match_moments", "bmnd_coverage"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
@@ -125,6 +125,8 @@ def load(path: str = LIB_PATH):
     lib.bmnd_graph_destroy.argtypes = [vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.bmnd_match_moments.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp]
+    lib.bmnd_coverage.argtypes = [vp, ctypes.c_int, i64p, ip, ip, P(bmnd_params), vp, i64p,
+                                  ctypes.POINTER(ctypes.c_double), vp]
     for name in EXPORTS[1:]:
         if name != "bmnd_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -302,6 +304,23 @@ class Context:
                                      _ptr(origins), cap, ctypes.byref(n), _stream(stream))
         self._check(st)
         return origins[: n.value]
+
+    def bmnd_coverage(self, shape, patch, step, prm: bmnd_params | None = None, coverage=None, stream=None):
+        """Reference coverage of a schedule (Sec. 9.3): fills the int32 CUDA
+        tensor `coverage` (if given) with C(x) and returns (|R|, CV(C))."""
+        if coverage is not None:
+            import torch
+            if not (coverage.is_cuda and coverage.dtype == torch.int32 and coverage.is_contiguous()
+                    and coverage.numel() == int(np.prod(shape))):
+                raise ValueError("coverage must be a contiguous int32 CUDA tensor of prod(shape) elements")
+        n = ctypes.c_int64()
+        cv = ctypes.c_double()
+        st = self._lib.bmnd_coverage(self.handle, len(shape), _ints(shape, ctypes.c_int64), _ints(patch),
+                                     _ints(step), ctypes.byref(prm) if prm is not None else None,
+                                     _ptr(coverage) if coverage is not None else None, ctypes.byref(n),
+                                     ctypes.byref(cv), _stream(stream))
+        self._check(st)
+        return n.value, cv.value
 
     def bmnd_match(self, guide, noise_spec, patch, step, search, group_max, stage,
                    prm: bmnd_params | None = None, stream=None):

@@ -26,6 +26,9 @@ void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off,
 void launch_sched(const SGeom &s, unsigned char *flags, const DJob *jobs, int ntiles, int *ref_local,
                   int *ref_count, cudaStream_t st);
 void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t st);
+void launch_sched_mark(const SGeom &s, unsigned char *flags, cudaStream_t st);
+void launch_coverage(const CovGeom &c, const unsigned char *flags, int32_t *cov, unsigned long long *sums,
+                     cudaStream_t st);
 cudaError_t set_stage_smem(stage_fn f, int bytes);
 }  // namespace bmnd
 
@@ -1349,6 +1352,55 @@ bmnd_status bmnd_schedule(bmnd_ctx *ctx, int ndim, const int64_t *shape, const i
   bmnd_noise nz{BMND_NOISE_GAUSSIAN, 0.0, 1.0};
   return match_or_schedule(ctx, nullptr, ndim, shape, nz, patch, step, nullptr, 1, 1, params, origins,
                            nullptr, nullptr, cap, n_refs, stream, false);
+}
+
+bmnd_status bmnd_coverage(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
+                          const bmnd_params *params, int32_t *coverage, int64_t *n_refs, double *cv, void *stream) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (!n_refs || !cv) return fail(ctx, BMND_EINVAL, "null n_refs or cv");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  static const int ones[BMND_MAX_NDIM] = {1, 1, 1, 1, 1, 1, 1, 1};
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(cudaSetDevice(ctx->device));
+  int gs[2] = {1, 1};
+  Plan pl;
+  bmnd_status rc = make_plan(ctx, ndim, shape, patch, step, ones, gs, 1, 0, pr, pl);
+  if (rc != BMND_OK) return rc;
+  const size_t o_sums = al256(pl.o_flags + (size_t)pl.nflags);
+  rc = ensure_arena(ctx, o_sums + 3 * sizeof(unsigned long long), st);
+  if (rc != BMND_OK) return rc;
+  unsigned char *B = (unsigned char *)ctx->arena;
+  unsigned long long *sums = (unsigned long long *)(B + o_sums);
+  CovGeom c;
+  memset(&c, 0, sizeof(c));
+  c.D = pl.D;
+  c.P = pl.g.P;
+  c.N = pl.g.N;
+  c.nflags = pl.nflags;
+  for (int a = 0; a < pl.D; ++a) {
+    c.L[a] = pl.g.L[a];
+    c.ell[a] = pl.g.ell[a];
+    c.fst[a] = pl.s.fst[a];
+    c.j[a] = pl.g.j[a];
+  }
+  {
+    ProfScope ps(ctx, BMND_KERNEL_SCHEDULE, st);
+    CU(cudaMemsetAsync(B + pl.o_flags, 0, (size_t)pl.nflags, st));
+    CU(cudaMemsetAsync(sums, 0, 3 * sizeof(unsigned long long), st));
+    launch_sched_mark(pl.s, B + pl.o_flags, st);
+    launch_coverage(c, B + pl.o_flags, coverage, sums, st);
+    CU(cudaGetLastError());
+  }
+  unsigned long long h[3];
+  CU(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *n_refs = (int64_t)h[2];
+  const double mu = (double)h[0] / (double)c.N;
+  const double var = (double)h[1] / (double)c.N - mu * mu;
+  *cv = mu > 0 ? std::sqrt(std::max(var, 0.0)) / mu : 0.0;
+  return BMND_OK;
 }
 
 bmnd_status bmnd_match(bmnd_ctx *ctx, const float *guide, int ndim, const int64_t *shape,

@@ -68,6 +68,56 @@ __global__ void k_sched_mark(SGeom s, unsigned char *__restrict__ flags) {
   }
 }
 
+// Reference coverage (Sec. 9.3): one thread per location x (grid-stride),
+// C(x) = sum over the patch offsets o of flag[x - o] over the valid origins
+// x - o -- a gather over the schedule's byte grid, so the map needs no
+// atomics.  sums[0], sums[1], sums[2] accumulate sum C, sum C^2 and the
+// number of scheduled origins with integer atomics (order-independent).
+__global__ void k_coverage(CovGeom c, const unsigned char *__restrict__ flags, int32_t *__restrict__ cov,
+                           unsigned long long *__restrict__ sums) {
+  unsigned long long s1 = 0, s2 = 0, nr = 0;
+  const int64_t total = c.N > c.nflags ? c.N : c.nflags;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < c.N) {
+      int64_t x[KMAXD];
+      int64_t rem = t;
+      for (int a = c.D - 1; a >= 0; --a) {
+        x[a] = rem % c.L[a];
+        rem /= c.L[a];
+      }
+      int cnt = 0;
+      for (int i = 0; i < c.P; ++i) {
+        int ri = i;
+        int64_t idx = 0;
+        bool ok = true;
+        for (int a = c.D - 1; a >= 0; --a) {
+          const int o = ri % c.j[a];
+          ri /= c.j[a];
+          const int64_t r = x[a] - o;
+          ok = ok && r >= 0 && r <= c.ell[a];
+          idx += r * c.fst[a];
+        }
+        if (ok) cnt += flags[idx];
+      }
+      if (cov) cov[t] = cnt;
+      s1 += (unsigned long long)cnt;
+      s2 += (unsigned long long)cnt * (unsigned long long)cnt;
+    }
+    if (t < c.nflags) nr += flags[t];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    nr += __shfl_down_sync(0xffffffffu, nr, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], s1);
+    atomicAdd(&sums[1], s2);
+    atomicAdd(&sums[2], nr);
+  }
+}
+
 // One CTA per tile: compacts the marked origins of the tile's core box, in
 // C order, into the tile's reference list.
 __global__ void k_sched_compact(const DJob *__restrict__ jobs, int njobs, SGeom s,
@@ -2150,6 +2200,23 @@ void launch_sched(const SGeom &s, unsigned char *flags, const DJob *jobs, int nt
   if (grid < 1) grid = 1;
   k_sched_mark<<<grid, 256, 0, st>>>(s, flags);
   k_sched_compact<<<ntiles, 256, 0, st>>>(jobs, 1, s, flags, ref_local, ref_count);
+}
+
+void launch_sched_mark(const SGeom &s, unsigned char *flags, cudaStream_t st) {
+  int64_t total = s.nslots * s.passes;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 148 * 16) grid = 148 * 16;
+  if (grid < 1) grid = 1;
+  k_sched_mark<<<grid, 256, 0, st>>>(s, flags);
+}
+
+void launch_coverage(const CovGeom &c, const unsigned char *flags, int32_t *cov, unsigned long long *sums,
+                     cudaStream_t st) {
+  const int64_t total = c.N > c.nflags ? c.N : c.nflags;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 148 * 16) grid = 148 * 16;
+  if (grid < 1) grid = 1;
+  k_coverage<<<grid, 256, 0, st>>>(c, flags, cov, sums);
 }
 
 cudaError_t set_stage_smem(stage_fn f, int bytes) {

@@ -128,6 +128,16 @@ struct DJob {
   int64_t pcache_refs;
 };
 
+// Geometry of a reference-coverage map (Sec. 9.3) over the kernel axes:
+// array extents L, patch sides j, last valid origins ell and the strides fst
+// of the schedule's byte grid of origins (nflags bytes).
+struct CovGeom {
+  int D, P;
+  int64_t N, nflags;
+  int64_t L[KMAXD], ell[KMAXD], fst[KMAXD];
+  int j[KMAXD];
+};
+
 // Schedule geometry on the full (unsqueezed) shape.
 struct SGeom {
   int ndim;

@@ -645,3 +645,29 @@ def test_coverage_counts_every_patch_once(oracle, sched, rho, K):
         assert cov.min() >= 1
     elif (sched, rho) == ("generated", 4.0):
         assert np.argwhere(cov == 0).tolist() == [[32, 23]]
+
+
+def test_schedule_analysis_statements(oracle):
+    """Sec. 9.3 statements on 2-D shapes of the paper's test sets (8x8
+    patches, step 3): the sparse schedule generates the same origins as the
+    generated one when no axis is a singleton, and balanced (2, 2) has the
+    most uniform coverage (lowest CV) of the configurations compared; no
+    shifts (shift density 0) reduce to the off lattice."""
+    shapes = [(481, 321), (256, 256)]
+    def stats(sched, rho, K):
+        out = []
+        for sh in shapes:
+            p = oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule=sched, shift_density=rho, passes=K)
+            out.append(oracle.coverage(p)[1:])
+        return out
+    for sh in shapes:
+        g = oracle.schedule(oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule="generated"))
+        sp = oracle.schedule(oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule="sparse"))
+        np.testing.assert_array_equal(g, sp)
+        g0 = oracle.schedule(oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule="generated", shift_density=0.0))
+        off = oracle.schedule(oracle.params(sh, (8, 8), (3, 3), (1, 1), schedule="off"))
+        np.testing.assert_array_equal(g0, off)
+    cv = {c: np.median([s[1] for s in stats(*c)]) for c in
+          [("off", 2.0, 1), ("generated", 2.0, 2), ("generated", 1.0, 2), ("balanced", 2.0, 2), ("balanced", 4.0, 2),
+           ("balanced", 2.0, 1)]}
+    assert min(cv, key=cv.get) == ("balanced", 2.0, 2)
