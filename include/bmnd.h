@@ -371,6 +371,9 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
  *     stream, or order them).  A replay gives bitwise the output of
  *     bmnd_denoise_ex on the same input.
  *   - bmnd_graph_destroy waits for the device to be idle, then frees it.
+ *   - Replays read tables owned by the context (the DCT matrices, and the
+ *     finite-count moment tables of a Poisson matching distance): destroy
+ *     every graph of a context before the context.
  * Errors: those of bmnd_denoise_ex; BMND_ENOMEM / BMND_ECUDA when the scratch
  * cannot be allocated or the recording fails (bmnd_last_error of ctx says). */
 typedef struct bmnd_graph bmnd_graph;
