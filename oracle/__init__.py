@@ -64,6 +64,7 @@ class _Params(ctypes.Structure):
         ("kappa_s", ctypes.c_double),
         ("ht_rule", ctypes.c_int),
         ("weight_domain", ctypes.c_int),
+        ("cov_planes", ctypes.c_int),
     ]
 
 
@@ -170,6 +171,9 @@ def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 3
     p.ht_rule = HT_RULES[kw.pop("ht_rule", "hard")]
     # aggregation-weight domain (Sec. 7; coefficient domain in App. A)
     p.weight_domain = WEIGHT_DOMAINS[kw.pop("weight_domain", "coefficient")]
+    # leading group-axis planes with the shared-source variance (Sec. 5;
+    # App. A lists 4, the CUDA path implements 0 = the diagonal model)
+    p.cov_planes = int(kw.pop("cov_planes", 0))
     if kw:
         raise TypeError("unknown oracle parameters: %s" % sorted(kw))
     return p

@@ -89,6 +89,8 @@ typedef struct or_params {
                            /* 1 soft (Eq. soft-threshold)                      */
     int weight_domain;     /* 0 coefficient domain, 1 windowed synthesized     */
                            /* domain (Sec. 7.3), both stages                   */
+    int cov_planes;        /* k_ex: leading group-axis planes with the         */
+                           /* shared-source variance (Sec. 5; 0 = diagonal)    */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -769,6 +771,63 @@ static void synthesis_window_energy(const or_params *p, double *omq)
     }
 }
 
+typedef struct { int64_t u; int i; } or_src;
+
+static int cmp_src(const void *a, const void *b)
+{
+    const or_src *x = (const or_src *)a, *y = (const or_src *)b;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    return x->i - y->i;
+}
+
+/* Def. "Partial shared-source Poisson variance model" (Eq.
+ * partial-poisson-variance) for the coefficients k = (l, q) of the leading
+ * group-axis planes l < k_ex: sigma_k^2 = sum over the distinct source
+ * locations u of the group of |t_ku|^2 m_v(u), with the effective weights
+ * t_ku = sum of T_ki over the entries i taken from u (Def. "Effective
+ * transform weights"), T_ki = A0[l][m] prod_d DCT_d[q_d][p_d] for entry
+ * i = (member m, patch entry p).  mv[i] holds m_v(u_i).  READING: the
+ * "leading transform indices" are the first k_ex planes of the group-axis
+ * transform (App. A and B count exact covariance planes). */
+static void shared_source_variance(const or_params *p, const or_factors *f, int n, const int64_t *members,
+                                   const int64_t *off, const double *mv, double *S2)
+{
+    int64_t P = prod_patch(p), d = (int64_t)n * P;
+    int L = p->cov_planes < n ? p->cov_planes : n;
+    or_src *src = (or_src *)malloc(sizeof(or_src) * (size_t)d);
+    for (int m = 0; m < n; ++m)
+        for (int64_t q = 0; q < P; ++q) {
+            src[m * P + q].u = members[m] + off[q];
+            src[m * P + q].i = (int)(m * P + q);
+        }
+    qsort(src, (size_t)d, sizeof(or_src), cmp_src);
+    for (int l = 0; l < L; ++l)
+        for (int64_t q = 0; q < P; ++q) {
+            double sum = 0.0;
+            for (int64_t a = 0; a < d;) {
+                int64_t b = a;
+                double t = 0.0;
+                while (b < d && src[b].u == src[a].u) {
+                    int i = src[b].i, m = i / (int)P;
+                    int64_t pe = i % P, rp = pe, rq = q;
+                    double w = f->A[0][l * n + m];
+                    for (int dd = p->ndim - 1; dd >= 0; --dd) {
+                        int j = p->patch[dd];
+                        w *= f->A[1 + dd][(rq % j) * j + rp % j];
+                        rp /= j;
+                        rq /= j;
+                    }
+                    t += w;
+                    ++b;
+                }
+                sum += t * t * mv[src[a].i];
+                a = b;
+            }
+            S2[l * P + q] = sum;
+        }
+    free(src);
+}
+
 /* Filter one group.  stage 1: hard thresholding of Y = T y_g against
  * sigma_k from the variance map (Poisson: m_v = s_P [y]_+ with the plug-in
  * surrogate X^ = y, READING; Gaussian: sigma^2).  stage 2: Wiener shrinkage of
@@ -794,8 +853,12 @@ static void filter_group(const or_params *p, int stage, const double *y,
             else mv = p->sigma * p->sigma;
             S2[m * P + i] = mv;
         }
+    double *mv = (double *)malloc(sizeof(double) * (size_t)d);
+    memcpy(mv, S2, sizeof(double) * (size_t)d);
     apply_T(&f, Y, 0, tmp);   /* Y = T y_g */
     apply_T(&f, S2, 2, tmp);  /* sigma_k^2 = sum_i T_ki^2 m_v(u_i) */
+    if (p->cov_planes > 0) shared_source_variance(p, &f, n, G->members, off, mv, S2);
+    free(mv);
     /* Def. "Windowed synthesized-domain weighting models" with diagonal F_g
      * and noise model: tr(H F Sigma F^H) = sum_k H_kk |F_k|^2 sigma_k^2 (and
      * the risk term likewise), so every coefficient's weight term takes the
@@ -1113,7 +1176,11 @@ int or_filter_group(const or_params *p, int stage, const double *y, const double
                     var_out[m * P + i] = p->noise_kind == 1
                         ? p->s_p * pos(stage == 1 ? y[u] : pilot[u]) : p->sigma * p->sigma;
                 }
+            double *mv = (double *)malloc(sizeof(double) * (size_t)d);
+            memcpy(mv, var_out, sizeof(double) * (size_t)d);
             apply_T(&f, var_out, 2, tmp);
+            if (p->cov_planes > 0) shared_source_variance(p, &f, count, members, off, mv, var_out);
+            free(mv);
         }
         factors_free(&f);
     }

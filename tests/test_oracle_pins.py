@@ -671,3 +671,71 @@ def test_schedule_analysis_statements(oracle):
           [("off", 2.0, 1), ("generated", 2.0, 2), ("generated", 1.0, 2), ("balanced", 2.0, 2), ("balanced", 4.0, 2),
            ("balanced", 2.0, 1)]}
     assert min(cv, key=cv.get) == ("balanced", 2.0, 2)
+
+
+# ---------------------------------------------------------------------------
+# partial shared-source variance (Sec. 5, Def. "Partial shared-source
+# Poisson variance model")
+# ---------------------------------------------------------------------------
+
+def _overlap_members(shape):
+    return np.array([np.ravel_multi_index(c, shape) for c in [(3, 3), (4, 3), (3, 5), (5, 4)]])
+
+
+def test_shared_source_all_planes_equals_full_covariance(oracle):
+    """k_ex = n: sigma_k^2 = (T Sigma_g T^T)_kk with (Sigma_g)_ij = m_v(u_i) when
+    u_i = u_j and 0 otherwise (Eq. shared-voxel-group-covariance), built with
+    full matrices (scipy DCT, hand Haar) from the plug-in m_v = s_P [y]_+."""
+    s_p = 0.1
+    _, x, _, rng = _group_setup(oracle, ("poisson", s_p))
+    y = rng.poisson(x / s_p) * s_p
+    members = _overlap_members(x.shape)
+    p = oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", s_p), (8, 8), cov_planes=4)
+    g = oracle.filter_group(p, 1, y, None, members)
+    offs = [np.ravel_multi_index((a, b), x.shape) for a in range(4) for b in range(4)]
+    u = np.array([[m + o for o in offs] for m in members]).ravel()
+    mv = s_p * np.maximum(y.ravel()[u], 0)
+    Sigma = np.where(u[:, None] == u[None, :], mv[:, None], 0.0)
+    T = _full_T(oracle, 4, (4, 4))
+    np.testing.assert_allclose(g["var"].ravel(), np.diag(T @ Sigma @ T.T), rtol=1e-11, atol=1e-14)
+    # the hard threshold of the filter uses these variances
+    keep = np.abs(g["Y"]) > 3.0 * np.sqrt(g["var"]) * (1 + 1e-4)
+    np.testing.assert_array_equal(g["C"], np.where(keep, g["Y"], 0.0))
+
+
+def test_shared_source_leading_planes_only(oracle):
+    """k_ex = 1: plane 0 takes the shared-source variance, planes 1..n-1 keep
+    the diagonal model sum_i T_ki^2 m_v(u_i) (Remark "Limiting cases": k_ex = 0
+    is the diagonal model)."""
+    s_p = 0.1
+    _, x, _, rng = _group_setup(oracle, ("poisson", s_p))
+    y = rng.poisson(x / s_p) * s_p
+    members = _overlap_members(x.shape)
+    mk = lambda k: oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", s_p), (8, 8), cov_planes=k)
+    v0 = oracle.filter_group(mk(0), 1, y, None, members)["var"]
+    v1 = oracle.filter_group(mk(1), 1, y, None, members)["var"]
+    v4 = oracle.filter_group(mk(4), 1, y, None, members)["var"]
+    np.testing.assert_array_equal(v1[1:], v0[1:])
+    np.testing.assert_allclose(v1[0], v4[0], rtol=1e-14)
+    assert np.max(np.abs(v1[0] / v0[0] - 1)) > 0.1
+
+
+def test_shared_source_variance_monte_carlo(oracle):
+    """On overlapping patches, where the diagonal model visibly misses, the
+    shared-source model with the exact clean mean as surrogate is the
+    variance of the transformed Poisson group (20000 draws)."""
+    s_p = 0.05
+    _, x, _, rng = _group_setup(oracle, ("poisson", s_p))
+    members = _overlap_members(x.shape)
+    offs = [np.ravel_multi_index((a, b), x.shape) for a in range(4) for b in range(4)]
+    idx = np.array([[m + o for o in offs] for m in members]).ravel()
+    p = oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", s_p), (8, 8), cov_planes=4)
+    Ys = []
+    for _ in range(40):
+        yy = rng.poisson(x[None] / s_p, size=(500,) + x.shape) * s_p
+        grp = yy.reshape(500, -1)[:, idx].reshape(500, 4, 4, 4)
+        Ys.append(np.stack([oracle.group_transform(p, gi, 0).ravel() for gi in grp]))
+    emp = np.concatenate(Ys).var(axis=0, ddof=1)
+    var = oracle.filter_group(p, 1, x, None, members)["var"].ravel()
+    big = var > 0.05 * var.max()
+    np.testing.assert_allclose(emp[big], var[big], rtol=0.08)
