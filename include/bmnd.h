@@ -91,7 +91,15 @@ enum { BMND_DOMAIN_COEFFICIENT = 0, BMND_DOMAIN_WINDOWED = 1 };
  *     models").
  *   match_metric SSD (App. A); match_policy fixed; match_t 3.0; beta_s 0.1
  *     and kappa_s 1.0 (Sec. 9.4); ht_rule hard (App. A); weight_domain
- *     coefficient (App. A).
+ *     coefficient (App. A); cov_planes 0 (the diagonal variance model; App. A
+ *     lists 4 exact covariance planes).
+ *
+ * cov_planes = k_ex > 0 (scaled-Poisson noise only, at most 32) gives the
+ * coefficients of the first k_ex planes of the group-axis transform, in both
+ * stages, the partial shared-source variance of Def. "Partial shared-source
+ * Poisson variance model": entries of overlapping members that come from
+ * the same location add their transform weights before squaring (Def.
+ * "Effective transform weights").  It runs in the generic kernels.
  *
  * weight_domain = BMND_DOMAIN_WINDOWED measures the weighting models of both
  * stages in the windowed synthesized domain (Def. "Windowed synthesized-
@@ -150,6 +158,7 @@ typedef struct {
     double kappa_s;
     int ht_rule;
     int weight_domain;
+    int cov_planes;
 } bmnd_params;
 
 void bmnd_default_params(bmnd_params *p);

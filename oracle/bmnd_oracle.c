@@ -857,7 +857,9 @@ static void filter_group(const or_params *p, int stage, const double *y,
     memcpy(mv, S2, sizeof(double) * (size_t)d);
     apply_T(&f, Y, 0, tmp);   /* Y = T y_g */
     apply_T(&f, S2, 2, tmp);  /* sigma_k^2 = sum_i T_ki^2 m_v(u_i) */
-    if (p->cov_planes > 0) shared_source_variance(p, &f, n, G->members, off, mv, S2);
+    /* READING: the partial shared-source model is the Poisson variance
+     * model of Sec. 5; Gaussian noise keeps sigma^2 */
+    if (p->cov_planes > 0 && p->noise_kind == 1) shared_source_variance(p, &f, n, G->members, off, mv, S2);
     free(mv);
     /* Def. "Windowed synthesized-domain weighting models" with diagonal F_g
      * and noise model: tr(H F Sigma F^H) = sum_k H_kk |F_k|^2 sigma_k^2 (and
@@ -1179,7 +1181,8 @@ int or_filter_group(const or_params *p, int stage, const double *y, const double
             double *mv = (double *)malloc(sizeof(double) * (size_t)d);
             memcpy(mv, var_out, sizeof(double) * (size_t)d);
             apply_T(&f, var_out, 2, tmp);
-            if (p->cov_planes > 0) shared_source_variance(p, &f, count, members, off, mv, var_out);
+            if (p->cov_planes > 0 && p->noise_kind == 1)
+                shared_source_variance(p, &f, count, members, off, mv, var_out);
             free(mv);
         }
         factors_free(&f);

@@ -51,7 +51,7 @@ class bmnd_params(ctypes.Structure):
                 ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int),
                 ("match_metric", ctypes.c_int), ("match_policy", ctypes.c_int),
                 ("match_t", ctypes.c_double), ("beta_s", ctypes.c_double), ("kappa_s", ctypes.c_double),
-                ("ht_rule", ctypes.c_int), ("weight_domain", ctypes.c_int)]
+                ("ht_rule", ctypes.c_int), ("weight_domain", ctypes.c_int), ("cov_planes", ctypes.c_int)]
 
 
 class bmnd_job(ctypes.Structure):

@@ -173,6 +173,7 @@ struct Plan {
   int Mmax;
   int gtrans;            // group transform (Haar / DCT)
   int metric;            // stage-1 matching distance (BMND_METRIC_*)
+  int kex;               // shared-source variance planes (0 = diagonal)
   int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
@@ -187,10 +188,11 @@ struct Plan {
 
 // Patch side of the specialized stage kernels for a shape: they take cubic
 // patches (side jL on every axis) of the sizes instantiated with the kernels,
-// with a Haar group transform; 0 selects the generic kernel of the rank.
-int cube_side(int D, const int *j, int gtrans) {
+// with a Haar group transform and the diagonal variance model; 0 selects the
+// generic kernel of the rank.
+int cube_side(int D, const int *j, int gtrans, int kex) {
   const int jL = j[D - 1];
-  if (gtrans != BMND_GROUP_HAAR) return 0;
+  if (gtrans != BMND_GROUP_HAAR || kex > 0) return 0;
   for (int a = 0; a < D; ++a)
     if (j[a] != jL) return 0;
   if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
@@ -270,7 +272,7 @@ std::string tune_key(int ndim, const int64_t *shape, const int *patch, const int
   }
   snprintf(b, sizeof(b), "g%d,%d s%d m%d t%d sc%d p%d w%d,%d d%d", group_size[0], stages == 2 ? group_size[1] : 0,
            stages, mass_conserve, pr.group_transform, pr.schedule, pr.passes, pr.weight_model, pr.weight_scope,
-           pr.match_metric);
+           pr.match_metric + 16 * pr.cov_planes);
   k += b;
   return k;
 }
@@ -370,6 +372,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   if (pr.power_mode < 0 || pr.power_mode > 2) return fail(ctx, BMND_EINVAL, "unknown power mode");
   if (pr.ht_rule < 0 || pr.ht_rule > 1) return fail(ctx, BMND_EINVAL, "unknown thresholding rule");
   if (pr.weight_domain < 0 || pr.weight_domain > 1) return fail(ctx, BMND_EINVAL, "unknown weight domain");
+  if (pr.cov_planes < 0 || pr.cov_planes > MMAX) return fail(ctx, BMND_EINVAL, "cov_planes not in [0, %d]", MMAX);
   if (pr.match_metric < 0 || pr.match_metric > 3) return fail(ctx, BMND_EINVAL, "unknown matching distance");
   if (pr.match_policy < 0 || pr.match_policy > 2) return fail(ctx, BMND_EINVAL, "unknown matching policy");
   if (pr.match_metric != BMND_METRIC_SSD && (!(pr.match_t >= 0) || !(pr.beta_s >= 0) || !(pr.kappa_s > 0)))
@@ -424,12 +427,13 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   g.lean = D >= 3 ? 1 : 0;
   pl.gtrans = pr.group_transform;
   pl.metric = pr.match_metric;
+  pl.kex = pr.cov_planes;
   if (pl.metric != BMND_METRIC_SSD) {
     bmnd_status rc = ensure_moments(ctx, pl.metric);
     if (rc != BMND_OK) return rc;
     g.mom = ctx->mom[pl.metric];
   }
-  if (cube_side(D, g.j, pl.gtrans) && g.P <= 32) {
+  if (cube_side(D, g.j, pl.gtrans, pl.kex) && g.P <= 32) {
     // specialized kernels with members in registers: unpadded rows, odd
     // member stride (whole members and whole entry columns are read)
     g.LS = g.jL;
@@ -607,6 +611,7 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.lambda = (float)pr.lambda_ht;
   g.soft = stage == 1 && pr.ht_rule == BMND_HT_SOFT;
   g.wdomain = pr.weight_domain;
+  g.kex = pr.cov_planes;
   g.s_v = (float)pr.s_v;
   g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
   g.s_p = (float)(g.poisson ? nz.poisson_scale : 1.0);
@@ -614,7 +619,7 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
 }
 
 // Patch side of the specialized stage kernel for a plan (0: generic).
-int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans); }
+int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans, pl.kex); }
 
 // Kernel stage of a plan's stage s: 3 selects the stage-1 kernels with a
 // Poisson matching distance.
@@ -712,6 +717,8 @@ bmnd_status check_noise(bmnd_ctx *ctx, const bmnd_noise &nz, const bmnd_params *
   // the Poisson matching distances are defined on raw counts y / s_P
   if (pr && pr->match_metric != BMND_METRIC_SSD && nz.kind != BMND_NOISE_POISSON)
     return fail(ctx, BMND_EINVAL, "Poisson matching distances need the scaled-Poisson noise model");
+  if (pr && pr->cov_planes > 0 && nz.kind != BMND_NOISE_POISSON)
+    return fail(ctx, BMND_EINVAL, "the shared-source variance model needs the scaled-Poisson noise model");
   return BMND_OK;
 }
 
@@ -925,6 +932,7 @@ void bmnd_default_params(bmnd_params *p) {
   p->kappa_s = 1.0;
   p->ht_rule = BMND_HT_HARD;
   p->weight_domain = BMND_DOMAIN_COEFFICIENT;
+  p->cov_planes = 0;
 }
 
 bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {

@@ -1037,6 +1037,80 @@ __device__ __forceinline__ float syn_energy(const DGeom &g, int v) {
   return e;
 }
 
+// Entry (l, m) of the group-axis transform of n members: Haar rows ordered
+// [scaling, coarsest detail, ..., finest details], or the DCT-II from the
+// global table.
+__device__ __forceinline__ float group_axis_entry(const DGeom &g, const float *tab, int n, int l, int m) {
+  if (g.gtrans != 0) return __ldg(tab + gen_off(n) + l * n + m);
+  if (l == 0) return rsqrtf((float)n);
+  const int s = 31 - __clz(l);          // level: l in [2^s, 2^(s+1))
+  const int b = n >> s, r = l - (1 << s);
+  if (m < r * b || m >= (r + 1) * b) return 0.f;
+  const float v = rsqrtf((float)b);
+  return m < r * b + b / 2 ? v : -v;
+}
+
+// Def. "Partial shared-source Poisson variance model": for the leading kex
+// group-axis planes l, the variance of coefficient (l, q) sums the effective
+// weights of entries that share a source location (Def. "Effective transform
+// weights").  bufA holds the diagonal model sum_i T_ki^2 m_v(u_i); with
+// T_(l,q),(m,p) = A0[l][m] F_q(p), the shared locations add, for every
+// member pair m < m2 whose patches overlap (origin offset delta = o_m2 - o_m),
+//   2 A0[l][m] A0[l][m2] sum_p F_q(p) F_q(p - delta) m_v(o_m + p)
+// over the entries p of m that are entries p - delta of m2.  Lanes own
+// spatial coefficients q, so each updates its own column of bufA.
+__device__ __noinline__ void shared_source_planes(const DGeom &g, int n, int lane, const int *__restrict__ mem,
+                                                  const int *__restrict__ vbuf, const float *__restrict__ Sg,
+                                                  float *__restrict__ bufA, int MS, const float *mats,
+                                                  const int *moff, const float *tab) {
+  const int D = g.D;
+  const int L = min(g.kex, n);
+  for (int q = lane; q < g.P; q += 32) {
+    int qc[KMAXD];
+    {
+      int r = q;
+      for (int d = D - 1; d >= 0; --d) {
+        qc[d] = r % g.j[d];
+        r /= g.j[d];
+      }
+    }
+    for (int m = 0; m < n; ++m) {
+      int cm[KMAXD];
+      for (int d = 0; d < D; ++d) cm[d] = (mem[m] / g.rst[d]) % g.RG[d];
+      for (int m2 = m + 1; m2 < n; ++m2) {
+        int dl[KMAXD], ext[KMAXD], cnt = 1;
+        bool ov = true;
+        for (int d = 0; d < D; ++d) {
+          dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - cm[d];
+          ext[d] = g.j[d] - abs(dl[d]);
+          ov = ov && ext[d] > 0;
+          cnt *= ext[d] > 0 ? ext[d] : 0;
+        }
+        if (!ov) continue;
+        float X = 0.f;
+        for (int e = 0; e < cnt; ++e) {
+          int r = e, off = mem[m];
+          float f1 = 1.f, f2 = 1.f;
+          for (int d = D - 1; d >= 0; --d) {
+            const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
+            r /= ext[d];
+            const int J = g.j[d];
+            const float *F = mats + moff[d];
+            f1 *= F[qc[d] * J + pd];
+            f2 *= F[qc[d] * J + pd - dl[d]];
+            off += pd * g.rst[d];
+          }
+          X = fmaf(f1 * f2, g.s_p * fmaxf(Sg[off], 0.f), X);
+        }
+        for (int l = 0; l < L; ++l) {
+          const float w = group_axis_entry(g, tab, n, l, m) * group_axis_entry(g, tab, n, l, m2);
+          if (w != 0.f) bufA[l * MS + vbuf[q]] += 2.f * w * X;
+        }
+      }
+    }
+  }
+}
+
 // Entries (m, v) of a group, m < n members, v < P patch entries, visited with
 // a lane stride of 32 and no integer division.
 #define BMND_FOR_ENTRIES(body)                         \
@@ -1171,6 +1245,10 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       tb = bufB;
       tmode = 0;
     } else if (ph == 2) {
+      if (g.kex > 0 && g.poisson) {
+        shared_source_planes(g, n, lane, mem, vbuf, Sg, bufA, MS, mats, moff, tab);
+        __syncwarp();
+      }
       // ---- shrinkage; per-coefficient weight terms into bufA ----
       BMND_FOR_ENTRIES({
         const int a = m * MS + vbuf[v];

@@ -99,6 +99,9 @@ struct DGeom {
   // kaiser_d(p)^2 (the diagonal of the windowed synthesis metric)
   int wdomain;
   float wsyn[KMAXD][JMAX];
+  // leading group-axis planes with the partial shared-source Poisson
+  // variance (Sec. 5); 0 = the diagonal model.  Generic kernels only.
+  int kex;
   float mt, beta_p, kappa, inv_sp;
   const float2 *mom;
 };
