@@ -1772,7 +1772,10 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
     float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
     float *bufB = cmode ? bufA : bufA + g.M * MS;
-    float2 *fpb = reinterpret_cast<float2 *>(bufB + g.M * MS);
+    // the private footprint (float2) follows the group buffer(s), their
+    // float count rounded up to even so that it stays 8-byte aligned (one
+    // buffer of an odd group size times an odd member stride is odd)
+    float2 *fpb = reinterpret_cast<float2 *>(bufA + (((cmode ? 1 : 2) * g.M * MS + 1) & ~1));
     int64_t *gb = reinterpret_cast<int64_t *>(fpb + g.fp);
     float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
     float2 *acc = L.acc;

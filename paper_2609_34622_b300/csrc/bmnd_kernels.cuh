@@ -41,11 +41,11 @@ cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
 // Bytes of one warp's shared block: member list, weights, plane sums, the
 // members' footprint offsets and one spare list (5 x MMAX words), nbuf group buffers of M x MS floats (two for
 // filtering, one for a second mass-conservation sweep from the synthesis
-// cache), the private footprint (fp float2) and, when y and eta are read
-// from global memory (lean), the members' global origins (MMAX int64),
-// rounded up to 16.
+// cache; their float count rounded up to even), the private footprint (fp
+// float2, 8-byte aligned) and, when y and eta are read from global memory
+// (lean), the members' global origins (MMAX int64), rounded up to 16.
 __host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean, int nbuf = 2) {
-  return (5 * MMAX * 4 + nbuf * M * MS * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
+  return (5 * MMAX * 4 + ((nbuf * M * MS + 1) & ~1) * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
 }
 
 // Floats reserved in shared memory for the three J x J matrices of one patch
