@@ -1775,7 +1775,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     // the private footprint (float2) follows the group buffer(s), their
     // float count rounded up to even so that it stays 8-byte aligned (one
     // buffer of an odd group size times an odd member stride is odd)
-    float2 *fpb = reinterpret_cast<float2 *>(bufA + (((cmode ? 1 : 2) * g.M * MS + 1) & ~1));
+    float2 *fpb = reinterpret_cast<float2 *>(cmode ? bufA + ((g.M * MS + 1) & ~1) : bufB + g.M * MS);
     int64_t *gb = reinterpret_cast<int64_t *>(fpb + g.fp);
     float *Sg = L.Sg, *Sy = L.Sy, *Se = L.Se;
     float2 *acc = L.acc;
