@@ -56,6 +56,20 @@ def workload(name: str, item: int, edge: int = 128):
     raise SystemExit("unknown workload %s" % name)
 
 
+def replica_totals(dev_ms: float, e2e_ms: float, vox_step: int, steps: int, world: int, dist=None, device=None):
+    """Whole-job figures of N independent replicas (one seeded instance per
+    rank, no collective on the data path): the slowest rank's times (MAX over
+    ranks) and the voxels all ranks processed.  Returns (dev_ms, e2e_ms,
+    value, e2e value) with values in voxels/s."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    total = vox_step * steps * world
+    return dev_ms, e2e_ms, total / (dev_ms / 1e3), total / (e2e_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -600,14 +614,8 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
 
-    if dist:
-        t = torch.tensor([dev_ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms, e2e_ms = float(t[0]), float(t[1])
-
-    total_vox = vox_step * args.steps * world
-    value = total_vox / (dev_ms / 1e3)
-    e2e_val = total_vox / (e2e_ms / 1e3)
+    dev_ms, e2e_ms, value, e2e_val = replica_totals(dev_ms, e2e_ms, vox_step, args.steps, world,
+                                                    dist if dist else None, dev)
 
     # roofline of the dominant kernel (the stage kernel, both stages)
     n1, ms1 = kstats["stage1"]
