@@ -278,3 +278,15 @@ def test_match_ref_against_numpy_ranking(oracle, metric, policy):
                 assert abs(scores[a] - scores[b]) < 1e-5 * max(abs(scores[b]), 1.0)
         checked += 1
     assert checked >= 2
+
+
+@pytest.mark.parametrize("metric", METRICS)
+def test_contributions_symmetric_nonnegative(oracle, metric):
+    """Eqs. (deviance), (pearson), (anscombe-distance): each contribution is
+    symmetric in (r, c), non-negative, and zero exactly when r = c."""
+    rng = np.random.default_rng(9)
+    for r, c in zip(rng.gamma(0.8, 5.0, 200), rng.gamma(0.8, 5.0, 200)):
+        a, b = oracle.phi(metric, r, c), oracle.phi(metric, c, r)
+        assert a == pytest.approx(b, rel=1e-12, abs=1e-15)
+        assert a > 0.0
+        assert oracle.phi(metric, r, r) == pytest.approx(0.0, abs=1e-12)
