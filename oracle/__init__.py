@@ -25,7 +25,7 @@ MAXD = 8
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` with gcc (OpenMP, -O2)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
     return _LIB
 
 
@@ -112,10 +112,6 @@ def _load():
         _lib.or_phi.restype = ctypes.c_double
         _lib.or_moments.argtypes = [ctypes.c_int, ctypes.c_int, d, d]
         _lib.or_moment_table_f32.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_float), P(ctypes.c_float)]
-        _lib.or_log_f32.argtypes = [ctypes.c_float]
-        _lib.or_log_f32.restype = ctypes.c_float
-        _lib.or_phi_f32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_float]
-        _lib.or_phi_f32.restype = ctypes.c_float
     return _lib
 
 
@@ -335,19 +331,9 @@ def moments(metric: str, n: int):
 
 
 def moment_table_f32(metric: str, count: int = NMAX + 1):
-    """The float32 tables (mu, v) for n = 0..count-1 that the decisions read."""
+    """The FP64 moments (mu, v) for n = 0..count-1 rounded to float32."""
     mu = np.zeros(count, np.float32)
     v = np.zeros(count, np.float32)
     fp = ctypes.POINTER(ctypes.c_float)
     _load().or_moment_table_f32(METRICS[metric], int(count), mu.ctypes.data_as(fp), v.ctypes.data_as(fp))
     return mu, v
-
-
-def log_f32(x: float) -> float:
-    """The single-precision logarithm of the decision path (artanh series)."""
-    return _load().or_log_f32(float(x))
-
-
-def phi_f32(metric: str, r: float, c: float) -> float:
-    """phi_m(r, c) in the single precision of the decision path."""
-    return _load().or_phi_f32(METRICS[metric], float(r), float(c))

@@ -6,10 +6,8 @@
  * code, header, table or constant with the CUDA path.
  *
  * Everything is written as the plain definition, in double precision, in the
- * order the paper states it.  One exception: the block-matching scores, which
- * only serve to rank and accept candidates (an integer decision), are formed in
- * single precision, the CUDA kernels' precision, because the paper fixes none
- * and count data produce many exact ties whose order decides the group:
+ * order the paper states it, block-matching scores and thresholding decisions
+ * included:
  *   - reference schedule: Def. "Clipped reference origin", Eq. (number-shifts),
  *     Eq. (candidate-shift-list), Defs. "Generated / Balanced / Sparse / Off
  *     reference schedule" (Sec. 4.1);
@@ -40,7 +38,6 @@
  * left without a pin in the test suite, but the absolute PSNR of the whole
  * pipeline is only fixed by those pins, not by a printed worked example.
  */
-#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -472,158 +469,86 @@ void or_moments(int metric, int n, double *mu, double *v)
  * pooled count above OR_NMAX uses the moments at OR_NMAX. */
 #define OR_NMAX 4096
 
-static float or_mu_f[4][OR_NMAX + 1], or_v_f[4][OR_NMAX + 1];
+static double or_mu_t[4][OR_NMAX + 1], or_v_t[4][OR_NMAX + 1];
 static int or_tab_ready[4];
 
-/* The single-precision tables the acceptance decisions read: the FP64
- * moments rounded to float.  Built once per metric, outside parallel code. */
+/* FP64 moment tables mu_m(n), v_m(n), n = 0..OR_NMAX, built once per metric,
+ * outside parallel code. */
 void or_moment_tables(int metric)
 {
     if (metric < 1 || metric > 3 || or_tab_ready[metric]) return;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int n = 0; n <= OR_NMAX; ++n) {
-        double mu, v;
-        or_moments(metric, n, &mu, &v);
-        or_mu_f[metric][n] = (float)mu;
-        or_v_f[metric][n] = (float)v;
-    }
+    for (int n = 0; n <= OR_NMAX; ++n) or_moments(metric, n, &or_mu_t[metric][n], &or_v_t[metric][n]);
     or_tab_ready[metric] = 1;
 }
 
-/* Copies of the float tables (n = 0..count-1, count <= OR_NMAX + 1). */
+/* The FP64 moments rounded to float (n = 0..count-1, count <= OR_NMAX + 1),
+ * for the test that compares them with the CUDA library's host tables. */
 void or_moment_table_f32(int metric, int count, float *mu, float *v)
 {
     or_moment_tables(metric);
-    for (int n = 0; n < count && n <= OR_NMAX; ++n) { mu[n] = or_mu_f[metric][n]; v[n] = or_v_f[metric][n]; }
+    for (int n = 0; n < count && n <= OR_NMAX; ++n) { mu[n] = (float)or_mu_t[metric][n]; v[n] = (float)or_v_t[metric][n]; }
 }
 
-/* READING: ranking and acceptance under a Poisson metric are integer
- * decisions and are taken in single precision, with every operation below
- * rounded once, in the order written (the file is built without
- * floating-point contraction).  The logarithm is the artanh series
- * ln x = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9 + ...),
- * s = (m - 1) / (m + 1), after writing x = 2^e m with m in [1/sqrt 2, sqrt 2]
- * (|s| <= 0.172, so the terms after s^9 are below 1e-9 relative), and
- * e ln 2 added with ln 2 split into a 16-bit head and a float tail. */
-static float or_log_f(float x)
+/* Table index of a pooled count: the nearest integer (ties to even), capped
+ * at OR_NMAX.  READING: the moments are defined at integer n; a real pooled
+ * count is rounded. */
+static int or_count_index(double x)
 {
-    int e = 0;
-    if (x < FLT_MIN) { x = x * 0x1p23f; e = -23; }
-    uint32_t b;
-    memcpy(&b, &x, 4);
-    e += (int)((b >> 23) & 0xffu) - 127;
-    b = (b & 0x007fffffu) | 0x3f800000u;
-    float m;
-    memcpy(&m, &b, 4);
-    if (m > 0x1.6a09e6p+0f) { m = m * 0.5f; e += 1; }
-    float s = (m - 1.0f) / (m + 1.0f);
-    float s2 = s * s;
-    float q = fmaf(s2, 0x1.c71c72p-3f, 0x1.24924ap-2f);   /* 2/9, 2/7 */
-    q = fmaf(s2, q, 0x1.99999ap-2f);                       /* 2/5 */
-    q = fmaf(s2, q, 0x1.555556p-1f);                       /* 2/3 */
-    q = fmaf(s2, q, 2.0f);
-    float lm = s * q;
-    float fe = (float)e;
-    return fmaf(fe, 0x1.62e4p-1f, fmaf(fe, 0x1.7f7d1cp-20f, lm));
+    if (x > (double)OR_NMAX) x = (double)OR_NMAX;
+    return (int)rint(x);
 }
 
-/* phi_m(r, c) in single precision (same definitions as or_phi). */
-static float or_phi_f(int metric, float r, float c)
-{
-    float n = r + c;
-    if (metric == 1) {
-        if (!(n > 0.0f)) return 0.0f;
-        float a = r > 0.0f ? r * or_log_f((2.0f * r) / n) : 0.0f;
-        float b = c > 0.0f ? c * or_log_f((2.0f * c) / n) : 0.0f;
-        return 2.0f * (a + b);
-    }
-    if (metric == 2) {
-        if (!(n > 0.0f)) return 0.0f;
-        float d = r - c;
-        return (d * d) / n;
-    }
-    float d = 2.0f * sqrtf(c + 0.375f) - 2.0f * sqrtf(r + 0.375f);
-    return 0.5f * (d * d);
-}
-
-/* Exported for the tests: the single-precision log and contribution. */
-float or_log_f32(float x) { return or_log_f(x); }
-float or_phi_f32(int metric, float r, float c) { return or_phi_f(metric, r, c); }
-
-/* Table index of a pooled count: nearest integer (ties to even), capped. */
-static int or_count_index(float x)
-{
-    if (x > (float)OR_NMAX) x = (float)OR_NMAX;
-    return (int)rintf(x);
-}
-
-/* Eq. (raw-counts) in single precision: [p / s_P]_+ as p times the float
- * reciprocal of s_P. */
-static float or_raw_count_f(double p, float inv_sp) { return fmaxf((float)p * inv_sp, 0.0f); }
-
-/* r-bar^kappa of Eq. (reference-threshold): the exponents of the paper's
- * sensitivity grid (Sec. 9.4: 0.25, 0.5, 1, 2, 3, 4) by square roots and
- * products, any other by powf. */
-static float or_pow_kappa(float x, double kappa)
-{
-    if (kappa == 1.0) return x;
-    if (kappa == 0.5) return sqrtf(x);
-    if (kappa == 0.25) return sqrtf(sqrtf(x));
-    if (kappa == 2.0) return x * x;
-    if (kappa == 3.0) return (x * x) * x;
-    if (kappa == 4.0) { float x2 = x * x; return x2 * x2; }
-    return powf(x, (float)kappa);
-}
+/* Eq. (raw-counts): [p / s_P]_+. */
+static double or_raw_count(const or_params *p, double v) { return pos(v / p->s_p); }
 
 /* Acceptance threshold of one reference in sum units (P d_m), from the
- * reference patch alone (entries pr[i], C order):
+ * reference patch alone (entries pr[off[i]]):
  *   fixed:      P tau, tau = tau_ht if set, else the high-count null
  *               1 + t sqrt(2 / P) (READING; Thm. "Common high-count limit":
  *               mean 1 and variance 2 per entry);
  *   reference:  P T_ref of Eq. (reference-threshold) = sum mu(2 r_i)
  *               + t sqrt(sum v(2 r_i)) + beta_s P r-bar^kappa_s;
  *   standardized: t (Def. "Candidate-standardized distance": Z < t). */
-static float or_metric_threshold(const or_params *p, const double *pr, const int64_t *off, int64_t P)
+static double or_metric_threshold(const or_params *p, const double *pr, const int64_t *off, int64_t P)
 {
     if (p->match_policy == 0) {
         double tau = p->tau_ht > 0.0 ? p->tau_ht : 1.0 + p->match_t * sqrt(2.0 / (double)P);
-        return (float)(tau * (double)P);
+        return tau * (double)P;
     }
-    if (p->match_policy == 2) return (float)p->match_t;
+    if (p->match_policy == 2) return p->match_t;
     int m = p->match_metric;
-    float inv = (float)(1.0 / p->s_p);
-    float msum = 0.0f, vsum = 0.0f, rsum = 0.0f;
+    double msum = 0.0, vsum = 0.0, rsum = 0.0;
     for (int64_t i = 0; i < P; ++i) {
-        float r = or_raw_count_f(pr[off[i]], inv);
-        int n = or_count_index(2.0f * r);
-        msum = msum + or_mu_f[m][n];
-        vsum = vsum + or_v_f[m][n];
-        rsum = rsum + r;
+        double r = or_raw_count(p, pr[off[i]]);
+        int n = or_count_index(2.0 * r);
+        msum += or_mu_t[m][n];
+        vsum += or_v_t[m][n];
+        rsum += r;
     }
-    float rbar = rsum / (float)P;
-    float allow = (float)(p->beta_s * (double)P) * or_pow_kappa(rbar, p->kappa_s);
-    return (msum + (float)p->match_t * sqrtf(vsum)) + allow;
+    double rbar = rsum / (double)P;
+    return msum + p->match_t * sqrt(vsum) + p->beta_s * (double)P * pow(rbar, p->kappa_s);
 }
 
-/* Score of one candidate under a Poisson metric: P d_m (fixed and reference
- * policies) or Z_m of Eq. (standardized-distance). */
-static float or_metric_score(const or_params *p, const double *pr, const double *pq, const int64_t *off,
-                             int64_t P)
+/* Score of one candidate under a Poisson metric: P d_m = sum_i phi_m(r_i,
+ * c_i) (Eq. metric-from-contributions; fixed and reference policies) or Z_m
+ * of Eq. (standardized-distance). */
+static double or_metric_score(const or_params *p, const double *pr, const double *pq, const int64_t *off,
+                              int64_t P)
 {
     int m = p->match_metric;
-    float inv = (float)(1.0 / p->s_p);
-    float acc = 0.0f, msum = 0.0f, vsum = 0.0f;
+    double acc = 0.0, msum = 0.0, vsum = 0.0;
     for (int64_t i = 0; i < P; ++i) {
-        float r = or_raw_count_f(pr[off[i]], inv), c = or_raw_count_f(pq[off[i]], inv);
-        acc = acc + or_phi_f(m, r, c);
+        double r = or_raw_count(p, pr[off[i]]), c = or_raw_count(p, pq[off[i]]);
+        acc += or_phi(m, r, c);
         if (p->match_policy == 2) {
             int n = or_count_index(r + c);
-            msum = msum + or_mu_f[m][n];
-            vsum = vsum + or_v_f[m][n];
+            msum += or_mu_t[m][n];
+            vsum += or_v_t[m][n];
         }
     }
     if (p->match_policy != 2) return acc;
-    return vsum > 0.0f ? (acc - msum) / sqrtf(vsum) : 0.0f;
+    return vsum > 0.0 ? (acc - msum) / sqrt(vsum) : 0.0;
 }
 
 /* Match one reference patch.  Guide g is y in stage 1 and the stage-1
@@ -661,10 +586,9 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
     /* Poisson-aware matching applies to stage 1 (App. B: the Wiener stage
      * keeps SSD on the pilot with a fixed threshold) */
     int metric = stage == 1 ? p->match_metric : 0;
-    float taus = (float)tau;
     if (metric) {
         or_moment_tables(metric);
-        taus = or_metric_threshold(p, g + ref_lin, off, P);
+        tau = or_metric_threshold(p, g + ref_lin, off, P);
     }
     or_cand *cs = (or_cand *)malloc(sizeof(or_cand) * (size_t)ncand);
     int64_t nc = 0;
@@ -676,34 +600,27 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
             rem /= w;
         }
         if (lin == ref_lin) continue;
+        double sc;
         if (metric) {
-            cs[nc].score = or_metric_score(p, g + ref_lin, g + lin, off, P);
-            cs[nc].lin = lin;
-            ++nc;
-            continue;
+            sc = or_metric_score(p, g + ref_lin, g + lin, off, P);
+        } else {
+            /* Eq. (ssd) and Def. "Noise-bias-corrected SSD" */
+            double ssd = 0.0, bias = 0.0;
+            for (int64_t i = 0; i < P; ++i) {
+                double pi = g[ref_lin + off[i]], qi = g[lin + off[i]];
+                ssd += (qi - pi) * (qi - pi);
+                if (p->noise_kind == 1) bias += pos(pi + qi);
+            }
+            double B = p->noise_kind == 1 ? p->s_p * bias : 2.0 * (double)P * p->sigma * p->sigma;
+            sc = ssd - gamma * B;
         }
-        /* READING: the paper fixes no precision; the ranking is an integer
-         * decision, so it is taken in single precision (the kernel's), with
-         * the sum over patch entries in their C order and each squared
-         * difference added by one fused multiply-add. */
-        float ssd = 0.0f, bias = 0.0f;
-        for (int64_t i = 0; i < P; ++i) {
-            float pi = (float)g[ref_lin + off[i]], qi = (float)g[lin + off[i]];
-            float df = qi - pi;
-            ssd = fmaf(df, df, ssd);
-            if (p->noise_kind == 1) bias += fmaxf(pi + qi, 0.0f);
-        }
-        float B;
-        if (p->noise_kind == 1) B = (float)p->s_p * bias;
-        else B = 2.0f * (float)P * (float)(p->sigma * p->sigma);
-        float sc = gamma > 0.0 ? ssd - (float)gamma * B : ssd;
         cs[nc].score = sc;
         cs[nc].lin = lin;
         ++nc;
     }
     qsort(cs, (size_t)nc, sizeof(or_cand), cmp_cand);
     int64_t nacc = 0;
-    while (nacc < nc && (float)cs[nacc].score < taus) ++nacc;
+    while (nacc < nc && cs[nacc].score < tau) ++nacc;
     int64_t take = nacc < M - 1 ? nacc : M - 1;
     if (1 + take < p->min_group) {
         take = p->min_group - 1;
@@ -884,12 +801,19 @@ static void filter_group(const or_params *p, int stage, const double *y,
                     double ay = fabs(Y[k]), t = p->lambda_ht * sqrt(S2[k]);
                     a = ay > t ? (ay - t) / ay : 0.0;
                 } else {
-                    /* READING: count data make exact ties |Y_k| = lambda
-                     * sigma_k common; the strict inequality zeroes them.  To
-                     * resolve them that way in any floating-point precision,
-                     * a coefficient is kept only if it exceeds the threshold
-                     * by a relative 1e-4. */
-                    a = fabs(Y[k]) > p->lambda_ht * sqrt(S2[k]) * (1.0 + 1e-4) ? 1.0 : 0.0;
+                    /* Eq. (hard-threshold): keep Y_k iff |Y_k| > lambda
+                     * sigma_k, so a coefficient exactly at the threshold is
+                     * zeroed.  READING: such exact ties occur in real
+                     * arithmetic with integer-valued data (e.g. two members
+                     * whose patch sums K1, K2 satisfy (K1 - K2)^2 = lambda^2
+                     * (K1 + K2) tie their DC x Haar coefficient), and the
+                     * double-precision values of the two sides then differ
+                     * by rounding alone; two sides that agree to a relative
+                     * 1e-12 (thousands of times the rounding of these sums,
+                     * and 5e4 times below the float32 resolution of the
+                     * data) are that tie, and are zeroed. */
+                    double t = p->lambda_ht * sqrt(S2[k]);
+                    a = fabs(Y[k]) - t > 1e-12 * t ? 1.0 : 0.0;
                 }
                 G->C[k] = a * Y[k];
                 /* Def. "Coefficient-domain hard-thresholding weighting

@@ -295,12 +295,29 @@ def test_patch_weights_equal_exact_synthesized_noise(oracle):
     np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-12)
 
 
+def test_hard_threshold_exact_tie(oracle):
+    """Def. coefficient thresholding at an exact tie: with s_P = 1 and two
+    one-sample members y = (9, 0), Haar gives Y = (9/sqrt 2, 9/sqrt 2) and
+    sigma^2 = ((9 + 0)/2, (9 + 0)/2), so |Y_k| = 3 sigma_k for both
+    coefficients in real arithmetic and the strict inequality zeroes them;
+    a count of 9 + 1e-6 lifts both above the threshold."""
+    y = np.array([9.0, 0.0, 0.0])
+    p = oracle.params(y.shape, (1,), (1,), (3,), ("poisson", 1.0), (2, 2))
+    g = oracle.filter_group(p, 1, y, None, [0, 1])
+    np.testing.assert_allclose(np.abs(g["Y"].ravel()), 9 / np.sqrt(2), rtol=1e-15)
+    np.testing.assert_allclose(np.sqrt(g["var"].ravel()), np.sqrt(4.5), rtol=1e-15)
+    assert np.all(g["C"] == 0.0)
+    y[0] = 9.0 + 1e-6
+    g = oracle.filter_group(p, 1, y, None, [0, 1])
+    np.testing.assert_array_equal(g["C"], g["Y"])
+
+
 def test_hard_threshold_mask(oracle):
     """Def. coefficient thresholding: C_k = Y_k if |Y_k| > lambda sigma_k else 0."""
     p, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
     y = rng.poisson(x / 0.1) * 0.1
     g = oracle.filter_group(p, 1, y, None, members)
-    keep = np.abs(g["Y"]) > 3.0 * np.sqrt(g["var"]) * (1 + 1e-4)
+    keep = np.abs(g["Y"]) - 3.0 * np.sqrt(g["var"]) > 1e-12 * 3.0 * np.sqrt(g["var"])
     np.testing.assert_array_equal(g["C"], np.where(keep, g["Y"], 0.0))
 
 
@@ -506,7 +523,7 @@ def test_soft_identity_at_zero_threshold(oracle):
 
 def test_soft_shrinks_at_least_as_much_as_hard(oracle):
     """|C_soft| <= |C_hard| coefficient by coefficient, and they share their
-    zero set up to the hard rule's 1e-4 tie guard."""
+    zero set away from the threshold."""
     _, x, members, rng = _group_setup(oracle, ("poisson", 0.1))
     y = rng.poisson(x / 0.1) * 0.1
     gh = oracle.filter_group(oracle.params((16, 16), (4, 4), (2, 2), (7, 7), ("poisson", 0.1), (8, 8)),
@@ -699,7 +716,7 @@ def test_shared_source_all_planes_equals_full_covariance(oracle):
     T = _full_T(oracle, 4, (4, 4))
     np.testing.assert_allclose(g["var"].ravel(), np.diag(T @ Sigma @ T.T), rtol=1e-11, atol=1e-14)
     # the hard threshold of the filter uses these variances
-    keep = np.abs(g["Y"]) > 3.0 * np.sqrt(g["var"]) * (1 + 1e-4)
+    keep = np.abs(g["Y"]) - 3.0 * np.sqrt(g["var"]) > 1e-12 * 3.0 * np.sqrt(g["var"])
     np.testing.assert_array_equal(g["C"], np.where(keep, g["Y"], 0.0))
 
 

@@ -185,34 +185,6 @@ def test_float_tables_round_fp64_moments(oracle, metric):
         assert mu[n] == np.float32(m) and v[n] == np.float32(s)
 
 
-# ---------------------------------------------------------------------------
-# single-precision decision path
-# ---------------------------------------------------------------------------
-
-def test_log_f32_accuracy(oracle):
-    """The artanh-series logarithm of the decision path: within 2 float ulps of
-    log (relative to max(|log x|, 2^-24)) from subnormals to 2^100."""
-    xs = np.concatenate([np.geomspace(1e-44, 1e30, 4000), [1.0, 2.0, 0.5, math.sqrt(2), 1 - 2 ** -24, 1 + 2 ** -23]])
-    xs = xs.astype(np.float32)
-    for x in xs:
-        got = oracle.log_f32(float(x))
-        ref = math.log(float(x))
-        assert abs(got - ref) <= 2.5 * 2 ** -24 * max(abs(ref), 1.0) + 1e-12, (x, got, ref)
-    assert oracle.log_f32(1.0) == 0.0
-
-
-@pytest.mark.parametrize("metric", METRICS)
-def test_phi_f32_close_to_fp64(oracle, metric):
-    """phi_m in single precision stays within float rounding of the FP64 definition."""
-    rng = np.random.default_rng(3)
-    r = np.concatenate([rng.poisson(4.0, 300).astype(float), rng.gamma(0.5, 40.0, 300), [0, 0, 1]])
-    c = np.concatenate([rng.poisson(4.0, 300).astype(float), rng.gamma(0.5, 40.0, 300), [0, 5, 0]])
-    for a, b in zip(r.astype(np.float32), c.astype(np.float32)):
-        got = oracle.phi_f32(metric, float(a), float(b))
-        ref = oracle.phi(metric, float(a), float(b))
-        assert abs(got - ref) <= 2e-6 * (float(a) + float(b) + 1.0), (a, b, got, ref)
-
-
 def _np_threshold(metric, policy, pref, P, t, beta, kappa, tau=None):
     if policy == "fixed":
         return P * (tau if tau else 1 + t * math.sqrt(2 / P))
