@@ -296,6 +296,21 @@ bmnd_status bmnd_set_profiling(bmnd_ctx *ctx, int enable);
 bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launches,
                               double *total_ms);
 
+/* Counters of the decisions taken in double precision (diagnostics; no
+ * counterpart in the paper).  The kernels score candidates and compare
+ * coefficients with the hard threshold in FP32, each with an error bound;
+ * wherever the bound cannot separate two candidates' scores, a score from
+ * the acceptance threshold or a coefficient from lambda sigma_k, the
+ * decision is re-taken in double precision as the definitions read
+ * (Eq. ssd, Def. "Noise-bias-corrected SSD", App. A group rules, Eq.
+ * hard-threshold).  counts[0]: candidates rescored; counts[1]: windows scored
+ * entirely in double precision (an ambiguous run longer than the warp's
+ * list); counts[2]: coefficients decided in double precision.  Synchronizes
+ * the context's device; totals since the context was created or since the
+ * last reset (reset != 0 clears them after reading).
+ * Errors: BMND_EINVAL for a null context or counts, BMND_ECUDA. */
+bmnd_status bmnd_decision_stats(bmnd_ctx *ctx, int reset, uint64_t counts[3]);
+
 /* ---- Serving loop --------------------------------------------------------
  * A request server (the paper has no counterpart; it serves the data-parallel
  * path to many concurrent requests).  A worker thread admits submitted jobs in
@@ -395,7 +410,8 @@ bmnd_status bmnd_graph_destroy(bmnd_graph *graph);
 
 /* Allocation-free denoising (the paper has no counterpart: this is a
  * deployment convenience).  Same computation and arguments as bmnd_denoise
- * with the App. A profile, but no context and no allocation: it calls no
+ * with the parameters that bmnd_default_params sets, but no context and no
+ * allocation: it calls no
  * cudaMalloc, cudaFree, pinned-host or other allocating routine.  It is meant
  * for callers that cannot allocate device memory: code running while another
  * component owns the device allocator, services working inside a memory
@@ -408,15 +424,20 @@ bmnd_status bmnd_graph_destroy(bmnd_graph *graph);
  * signal of 262144 samples and a 2-D 512x512 image fit; a 2048x2048 image
  * does not).
  *   - The first call on a device (the current device) performs a one-time,
- *     synchronous set-up: it resolves the array's device address, loads the
- *     transform tables and constants and reads the device limits.  Make that
- *     first call before any stream capture.
+ *     synchronous set-up: it resolves the array's device address, copies the
+ *     float and double DCT tables into the array, uploads the butterfly-DCT
+ *     constants to the device's constant bank and reads the device limits.
+ *     A process may call this entry point without ever creating a context.
+ *   - Calls must not be recorded by stream capture (each call copies its
+ *     two-entry job table from host stack memory): a call on a capturing
+ *     stream returns BMND_EUNSUPPORTED before enqueueing anything.
  *   - Every call shares the array, which keeps the previous call's contents;
  *     the call clears what must start at zero.  Calls whose work overlaps on
  *     the GPU (different streams, or host threads on one device) race on the
  *     array and give wrong results: serialize them.
  *   - errbuf/errlen (may be NULL/0) receive a one-line message on error.
- * Errors: as bmnd_denoise, plus BMND_ENOMEM when the array is too small. */
+ * Errors: as bmnd_denoise, plus BMND_ENOMEM when the array is too small and
+ * BMND_EUNSUPPORTED on a capturing stream. */
 bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
                                  const int *patch, const int *step, const int *search,
                                  const int *group_size, int stages, int mass_conserve, float *out,

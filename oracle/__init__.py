@@ -111,6 +111,8 @@ def _load():
         _lib.or_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib.or_phi.restype = ctypes.c_double
         _lib.or_moments.argtypes = [ctypes.c_int, ctypes.c_int, d, d]
+        _lib.or_exact_sum.argtypes = [d, ctypes.c_int64]
+        _lib.or_exact_sum.restype = ctypes.c_double
         _lib.or_moment_table_f32.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_float), P(ctypes.c_float)]
     return _lib
 
@@ -337,3 +339,9 @@ def moment_table_f32(metric: str, count: int = NMAX + 1):
     fp = ctypes.POINTER(ctypes.c_float)
     _load().or_moment_table_f32(METRICS[metric], int(count), mu.ctypes.data_as(fp), v.ctypes.data_as(fp))
     return mu, v
+
+
+def exact_sum(x) -> float:
+    """The oracle's exact summation (Shewchuk expansions, rounded once)."""
+    a = _f64(x).ravel()
+    return _load().or_exact_sum(_dptr(a), len(a))

@@ -417,6 +417,50 @@ int64_t or_coverage(const or_params *p, int32_t *cov, double *cv)
 /* calibration (Sec. 4.3)                                                    */
 /* ------------------------------------------------------------------------ */
 
+/* Exact sum of doubles by Shewchuk's expansion arithmetic ("Adaptive
+ * precision floating-point arithmetic and fast robust geometric predicates",
+ * 1997; the method of Python's math.fsum): the terms are kept as a list of
+ * non-overlapping partials whose sum is exact, and the result is that sum
+ * rounded once to nearest.  It depends only on the multiset of the terms. */
+typedef struct { double p[128]; int n; } or_xsum;
+
+static void xsum_init(or_xsum *s) { s->n = 0; }
+
+static void xsum_add(or_xsum *s, double x)
+{
+    int i = 0;
+    for (int j = 0; j < s->n; ++j) {
+        double y = s->p[j];
+        if (fabs(x) < fabs(y)) { double t = x; x = y; y = t; }
+        double hi = x + y;
+        double lo = y - (hi - x);
+        if (lo != 0.0) s->p[i++] = lo;
+        x = hi;
+    }
+    if (i < 128) s->p[i++] = x;
+    s->n = i;
+}
+
+static double xsum_value(const or_xsum *s)
+{
+    int n = s->n;
+    double hi = 0.0, lo = 0.0;
+    if (n == 0) return 0.0;
+    hi = s->p[--n];
+    while (n > 0) {
+        double x = hi, y = s->p[--n];
+        hi = x + y;
+        lo = y - (hi - x);
+        if (lo != 0.0) break;
+    }
+    /* round half to even across the remaining partials */
+    if (n > 0 && ((lo < 0.0 && s->p[n - 1] < 0.0) || (lo > 0.0 && s->p[n - 1] > 0.0))) {
+        double y = lo * 2.0, x = hi + y;
+        if (y == x - hi) hi = x;
+    }
+    return hi;
+}
+
 /* Anscombe transform A(n) = 2 sqrt(n + 3/8) (Def. "Anscombe-SSD matching
  * statistic"). */
 double or_anscombe(double n) { return 2.0 * sqrt(n + 0.375); }
@@ -532,23 +576,41 @@ static double or_metric_threshold(const or_params *p, const double *pr, const in
 
 /* Score of one candidate under a Poisson metric: P d_m = sum_i phi_m(r_i,
  * c_i) (Eq. metric-from-contributions; fixed and reference policies) or Z_m
- * of Eq. (standardized-distance). */
+ * of Eq. (standardized-distance).  READING: the sums over the patch entries
+ * are exact (xsum), so that a score depends only on the multiset of its
+ * contributions.  Two patches whose contributions are a permutation of each
+ * other tie exactly, as they do in real arithmetic, and the index orders
+ * them; a sequential sum would order them by rounding, and the logarithm of
+ * the deviance rounds differently in different libraries. */
 static double or_metric_score(const or_params *p, const double *pr, const double *pq, const int64_t *off,
                               int64_t P)
 {
     int m = p->match_metric;
-    double acc = 0.0, msum = 0.0, vsum = 0.0;
+    or_xsum acc, msum, vsum;
+    xsum_init(&acc);
+    xsum_init(&msum);
+    xsum_init(&vsum);
     for (int64_t i = 0; i < P; ++i) {
         double r = or_raw_count(p, pr[off[i]]), c = or_raw_count(p, pq[off[i]]);
-        acc += or_phi(m, r, c);
+        xsum_add(&acc, or_phi(m, r, c));
         if (p->match_policy == 2) {
             int n = or_count_index(r + c);
-            msum += or_mu_t[m][n];
-            vsum += or_v_t[m][n];
+            xsum_add(&msum, or_mu_t[m][n]);
+            xsum_add(&vsum, or_v_t[m][n]);
         }
     }
-    if (p->match_policy != 2) return acc;
-    return vsum > 0.0 ? (acc - msum) / sqrt(vsum) : 0.0;
+    if (p->match_policy != 2) return xsum_value(&acc);
+    double a = xsum_value(&acc), ms = xsum_value(&msum), vs = xsum_value(&vsum);
+    return vs > 0.0 ? (a - ms) / sqrt(vs) : 0.0;
+}
+
+/* Exported for the tests: the exact sum of n doubles. */
+double or_exact_sum(const double *x, int64_t n)
+{
+    or_xsum s;
+    xsum_init(&s);
+    for (int64_t i = 0; i < n; ++i) xsum_add(&s, x[i]);
+    return xsum_value(&s);
 }
 
 /* Match one reference patch.  Guide g is y in stage 1 and the stage-1
@@ -604,15 +666,21 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
         if (metric) {
             sc = or_metric_score(p, g + ref_lin, g + lin, off, P);
         } else {
-            /* Eq. (ssd) and Def. "Noise-bias-corrected SSD" */
-            double ssd = 0.0, bias = 0.0;
+            /* Eq. (ssd) and Def. "Noise-bias-corrected SSD".  READING: the
+             * sums over the patch entries are exact (xsum, as for the
+             * Poisson distances), so a score depends only on the multiset of
+             * its terms and patches whose terms are a permutation of each
+             * other tie exactly, as in real arithmetic */
+            or_xsum ssd, bias;
+            xsum_init(&ssd);
+            xsum_init(&bias);
             for (int64_t i = 0; i < P; ++i) {
                 double pi = g[ref_lin + off[i]], qi = g[lin + off[i]];
-                ssd += (qi - pi) * (qi - pi);
-                if (p->noise_kind == 1) bias += pos(pi + qi);
+                xsum_add(&ssd, (qi - pi) * (qi - pi));
+                if (p->noise_kind == 1) xsum_add(&bias, pos(pi + qi));
             }
-            double B = p->noise_kind == 1 ? p->s_p * bias : 2.0 * (double)P * p->sigma * p->sigma;
-            sc = ssd - gamma * B;
+            double B = p->noise_kind == 1 ? p->s_p * xsum_value(&bias) : 2.0 * (double)P * p->sigma * p->sigma;
+            sc = xsum_value(&ssd) - gamma * B;
         }
         cs[nc].score = sc;
         cs[nc].lin = lin;

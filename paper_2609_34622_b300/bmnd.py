@@ -78,7 +78,7 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
            "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune",
-           "bmnd_match_moments", "bmnd_coverage"]
+           "bmnd_match_moments", "bmnd_coverage", "bmnd_decision_stats"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH):
     lib.bmnd_graph_launch.argtypes = [vp, vp]
     lib.bmnd_autotune.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp, ip]
     lib.bmnd_graph_destroy.argtypes = [vp]
+    lib.bmnd_decision_stats.argtypes = [vp, ctypes.c_int, P(ctypes.c_uint64)]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.bmnd_match_moments.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp]
     lib.bmnd_coverage.argtypes = [vp, ctypes.c_int, i64p, ip, ip, P(bmnd_params), vp, i64p,
@@ -371,6 +372,14 @@ class Context:
 
     def bmnd_set_profiling(self, enable: bool):
         self._check(self._lib.bmnd_set_profiling(self.handle, int(bool(enable))))
+
+    def bmnd_decision_stats(self, reset: bool = False) -> dict:
+        """Counts of the decisions taken in double precision since the last reset:
+        rescored candidates, windows scored entirely in double precision, and
+        coefficients decided in double precision at the hard threshold."""
+        c = (ctypes.c_uint64 * 3)()
+        self._check(self._lib.bmnd_decision_stats(self.handle, int(reset), c))
+        return {"rescored": int(c[0]), "full_windows": int(c[1]), "ht_coefficients": int(c[2])}
 
     def bmnd_kernel_stats(self, reset: bool = False) -> dict:
         """{kind: (launches, total_ms)} for every kernel kind; reset clears after reading."""

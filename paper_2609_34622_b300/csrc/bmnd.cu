@@ -40,7 +40,9 @@ struct bmnd_ctx {
   char err[512] = {0};
   void *arena = nullptr;
   size_t arena_size = 0;
-  float *tab = nullptr;        // generic DCT matrices, sizes 1..32 (+ squares)
+  float *tab = nullptr;        // generic DCT matrices, sizes 1..32 (+ squares), then the double matrices
+  const double *tab64 = nullptr;  // double matrices inside the tab allocation (TAB64_OFFSET)
+  unsigned long long *diag = nullptr;  // counters of the double-precision decisions (3)
   DJob *djobs = nullptr;       // device job tables
   size_t djobs_cap = 0;
   DJob *hjobs = nullptr;       // pinned staging for the job tables
@@ -111,10 +113,11 @@ double kaiser_at(int n, int i, double beta) {
 std::mutex g_const_mu;
 bool g_const_ready[64] = {false};
 
-// Constants of the butterfly DCT (once per device).
-bmnd_status init_constants(bmnd_ctx *ctx) {
+// Constants of the butterfly DCT, once per device; the device must be
+// current.  Returns the CUDA error of the upload.
+cudaError_t init_constants_on(int device) {
   std::lock_guard<std::mutex> lk(g_const_mu);
-  if (ctx->device < 64 && g_const_ready[ctx->device]) return BMND_OK;
+  if (device >= 0 && device < 64 && g_const_ready[device]) return cudaSuccess;
   float sec[31], scale[12];
   for (int N = 2; N <= 32; N *= 2)
     for (int n = 0; n < N / 2; ++n) sec[N / 2 - 1 + n] = (float)(1.0 / (2.0 * std::cos(M_PI * (2.0 * n + 1.0) / (2.0 * N))));
@@ -123,9 +126,33 @@ bmnd_status init_constants(bmnd_ctx *ctx) {
     scale[2 * l] = (float)std::sqrt(1.0 / N);
     scale[2 * l + 1] = (float)std::sqrt(2.0 / N);
   }
-  CU(upload_fast_dct_constants(sec, scale));
-  if (ctx->device < 64) g_const_ready[ctx->device] = true;
+  cudaError_t e = upload_fast_dct_constants(sec, scale);
+  if (e == cudaSuccess && device >= 0 && device < 64) g_const_ready[device] = true;
+  return e;
+}
+
+bmnd_status init_constants(bmnd_ctx *ctx) {
+  CU(init_constants_on(ctx->device));
   return BMND_OK;
+}
+
+// Host image of the transform tables (TAB_BYTES): the float DCT-II matrices
+// of sizes 1..32 and their entrywise squares, and the double matrices at
+// TAB64_OFFSET.
+void fill_tables(std::vector<unsigned char> &img) {
+  img.assign(TAB_BYTES, 0);
+  float *t = reinterpret_cast<float *>(img.data());
+  double *t64 = reinterpret_cast<double *>(img.data() + TAB64_OFFSET);
+  for (int J = 1; J <= 32; ++J) {
+    int off = (J - 1) * J * (2 * J - 1) / 6;
+    for (int k = 0; k < J; ++k)
+      for (int i = 0; i < J; ++i) {
+        double v = dct_entry(J, k, i);
+        t[off + k * J + i] = (float)v;
+        t[GEN_TOTAL + off + k * J + i] = (float)(v * v);
+        t64[off + k * J + i] = v;
+      }
+  }
 }
 
 cudaEvent_t pool_event(bmnd_ctx *ctx) {
@@ -428,6 +455,8 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.gtrans = pr.group_transform;
   pl.metric = pr.match_metric;
   pl.kex = pr.cov_planes;
+  g.dct64 = ctx->tab64;
+  g.diag = ctx->diag;
   if (pl.metric != BMND_METRIC_SSD) {
     bmnd_status rc = ensure_moments(ctx, pl.metric);
     if (rc != BMND_OK) return rc;
@@ -616,6 +645,25 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.a_power = pr.power_mode == 0 ? 0.f : (pr.power_mode == 1 ? 1.f : (float)pr.s_v);
   g.s_p = (float)(g.poisson ? nz.poisson_scale : 1.0);
   g.var_g = (float)(g.poisson ? 0.0 : nz.sigma * nz.sigma);
+  // double-precision decisions: the scalars as the definitions have them
+  // (the Gaussian bias as 2 P sigma^2, evaluated left to right)
+  g.s_p64 = g.poisson ? nz.poisson_scale : 1.0;
+  g.gamma64 = g.metric == BMND_METRIC_SSD ? gamma : 0.0;
+  g.gbias64 = g.poisson ? 0.0 : 2.0 * (double)g.P * nz.sigma * nz.sigma;
+  g.tau64 = tau;
+  g.lambda64 = pr.lambda_ht;
+  g.var64 = g.poisson ? 0.0 : nz.sigma * nz.sigma;
+  // |s32 - s| <= (P + 6) 2^-24 (ssd + gamma B) for the FP32 score (one
+  // rounding per entry in the SSD and the bias sums, a few in the
+  // combination), with margin
+  g.ku = (float)((g.P + 8) * std::ldexp(1.0, -24) * 1.05);
+  double t2 = 1.0;
+  for (int a = 0; a < g.D; ++a) t2 *= g.j[a] >= 2 ? 2.0 / g.j[a] : 1.0;
+  g.ht_t2 = (float)t2;
+  int ex = 0;
+  const bool pow2 = g.poisson && std::frexp(nz.poisson_scale, &ex) == 0.5;
+  g.exact_ok = stage == 1 && g.metric == BMND_METRIC_SSD && pow2 && gamma >= 0 && gamma <= 64 &&
+               gamma == std::floor(gamma);
 }
 
 // Patch side of the specialized stage kernel for a plan (0: generic).
@@ -959,18 +1007,13 @@ bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes)
     // the static tile counter of the persistent kernel shares the CTA's shared memory
     ctx->max_smem -= 64;
     if (cudaMalloc(&ctx->counters, 64 * sizeof(int)) != cudaSuccess) { rc = BMND_ENOMEM; break; }
-    std::vector<float> t(2 * GEN_TOTAL);
-    for (int J = 1; J <= 32; ++J) {
-      int off = (J - 1) * J * (2 * J - 1) / 6;
-      for (int k = 0; k < J; ++k)
-        for (int i = 0; i < J; ++i) {
-          double v = dct_entry(J, k, i);
-          t[off + k * J + i] = (float)v;
-          t[GEN_TOTAL + off + k * J + i] = (float)(v * v);
-        }
-    }
-    if (cudaMalloc(&ctx->tab, sizeof(float) * t.size()) != cudaSuccess) { rc = BMND_ENOMEM; break; }
-    if (cudaMemcpy(ctx->tab, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMalloc(&ctx->diag, 4 * sizeof(unsigned long long)) != cudaSuccess) { rc = BMND_ENOMEM; break; }
+    if (cudaMemset(ctx->diag, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) { rc = BMND_ECUDA; break; }
+    std::vector<unsigned char> t;
+    fill_tables(t);
+    if (cudaMalloc(&ctx->tab, t.size()) != cudaSuccess) { rc = BMND_ENOMEM; break; }
+    ctx->tab64 = reinterpret_cast<const double *>(reinterpret_cast<unsigned char *>(ctx->tab) + TAB64_OFFSET);
+    if (cudaMemcpy(ctx->tab, t.data(), t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       rc = BMND_ECUDA;
       break;
     }
@@ -1013,6 +1056,17 @@ bmnd_status bmnd_kernel_stats(bmnd_ctx *ctx, int kind, int reset, int64_t *launc
   return BMND_OK;
 }
 
+bmnd_status bmnd_decision_stats(bmnd_ctx *ctx, int reset, uint64_t counts[3]) {
+  if (!ctx || !counts) return BMND_EINVAL;
+  CU(cudaSetDevice(ctx->device));
+  CU(cudaDeviceSynchronize());
+  unsigned long long h[4] = {0, 0, 0, 0};
+  CU(cudaMemcpy(h, ctx->diag, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 3; ++k) counts[k] = h[k];
+  if (reset) CU(cudaMemset(ctx->diag, 0, sizeof(h)));
+  return BMND_OK;
+}
+
 bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   if (!ctx) return BMND_EINVAL;
   cudaSetDevice(ctx->device);
@@ -1021,6 +1075,7 @@ bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->tab) cudaFree(ctx->tab);
+  if (ctx->diag) cudaFree(ctx->diag);
   if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->djobs) cudaFree(ctx->djobs);
   if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
@@ -1471,7 +1526,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 constexpr size_t kNoallocCounter = 0;
 constexpr size_t kNoallocJobs = 256;
 constexpr size_t kNoallocTab = (kNoallocJobs + 2 * sizeof(DJob) + 255) & ~(size_t)255;
-constexpr size_t kNoallocWork = (kNoallocTab + 2 * GEN_TOTAL * sizeof(float) + 255) & ~(size_t)255;
+constexpr size_t kNoallocWork = (kNoallocTab + TAB_BYTES + 255) & ~(size_t)255;
 
 struct NoallocDevice {
   bool ready;
@@ -1481,12 +1536,12 @@ struct NoallocDevice {
 };
 std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc[64];
-float g_noalloc_tab_host[2 * GEN_TOTAL];
 
 // One-time set-up on the current device: resolve the array's device address,
-// load the DCT tables and constants, read the SM count and shared-memory
-// limit.  Synchronous; the first call on a device must precede any stream
-// capture.
+// copy the transform tables (float and double DCT matrices) into it, upload
+// the butterfly-DCT constants to the device's constant bank (the same ones
+// bmnd_create uploads), read the SM count and shared-memory limit.
+// Synchronous; the first call on a device must precede any stream capture.
 bmnd_status noalloc_setup(int device, NoallocDevice *&out, char *err, size_t errlen) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (device < 0 || device >= 64) {
@@ -1502,17 +1557,10 @@ bmnd_status noalloc_setup(int device, NoallocDevice *&out, char *err, size_t err
       cudaGetLastError();
       return BMND_ECUDA;
     }
-    for (int J = 1; J <= 32; ++J) {
-      int off = (J - 1) * J * (2 * J - 1) / 6;
-      for (int k = 0; k < J; ++k)
-        for (int i = 0; i < J; ++i) {
-          double v = dct_entry(J, k, i);
-          g_noalloc_tab_host[off + k * J + i] = (float)v;
-          g_noalloc_tab_host[GEN_TOTAL + off + k * J + i] = (float)(v * v);
-        }
-    }
-    e = cudaMemcpy((unsigned char *)ptr + kNoallocTab, g_noalloc_tab_host, sizeof(g_noalloc_tab_host),
-                   cudaMemcpyHostToDevice);
+    std::vector<unsigned char> img;
+    fill_tables(img);
+    e = cudaMemcpy((unsigned char *)ptr + kNoallocTab, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = init_constants_on(device);
     int max_smem = 0, num_sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -1618,6 +1666,19 @@ bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape,
     snprintf(err, sizeof(err), "no current CUDA device");
     rc = BMND_ECUDA;
   }
+  if (rc == BMND_OK) {
+    // the job table is copied from this call's stack: a recorded copy would
+    // outlive it, so capture is refused
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      snprintf(err, sizeof(err), "cudaStreamIsCapturing failed");
+      rc = BMND_ECUDA;
+    } else if (cs != cudaStreamCaptureStatusNone) {
+      snprintf(err, sizeof(err), "the allocation-free entry point cannot be recorded by stream capture");
+      rc = BMND_EUNSUPPORTED;
+    }
+  }
   NoallocDevice *dev = nullptr;
   if (rc == BMND_OK) rc = noalloc_setup(device, dev, err, sizeof(err));
   if (rc == BMND_OK) {
@@ -1628,6 +1689,7 @@ bmnd_status bmnd_denoise_noalloc(const float *y, int ndim, const int64_t *shape,
     c.counters = (int *)(dev->base + kNoallocCounter);
     c.djobs = (DJob *)(dev->base + kNoallocJobs);
     c.tab = (float *)(dev->base + kNoallocTab);
+    c.tab64 = (const double *)(dev->base + kNoallocTab + TAB64_OFFSET);
     rc = noalloc_run(&c, dev, y, ndim, shape, noise, patch, step, search, group_size, stages, mass_conserve, out,
                      (cudaStream_t)stream);
     if (rc != BMND_OK) snprintf(err, sizeof(err), "%s", c.err);

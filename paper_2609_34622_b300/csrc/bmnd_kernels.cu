@@ -173,19 +173,21 @@ __global__ void k_sched_compact(const DJob *__restrict__ jobs, int njobs, SGeom 
 // warp-level helpers
 // ---------------------------------------------------------------------------
 
-struct KV { float k; int i; };
-
-__device__ __forceinline__ bool kv_less(float ak, int ai, float bk, int bi) {
+// (key, index) pairs order by key, then by index; T is float (FP32
+// screening) or double (double-precision decisions).
+template <typename T>
+__device__ __forceinline__ bool kv_less(T ak, int ai, T bk, int bi) {
   return ak < bk || (ak == bk && ai < bi);
 }
 
 // Sort one (key, index) pair per lane ascending across the warp (bitonic).
-__device__ __forceinline__ void warp_sort(float &k, int &i, int lane) {
+template <typename T>
+__device__ __forceinline__ void warp_sort(T &k, int &i, int lane) {
 #pragma unroll
   for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      float ok = __shfl_xor_sync(0xffffffffu, k, stride);
+      T ok = __shfl_xor_sync(0xffffffffu, k, stride);
       int oi = __shfl_xor_sync(0xffffffffu, i, stride);
       bool up = (lane & size) == 0;
       bool lower = (lane & stride) == 0;
@@ -198,13 +200,14 @@ __device__ __forceinline__ void warp_sort(float &k, int &i, int lane) {
 
 // Merge a sorted warp list (lk, li) with sorted offers (ok, oi): keeps the 32
 // smallest of the 64, sorted ascending.
-__device__ __forceinline__ void warp_merge(float &lk, int &li, float ok, int oi, int lane) {
-  float rk = __shfl_sync(0xffffffffu, ok, 31 - lane);
+template <typename T>
+__device__ __forceinline__ void warp_merge(T &lk, int &li, T ok, int oi, int lane) {
+  T rk = __shfl_sync(0xffffffffu, ok, 31 - lane);
   int ri = __shfl_sync(0xffffffffu, oi, 31 - lane);
   if (kv_less(rk, ri, lk, li)) { lk = rk; li = ri; }
 #pragma unroll
   for (int stride = 16; stride > 0; stride >>= 1) {
-    float pk = __shfl_xor_sync(0xffffffffu, lk, stride);
+    T pk = __shfl_xor_sync(0xffffffffu, lk, stride);
     int pi = __shfl_xor_sync(0xffffffffu, li, stride);
     bool lower = (lane & stride) == 0;
     bool p_less = kv_less(pk, pi, lk, li);
@@ -215,6 +218,11 @@ __device__ __forceinline__ void warp_merge(float &lk, int &li, float ok, int oi,
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 // single-instruction warp reductions of 32-bit integers
@@ -776,11 +784,286 @@ __device__ __noinline__ float metric_threshold(const DGeom &g, const float *p, c
 // block matching of one reference (Sec. 4.2 / 4.4, App. A group rules)
 // ---------------------------------------------------------------------------
 
+// Double-precision score of one candidate: Eq. (ssd) minus gamma times the
+// noise bias (Def. "Noise-bias-corrected SSD"), evaluated as the definition
+// reads: patch entries in C order, every difference, square, sum and
+// product rounded once in double precision (no fused operations).  rb / cb:
+// region offsets of the reference and the candidate patch.
+__device__ __forceinline__ double ssd_score64(const DGeom &g, const float *__restrict__ S, const int *rowoff,
+                                              int rb, int cb) {
+  double ssd = 0.0, bias = 0.0;
+  const bool pb = g.poisson && g.gamma64 != 0.0;
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = S + rb + rowoff[r], *qr = S + cb + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const double p = pr[i], q = qr[i];
+      const double d = __dsub_rn(q, p);
+      ssd = __dadd_rn(ssd, __dmul_rn(d, d));
+      if (pb) {
+        const double t = __dadd_rn(p, q);
+        bias = __dadd_rn(bias, t > 0.0 ? t : 0.0);
+      }
+    }
+  }
+  const double B = pb ? __dmul_rn(g.s_p64, bias) : g.gbias64;
+  return __dsub_rn(ssd, __dmul_rn(g.gamma64, B));
+}
+
+// Exact integer arithmetic on a tile's guide values.  Every staged value is
+// an integer multiple of q0 = 2^emin (emin: the lowest set-bit exponent over
+// the tile) of magnitude below 2^span q0.  fixed_of returns v / q0.
+__device__ __forceinline__ long long fixed_of(float v, int emin) {
+  const unsigned b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 0xffu);
+  const long long m = (long long)((b & 0x7fffffu) | (ex ? 0x800000u : 0u));
+  const int sh = (ex ? ex : 1) - 150 - emin;  // v = m 2^(ex - 150)
+  const long long r = sh >= 0 ? (m << sh) : (m >> -sh);
+  return (b >> 31) ? -r : r;
+}
+
+// The unsigned 128-bit integer hi 2^64 + lo rounded once to double (the top
+// 64 bits, with a sticky bit for the rest, converted with round-to-nearest-
+// even: the sticky bit lies far below the rounding position).
+__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
+  if (hi == 0ull) return __ull2double_rn(lo);
+  const int lz = __clzll((long long)hi);
+  const unsigned long long top = lz ? ((hi << lz) | (lo >> (64 - lz))) : hi;
+  const unsigned long long rest = lo << lz;
+  return ldexp(__ull2double_rn(top | (rest != 0ull ? 1ull : 0ull)), 64 - lz);
+}
+
+// Double-precision score of one candidate from exact sums (the terms of
+// Eq. ssd and of the Poisson bias summed exactly, then rounded once, as the
+// oracle does): the SSD in units of q0^2 as a 128-bit integer, the bias sum
+// in units of q0, then B = s_P bias and score = ssd - gamma B (Def.
+// "Noise-bias-corrected SSD").  span <= 31: the differences fit 32 bits and
+// their squares 64; span <= 51: 64-bit differences, 128-bit squares, and the
+// bias sum of P <= 1024 entries stays below 2^63.  The sums depend only on
+// the multiset of the terms.
+__device__ __forceinline__ double ssd_score_exact(const DGeom &g, const float *__restrict__ S, const int *rowoff,
+                                                  int rb, int cb, int emin, int span) {
+  unsigned long long lo = 0ull, hi = 0ull;
+  long long bsum = 0;
+  const bool pb = g.poisson && g.gamma64 != 0.0;
+  if (span <= 30 && emin >= -126) {
+    // 32-bit path: v / q0 is an integer below 2^30 (a float scaled by a
+    // power of two that is itself a normal float, so the conversion is
+    // exact), differences and sums fit 32 bits, squares 64
+    const float sc = ldexpf(1.f, -emin);
+    for (int r = 0; r < g.rows; ++r) {
+      const float *pr = S + rb + rowoff[r], *qr = S + cb + rowoff[r];
+#pragma unroll 4
+      for (int i = 0; i < g.jL; ++i) {
+        const int ip = __float2int_rn(pr[i] * sc), iq = __float2int_rn(qr[i] * sc);
+        const unsigned ud = (unsigned)abs(iq - ip);
+        const unsigned long long sq = (unsigned long long)ud * ud;
+        lo += sq;
+        hi += lo < sq ? 1ull : 0ull;
+        if (pb) bsum += max(ip + iq, 0);
+      }
+    }
+    const double ssd = ldexp(u128_to_double(hi, lo), 2 * emin);
+    const double B = pb ? __dmul_rn(g.s_p64, ldexp(__ll2double_rn(bsum), emin)) : g.gbias64;
+    return __dsub_rn(ssd, __dmul_rn(g.gamma64, B));
+  }
+  const bool narrow = span <= 31;
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = S + rb + rowoff[r], *qr = S + cb + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const long long ip = fixed_of(pr[i], emin), iq = fixed_of(qr[i], emin);
+      const long long d = iq - ip;
+      const unsigned long long ud = (unsigned long long)(d < 0 ? -d : d);
+      unsigned long long sq_lo, sq_hi;
+      if (narrow) {
+        sq_lo = ud * ud;
+        sq_hi = 0ull;
+      } else {
+        sq_lo = ud * ud;
+        sq_hi = __umul64hi(ud, ud);
+      }
+      lo += sq_lo;
+      hi += sq_hi + (lo < sq_lo ? 1ull : 0ull);
+      if (pb) {
+        const long long t = ip + iq;
+        bsum += t > 0 ? t : 0;
+      }
+    }
+  }
+  const double ssd = ldexp(u128_to_double(hi, lo), 2 * emin);
+  const double B = pb ? __dmul_rn(g.s_p64, ldexp(__ll2double_rn(bsum), emin)) : g.gbias64;
+  return __dsub_rn(ssd, __dmul_rn(g.gamma64, B));
+}
+
+__device__ __noinline__ double ssd_score64_call(const DGeom &g, const float *__restrict__ S, const int *rowoff, int rb,
+                                                int cb) {
+  return ssd_score64(g, S, rowoff, rb, cb);
+}
+
+// Score of a candidate for a double-precision decision: exact sums where the
+// tile's span allows (span <= 51), else the sequential double sum.
+__device__ __forceinline__ double score_decide(const DGeom &g, const float *__restrict__ S, const int *rowoff, int rb,
+                                               int cb, int emin, int span) {
+  return span <= 51 ? ssd_score_exact(g, S, rowoff, rb, cb, emin, span) : ssd_score64_call(g, S, rowoff, rb, cb);
+}
+
+// Every candidate of a window (window indices 0..ncand-1, region offsets
+// from the window origin lo and extents W) scored in double precision;
+// returns this lane's entry of the sorted list of the 32 best by (score,
+// window index), the reference (ridx) left out.
+template <int D>
+__device__ __noinline__ void full_window(const DGeom &g, const float *__restrict__ S, const int *rowoff, int lane,
+                                         int rbase, int ridx, int ncand, const int *lo, const int *W, int emin,
+                                         int span, double &fk, int &fi) {
+  fk = DBL_MAX;
+  fi = INT_MAX;
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    const int c = c0 + lane;
+    double sc = DBL_MAX;
+    int wi = INT_MAX;
+    if (c < ncand && c != ridx) {
+      int rem = c, off = 0;
+#pragma unroll
+      for (int d = D - 1; d >= 0; --d) {
+        const int x = rem % W[d];
+        rem /= W[d];
+        off += (lo[d] + x) * g.rst[d];
+      }
+      sc = score_decide(g, S, rowoff, rbase, off, emin, span);
+      wi = c;
+    }
+    warp_sort(sc, wi, lane);
+    warp_merge(fk, fi, sc, wi, lane);
+  }
+}
+
+// The group of one reference from the warp's FP32 list (lk, li): the best
+// candidates by (FP32 score, window index), one per lane, sorted; past the
+// valid entries (li = INT_MAX) the list is empty.  Ranking and acceptance
+// (App. A group rules) are decided as the double-precision definition
+// decides them.  Every FP32 score s carries an error bound ku (|s| + 2 gamma
+// Bm) (Bm: a bound on the noise bias of every candidate), so each list
+// entry is an interval; the entries split into runs between the gaps where
+// every interval to the left lies below every interval to the right (prefix
+// maximum of the upper ends against the suffix minimum of the lower ends).
+// A run of two or more entries that reaches a group position (the first
+// M - 1), and a group position whose interval holds tau, are rescored in
+// double precision (decide_refine); candidates outside the list (never
+// offered: FP32 score above the final offer threshold thr; or pushed out:
+// at least the last entry) are bounded below, and if that bound reaches the
+// upper ends of the group positions, the whole window is scored in double
+// precision.  exact: the tile's data are dyadic and every FP32 score is
+// exact.  Returns the number of accepted list entries among the first
+// M - 1 (the accepted candidates are a prefix of the sorted list); li may be
+// reordered.
+
+// The rare part: rescoring of the flagged entries (resc) or of the whole
+// window (full), the list sorted again in double precision, and the
+// acceptance count.
+template <int D>
+__device__ __noinline__ int decide_refine(const DGeom &g, const float *__restrict__ S, const int *rr,
+                                          const int *org, const int *rowoff, int lane, int rbase, int ridx,
+                                          int ncand, int nl, int KK, bool resc, bool full, int emin, int span,
+                                          float lk, int &li) {
+  const unsigned FULL = 0xffffffffu;
+  int lo[D], W[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int rglob = rr[d] + org[d];
+    const int l = max(rglob - g.rad[d], 0);
+    const int h = (int)min((int64_t)rglob + g.rad[d], g.ell[d]);
+    lo[d] = l - org[d];
+    W[d] = h - l + 1;
+  }
+  double key = lane < nl ? (double)lk : DBL_MAX;
+  if (full) {
+    full_window<D>(g, S, rowoff, lane, rbase, ridx, ncand, lo, W, emin, span, key, li);
+    if (g.diag && lane == 0) atomicAdd(g.diag + 1, 1ull);
+  } else {
+    int off = 0;
+    {
+      int rem = li;
+#pragma unroll
+      for (int d = D - 1; d >= 0; --d) {
+        const int c = rem % W[d];
+        rem /= W[d];
+        off += (lo[d] + c) * g.rst[d];
+      }
+    }
+    if (resc) key = score_decide(g, S, rowoff, rbase, off, emin, span);
+    if (g.diag) {
+      const int nr = __popc(__ballot_sync(FULL, resc));
+      if (lane == 0) atomicAdd(g.diag, (unsigned long long)nr);
+    }
+    warp_sort(key, li, lane);
+  }
+  // acceptance: score < tau (App. A), in double precision
+  return __popc(__ballot_sync(FULL, lane < KK && key < g.tau64));
+}
+
+template <int D>
+__device__ __forceinline__ int decide_group(const DGeom &g, const float *__restrict__ S, const int *rr, const int *org,
+                                            const int *rowoff, int lane, int rbase, int ridx, int ncand, float Bm,
+                                            float thr, bool exact, int emin, int span, float lk, int &li) {
+  const unsigned FULL = 0xffffffffu;
+  const int K = g.M - 1;
+  const int navail = ncand - 1;
+  const int nl = __popc(__ballot_sync(FULL, li != INT_MAX));  // valid list entries (a prefix)
+  const int KK = min(K, nl);
+  // tau bracketed in float: below tlo certainly accepted, at or above thi
+  // certainly not
+  const float tlo = g.tau - fabsf(g.tau) * 2.4e-7f, thi = g.tau + fabsf(g.tau) * 2.4e-7f;
+  if (exact || KK <= 0) {
+    // exact FP32 scores: only a score within a float step of tau needs the
+    // double-precision comparison
+    const bool amb = lane < KK && lk >= tlo && lk < thi;
+    const bool acc = lane < KK && (lk < tlo || (amb && (double)lk < g.tau64));
+    return __popc(__ballot_sync(FULL, acc));
+  }
+  const float gam = g.gamma;
+  // |s32 - s| <= ku (ssd + gamma B) <= ku (|s32| + 2 gamma Bm)
+  const float dl = lane < nl ? g.ku * (fabsf(lk) + 2.f * gam * Bm) : 0.f;
+  const float flo = lane < nl ? lk - dl : FLT_MAX;
+  const float fhi = lane < nl ? lk + dl : -FLT_MAX;
+  const float lk31 = __shfl_sync(FULL, lk, 31);
+  const float kout = nl == 32 ? fminf(thr, lk31) : thr;
+  const float outlb = navail > nl ? kout - g.ku * (fabsf(kout) + 2.f * gam * Bm) : FLT_MAX;
+  float pmax = fhi, smin = flo;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float a = __shfl_up_sync(FULL, pmax, o);
+    const float b = __shfl_down_sync(FULL, smin, o);
+    if (lane >= o) pmax = fmaxf(pmax, a);
+    if (lane + o < 32) smin = fminf(smin, b);
+  }
+  const float snext = __shfl_down_sync(FULL, smin, 1);
+  // gap after position `lane` open (every interval to its left below every
+  // list interval to its right); positions past the list are empty
+  const unsigned G = __ballot_sync(FULL, lane + 1 >= nl || pmax < snext);
+  const unsigned below = G & ((1u << lane) - 1u);
+  const int a = below ? 32 - __clz(below) : 0;             // first position of this run
+  const unsigned atabove = G & (~0u << lane);
+  const int b = atabove ? __ffs(atabove) - 1 : 32;         // last position of this run
+  const bool relevant = lane < nl && a <= KK - 1;
+  const bool tamb = lane < KK && flo < thi && fhi >= tlo;
+  const bool resc = (relevant && b > a) || tamb;
+  // the (M-1)-th smallest exact score is at most the largest upper end among
+  // the first M - 1 entries; a candidate outside the list whose lower bound
+  // stays above it cannot enter the group
+  const float hull = __shfl_sync(FULL, pmax, KK - 1);
+  const bool full = outlb <= hull;
+  if (full || __any_sync(FULL, resc))
+    return decide_refine<D>(g, S, rr, org, rowoff, lane, rbase, ridx, ncand, nl, KK, resc, full, emin, span, lk, li);
+  return __popc(__ballot_sync(FULL, lane < KK && lk < tlo));
+}
+
 template <int D, int JL, int KB, int ST>
 // nonneg: every staged guide value is >= 0 (count data), where
 // [p + q]_+ = p + q exactly and the bias term skips the max.
+// exact: every staged guide value lies on a dyadic grid fine enough that
+// the FP32 scores are exact (decide_group).
 __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
-                          const int *org, const int *rowoff, int lane, int *mem, bool nonneg) {
+                          const int *org, const int *rowoff, int lane, int *mem, bool nonneg, bool exact,
+                          int emin, int span, float vmaxf, unsigned long long *diag) {
   int lo[D], W[D];
   int64_t ncand = 1;
 #pragma unroll
@@ -818,6 +1101,26 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
   float thr = FLT_MAX;
   int thri = INT_MAX;
   int nacc = 0;
+  // Offers must beat the (M-1)-th list entry widened by the error bounds of
+  // the FP32 scores (decide_group): lk[M-2] + 3 ku (|lk[M-2]| + 2 gamma Bm),
+  // Bm a bound on the noise bias of every candidate (Poisson: s_P times the
+  // reference's sum plus P times the tile's largest value; Gaussian: 2 P
+  // sigma^2).  The widened threshold only falls as the list improves, and a
+  // candidate that was never offered has a lower bound above the upper ends
+  // of the first M - 1 entries, so it cannot belong to the group in double
+  // precision.  Exact tiles take no margin.
+  const int KP = g.M >= 2 ? g.M - 2 : 0;
+  float Bm = 0.f;
+  if (!pmetric && gam > 0.f) {
+    if (g.poisson) {
+      float ps = 0.f;
+      for (int e = lane; e < g.P; e += 32) ps += fmaxf(S[rbase + rowoff[e / g.jL] + e % g.jL], 0.f);
+      Bm = g.s_p * (warp_sum(ps) + (float)g.P * vmaxf);
+    } else {
+      Bm = 2.f * (float)g.P * g.var_g;
+    }
+  }
+  const float kmar = (exact || pmetric) ? 0.f : 3.f * g.ku;
   int iters = (total + 31) / 32;
   for (int it = 0; it < iters; ++it) {
     int c = it * 32 + lane;
@@ -983,8 +1286,16 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           warp_sort(ok, oi, lane);
           warp_merge(lk, li, ok, oi, lane);
         }
-        thr = __shfl_sync(0xffffffffu, lk, g.M - 2 >= 0 ? g.M - 2 : 0);
-        thri = __shfl_sync(0xffffffffu, li, g.M - 2 >= 0 ? g.M - 2 : 0);
+        {
+          const float t = __shfl_sync(0xffffffffu, lk, KP);
+          thri = __shfl_sync(0xffffffffu, li, KP);
+          if (kmar > 0.f && t != FLT_MAX) {
+            thr = t + kmar * (fabsf(t) + 2.f * gam * Bm);
+            thri = INT_MAX;
+          } else {
+            thr = t;
+          }
+        }
       } else if (sorted) {
         break;
       }
@@ -992,10 +1303,14 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
       for (int t = 0; t < KB - 1; ++t) { key[t] = key[t + 1]; idx[t] = idx[t + 1]; }
     }
   }
-  nacc = warp_sum_i(nacc);
   int K = g.M - 1;
   int navail = (int)ncand - 1;
-  int take = min(nacc, K);
+  int take;
+  if (pmetric) {
+    take = min(warp_sum_i(nacc), K);
+  } else {
+    take = decide_group<D>(g, S, rr, org, rowoff, lane, rbase, ridx, (int)ncand, Bm, thr, exact, emin, span, lk, li);
+  }
   if (1 + take < g.min_group) take = min(min(g.min_group - 1, K), navail);
   int count = 1 + take;
   if (g.gtrans == 0) {
@@ -1111,6 +1426,202 @@ __device__ __noinline__ void shared_source_planes(const DGeom &g, int n, int lan
   }
 }
 
+// Entry (l, m) of the group-axis transform in double precision (rows as in
+// group_axis_entry).
+// 1 / sqrt(2^t): 2^(-t/2), times 1/sqrt(2) for odd t (n and b are powers
+// of two for the Haar transform).
+__device__ __forceinline__ double inv_sqrt_pow2(int t) {
+  const double h = ldexp(1.0, -(t >> 1));
+  return (t & 1) ? h * 0.70710678118654752440 : h;
+}
+
+__device__ __forceinline__ double group_axis_entry64(const DGeom &g, int n, int l, int m) {
+  if (g.gtrans != 0) return __ldg(g.dct64 + gen_off(n) + l * n + m);
+  const int tn = 31 - __clz(n);
+  if (l == 0) return inv_sqrt_pow2(tn);
+  const int s = 31 - __clz(l);
+  const int b = n >> s, r = l - (1 << s);
+  if (m < r * b || m >= (r + 1) * b) return 0.0;
+  const double v = inv_sqrt_pow2(tn - s);
+  return m < r * b + b / 2 ? v : -v;
+}
+
+// Hard-threshold decision (Eq. hard-threshold) for coefficient k = (l, q) of
+// a stage-1 group in double precision, for the coefficients whose FP32
+// values lie too close to the threshold to decide: Y_k = sum_i T_ki y_i and
+// sigma_k^2 = sum_i T_ki^2 m_v(u_i) (Lemma "Covariance propagation", Def.
+// "Poisson variance map"), T_ki = A0[l][m] prod_d DCT_d[q_d][p_d] for entry
+// i = (member m, patch entry p); for the leading k_ex planes the
+// shared-source terms of Def. "Partial shared-source Poisson variance model"
+// are added member pair by member pair (as shared_source_planes does);
+// Gaussian noise: sigma_k^2 = sigma^2 (Cor. "White-noise transform
+// variance").  Keeps Y_k iff |Y_k| > lambda sigma_k; two sides equal to a
+// relative 1e-12 are an exact tie in real arithmetic and are not kept.
+// mem: member origins (region offsets), vreg: entry offsets, Sg: the staged
+// observation.  One lane, sequential; the caller counts it.
+__device__ __noinline__ bool ht_keep64(const DGeom &g, int n, int l, int q, const int *__restrict__ mem,
+                                       const int *__restrict__ vreg, const float *__restrict__ Sg) {
+  const int D = g.D;
+  int qc[KMAXD];
+  {
+    int r = q;
+    for (int d = D - 1; d >= 0; --d) {
+      qc[d] = r % g.j[d];
+      r /= g.j[d];
+    }
+  }
+  auto basis = [&](int p) {
+    double f = 1.0;
+    for (int d = D - 1; d >= 0; --d) {
+      const int J = g.j[d];
+      f *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + p % J);
+      p /= J;
+    }
+    return f;
+  };
+  double Y = 0.0, V = 0.0;
+  for (int m = 0; m < n; ++m) {
+    const double a = group_axis_entry64(g, n, l, m);
+    if (a == 0.0) continue;
+    double ys = 0.0, vs = 0.0;
+    for (int p = 0; p < g.P; ++p) {
+      const double f = basis(p);
+      const double y = Sg[mem[m] + vreg[p]];
+      ys = fma(f, y, ys);
+      if (g.poisson) vs = fma(f * f, g.s_p64 * (y > 0.0 ? y : 0.0), vs);
+    }
+    Y = fma(a, ys, Y);
+    V = fma(a * a, vs, V);
+  }
+  if (!g.poisson) {
+    V = g.var64;
+  } else if (l < g.kex) {
+    for (int m = 0; m < n; ++m) {
+      const double am = group_axis_entry64(g, n, l, m);
+      if (am == 0.0) continue;
+      int cm[KMAXD];
+      for (int d = 0; d < D; ++d) cm[d] = (mem[m] / g.rst[d]) % g.RG[d];
+      for (int m2 = m + 1; m2 < n; ++m2) {
+        const double am2 = group_axis_entry64(g, n, l, m2);
+        if (am2 == 0.0) continue;
+        int dl[KMAXD], ext[KMAXD], cnt = 1;
+        for (int d = 0; d < D; ++d) {
+          dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - cm[d];
+          ext[d] = g.j[d] - abs(dl[d]);
+          cnt *= ext[d] > 0 ? ext[d] : 0;
+        }
+        double X = 0.0;
+        for (int e = 0; e < cnt; ++e) {
+          int r = e, off = mem[m];
+          double f1 = 1.0, f2 = 1.0;
+          for (int d = D - 1; d >= 0; --d) {
+            const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
+            r /= ext[d];
+            const int J = g.j[d];
+            f1 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd);
+            f2 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd - dl[d]);
+            off += pd * g.rst[d];
+          }
+          const double y = Sg[off];
+          X = fma(f1 * f2, g.s_p64 * (y > 0.0 ? y : 0.0), X);
+        }
+        V = fma(2.0 * am * am2, X, V);
+      }
+    }
+  }
+  const double t = g.lambda64 * sqrt(V > 0.0 ? V : 0.0);
+  return fabs(Y) - t > 1e-12 * t;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ht_keep64 with the warp's lanes sharing the group's entries (and, for the
+// shared-source planes, its member pairs); every lane calls it with the same
+// (l, q) and gets the same decision.
+__device__ __noinline__ bool ht_keep64_warp(const DGeom &g, int n, int l, int q, const int *__restrict__ mem,
+                                            const int *__restrict__ vreg, const float *__restrict__ Sg, int lane) {
+  const int D = g.D;
+  int qc[KMAXD];
+  {
+    int r = q;
+    for (int d = D - 1; d >= 0; --d) {
+      qc[d] = r % g.j[d];
+      r /= g.j[d];
+    }
+  }
+  double Y = 0.0, V = 0.0;
+  const int tot = n * g.P;
+  for (int e = lane; e < tot; e += 32) {
+    const int m = e / g.P, p = e - m * g.P;
+    const double a = group_axis_entry64(g, n, l, m);
+    if (a == 0.0) continue;
+    double f = a;
+    for (int d = D - 1, r = p; d >= 0; --d) {
+      const int J = g.j[d];
+      f *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + r % J);
+      r /= J;
+    }
+    const double y = Sg[mem[m] + vreg[p]];
+    Y = fma(f, y, Y);
+    if (g.poisson) V = fma(f * f, g.s_p64 * (y > 0.0 ? y : 0.0), V);
+  }
+  if (g.poisson && l < g.kex) {
+    // shared-source terms, member pairs over the lanes
+    for (int t = lane; t < n * n; t += 32) {
+      const int m = t / n, m2 = t - m * n;
+      if (m2 <= m) continue;
+      const double am = group_axis_entry64(g, n, l, m), am2 = group_axis_entry64(g, n, l, m2);
+      if (am == 0.0 || am2 == 0.0) continue;
+      int dl[KMAXD], ext[KMAXD], cnt = 1;
+      for (int d = 0; d < D; ++d) {
+        dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - (mem[m] / g.rst[d]) % g.RG[d];
+        ext[d] = g.j[d] - abs(dl[d]);
+        cnt *= ext[d] > 0 ? ext[d] : 0;
+      }
+      double X = 0.0;
+      for (int e = 0; e < cnt; ++e) {
+        int r = e, off = mem[m];
+        double f1 = 1.0, f2 = 1.0;
+        for (int d = D - 1; d >= 0; --d) {
+          const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
+          r /= ext[d];
+          const int J = g.j[d];
+          f1 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd);
+          f2 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd - dl[d]);
+          off += pd * g.rst[d];
+        }
+        const double y = Sg[off];
+        X = fma(f1 * f2, g.s_p64 * (y > 0.0 ? y : 0.0), X);
+      }
+      V = fma(2.0 * am * am2, X, V);
+    }
+  }
+  Y = warp_sum_d(Y);
+  V = warp_sum_d(V);
+  if (!g.poisson) V = g.var64;
+  const double t = g.lambda64 * sqrt(V > 0.0 ? V : 0.0);
+  return fabs(Y) - t > 1e-12 * t;
+}
+
+// FP32 hard-threshold decision with its error band: |X| > lambda sigma is
+// taken in FP32 unless |X^2 - lambda^2 s2| lies within the error the FP32
+// transforms can carry (eX = 2^-19 ||y_g|| on a coefficient, eS = 2^-20
+// (s2 + sum m_v max T^2) on a variance: eight and thirty-two times the
+// largest errors of the butterfly DCT and Haar measured against double
+// precision on count data, 2^-22 and 2^-25), where the double-precision
+// evaluation decides.  Returns 1 keep, 0 drop, -1 undecided in FP32.
+__device__ __forceinline__ int ht_decide32(float X, float s2, float lam2, float eX, float eS0) {
+  const float xx = X * X, ts = lam2 * s2;
+  const float eS = 9.537e-7f * s2 + eS0;
+  const float band = 2.f * fabsf(X) * eX + eX * eX + lam2 * eS + 2.5e-7f * (xx + ts);
+  if (fabsf(xx - ts) <= band) return -1;
+  return xx > ts ? 1 : 0;
+}
+
 // Entries (m, v) of a group, m < n members, v < P patch entries, visited with
 // a lane stride of 32 and no integer division.
 #define BMND_FOR_ENTRIES(body)                         \
@@ -1191,6 +1702,37 @@ __device__ __forceinline__ float mc_alpha(const DGeom &g, int n, int lane, const
   return z1 > 0.f ? dg / z1 : 0.f;
 }
 
+// Settles the hard-threshold coefficients that FP32 left undecided in the
+// shared-memory filter (lane L's visit k is entry L + 32 k; the coefficient
+// is still in bufB, kept): each decided in double precision by the whole
+// warp; those below the threshold and their weight terms go to zero.
+__device__ __noinline__ void smem_ht_settle(const DGeom &g, int n, int P, int MS, int lane,
+                                            unsigned long long undecided, const int *__restrict__ mem,
+                                            const int *__restrict__ vreg, const int *__restrict__ vbuf,
+                                            const float *__restrict__ Sg, float *bufA, float *bufB) {
+  __syncwarp();
+  unsigned pending = __ballot_sync(0xffffffffu, undecided != 0ull);
+  while (pending) {
+    const int L = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const unsigned long long um = __shfl_sync(0xffffffffu, undecided, L);
+    for (unsigned long long u = um; u; u &= u - 1) {
+      const int k = __ffsll((long long)u) - 1;
+      const int e = L + 32 * k, m = e / P, v = e - m * P;
+      const bool keep = ht_keep64_warp(g, n, m, v, mem, vreg, Sg, lane);
+      if (!keep && lane == 0) {
+        const int a = m * MS + vbuf[v];
+        bufB[a] = 0.f;
+        bufA[a] = 0.f;
+      }
+    }
+  }
+  if (g.diag) {
+    const int t = warp_sum_i(__popcll(undecided));
+    if (lane == 0) atomicAdd(g.diag + 2, (unsigned long long)t);
+  }
+}
+
 // Filters the group whose member origins (region offsets) are in mem[0..n).
 // Stage 1: hard thresholding of T y_g against sigma_k from the variance map;
 // stage 2: Wiener shrinkage of T y_g with gains from the pilot group.  Leaves
@@ -1207,7 +1749,8 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
                                          float *__restrict__ rr_s, const float *mats, const int *moff,
                                          const float *tab, const float *__restrict__ gy,
                                          const float *__restrict__ ge, const int64_t *__restrict__ gb,
-                                         const int64_t *__restrict__ vgl, float *alpha_out) {
+                                         const int64_t *__restrict__ vgl, float *alpha_out,
+                                         unsigned long long *diag) {
   using SH = CubeShape<D, JC>;
   const int P = SH::fixed ? SH::P : g.P;
   const int MS = SH::fixed ? SH::MS : g.MS;
@@ -1217,10 +1760,14 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
   // gather / shrink / gain step.
   //   stage 1: T^2 m_v (Poisson) | T y_g | shrink, weights | T^T C
   //   stage 2: T^2 m_v (Poisson) | T gamma_g | gains, weights | T y_g | G Y, T^T C
-  const float lam = g.lambda * 1.0001f, lam2 = lam * lam;
+  const float lam2 = g.lambda * g.lambda;
   float *syn = stage2 ? bufA : bufB;
   const int first = g.poisson ? 0 : 1;
   const int last = stage2 ? 4 : 3;
+  // stage-1 hard threshold: group norm and variance-map total for the FP32
+  // error band of the decision (ht_decide32)
+  const bool hard = !stage2 && !g.soft;
+  float n2 = 0.f, sm = 0.f;
   for (int ph = first; ph <= last; ++ph) {
     float *tb;
     int tmode;
@@ -1232,14 +1779,21 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         const float gv = Sg[mem[m] + vreg[v]];
         const int a = m * MS + vbuf[v];
         bufB[a] = gv;
-        bufA[a] = g.s_p * fmaxf(gv, 0.f);
+        const float mv = g.s_p * fmaxf(gv, 0.f);
+        bufA[a] = mv;
+        n2 = fmaf(gv, gv, n2);
+        sm += mv;
       });
       __syncwarp();
       tb = bufA;
       tmode = 2;
     } else if (ph == 1) {
       if (!g.poisson) {
-        BMND_FOR_ENTRIES({ bufB[m * MS + vbuf[v]] = Sg[mem[m] + vreg[v]]; });
+        BMND_FOR_ENTRIES({
+          const float gv = Sg[mem[m] + vreg[v]];
+          bufB[m * MS + vbuf[v]] = gv;
+          n2 = fmaf(gv, gv, n2);
+        });
         __syncwarp();
       }
       tb = bufB;
@@ -1249,6 +1803,18 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         shared_source_planes(g, n, lane, mem, vbuf, Sg, bufA, MS, mats, moff, tab);
         __syncwarp();
       }
+      float eX = 0.f, eS0 = 0.f;
+      if (hard) {
+        n2 = warp_sum(n2);
+        sm = warp_sum(sm);
+        const float a2 = n == 1 ? 1.f : (g.gtrans == 0 ? 0.5f : 2.f / (float)n);
+        eX = 1.9073e-6f * sqrtf(n2);
+        eS0 = 9.537e-7f * sm * a2 * g.ht_t2 * (g.kex > 0 ? 16.f : 1.f);
+      }
+      // undecided hard-threshold coefficients of this lane, by visit number
+      // (entries lane + 32 k); kept until settled below
+      unsigned long long undecided = 0ull;
+      int visit = 0;
       // ---- shrinkage; per-coefficient weight terms into bufA ----
       BMND_FOR_ENTRIES({
         const int a = m * MS + vbuf[v];
@@ -1264,11 +1830,14 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
           bufB[a] = att * X;
           wterm = att * att * (g.wmodel == 0 ? 1.f : s2);
         } else if (!stage2) {
-          // |X| > lambda sigma with a relative guard of 1e-4 (exact ties,
-          // common with count data, are zeroed whatever the rounding)
-          const bool keep = X * X > lam2 * s2;
-          bufB[a] = keep ? X : 0.f;
-          wterm = keep ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
+          // |X| > lambda sigma; undecided in FP32: kept until settled
+          int kp = ht_decide32(X, s2, lam2, eX, eS0);
+          if (kp < 0) {
+            if (visit < 64) undecided |= 1ull << visit;
+            else kp = ht_keep64(g, n, m, v, mem, vreg, Sg) ? 1 : 0;  // past 64 visits: at once
+          }
+          bufB[a] = kp ? X : 0.f;
+          wterm = kp ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
         } else {
           const float S = fmaxf(X * X - g.a_power * s2, 0.f);
           const float den = S + g.s_v * s2;
@@ -1279,7 +1848,10 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         }
         if (g.wdomain) wterm *= syn_energy(g, v);
         bufA[a] = wterm;
+        ++visit;
       });
+      if (hard && __any_sync(0xffffffffu, undecided != 0ull))
+        smem_ht_settle(g, n, P, MS, lane, undecided, mem, vreg, vbuf, Sg, bufA, bufB);
       __syncwarp();
       // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums
       // its row, starting at its own entry so the reads spread over banks) ----
@@ -1374,8 +1946,12 @@ __device__ __forceinline__ void col_store(float *buf, int v, const float (&y)[N]
 // Stage 1, one column: sigma^2 = H^2 s (s = T_patch^2 m_v in bufA, or the
 // Gaussian variance), X = H x, hard threshold with weight terms into bufA,
 // then H^T of the kept coefficients back into bufB.
+// Returns the planes whose hard-threshold decision FP32 cannot take
+// (bitmask); they are kept for now and settled by col_ht_settle.
 template <int N, int MS>
-__device__ __forceinline__ void col_hard_threshold(const DGeom &g, float *bufA, float *bufB, int v, float lam2) {
+__device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bufA, float *bufB, int v, float lam2,
+                                                       float eX, float eS0) {
+  unsigned undecided = 0u;
   float X[N], S[N];
   col_load<N, MS>(X, bufB, v);
   haar_fwd_levels<N, N, false>(X);
@@ -1399,13 +1975,32 @@ __device__ __forceinline__ void col_hard_threshold(const DGeom &g, float *bufA, 
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      // |X| > lambda sigma with a relative guard of 1e-4 (exact ties, common
-      // with count data, are zeroed whatever the rounding)
-      const bool keep = X[m] * X[m] > lam2 * S[m];
-      bufA[m * MS + v] = keep ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
-      X[m] = keep ? X[m] : 0.f;
+      // |X| > lambda sigma; undecided in FP32: kept until col_ht_settle
+      const int kp = ht_decide32(X[m], S[m], lam2, eX, eS0);
+      if (kp < 0) undecided |= 1u << m;
+      bufA[m * MS + v] = kp ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
+      X[m] = kp ? X[m] : 0.f;
     }
   }
+  haar_inv_levels<N, 2>(X);
+  col_store<N, MS>(bufB, v, X);
+  return undecided;
+}
+
+// Drops the planes in `drop` from the stored column v (H^T of the kept
+// coefficients): forward Haar, zero, inverse Haar; their weight terms go to
+// zero.
+template <int N, int MS>
+__device__ __forceinline__ void col_ht_drop(float *bufA, float *bufB, int v, unsigned drop) {
+  float X[N];
+  col_load<N, MS>(X, bufB, v);
+  haar_fwd_levels<N, N, false>(X);
+#pragma unroll
+  for (int m = 0; m < N; ++m)
+    if (drop & (1u << m)) {
+      X[m] = 0.f;
+      bufA[m * MS + v] = 0.f;
+    }
   haar_inv_levels<N, 2>(X);
   col_store<N, MS>(bufB, v, X);
 }
@@ -1461,6 +2056,42 @@ __device__ __forceinline__ void col_wiener_apply(float *bufA, const float *bufB,
     }                                                                \
   }
 
+// Settles the hard-threshold coefficients that FP32 left undecided in the
+// register filter (one column per lane, `undecided` the lane's planes; they
+// were kept): each decided in double precision by the whole warp, and the
+// columns of those below the threshold redone without them.
+template <int MS>
+__device__ __noinline__ void rf_ht_settle(const DGeom &g, int n, int lane, unsigned undecided,
+                                          const int *__restrict__ mem, const int *__restrict__ vreg,
+                                          const float *__restrict__ Sg, float *bufA, float *bufB) {
+  unsigned pending = __ballot_sync(0xffffffffu, undecided != 0u);
+  unsigned drop = 0u;
+  while (pending) {
+    const int L = __ffs(pending) - 1;
+    pending &= pending - 1;
+    for (unsigned u = __shfl_sync(0xffffffffu, undecided, L); u; u &= u - 1) {
+      const int m = __ffs(u) - 1;
+      const bool keep = ht_keep64_warp(g, n, m, L, mem, vreg, Sg, lane);
+      if (!keep && lane == L) drop |= 1u << m;
+    }
+  }
+  if (drop) {
+    const int v = lane;
+    switch (n) {
+      case 1: col_ht_drop<1, MS>(bufA, bufB, v, drop); break;
+      case 2: col_ht_drop<2, MS>(bufA, bufB, v, drop); break;
+      case 4: col_ht_drop<4, MS>(bufA, bufB, v, drop); break;
+      case 8: col_ht_drop<8, MS>(bufA, bufB, v, drop); break;
+      case 16: col_ht_drop<16, MS>(bufA, bufB, v, drop); break;
+      default: col_ht_drop<32, MS>(bufA, bufB, v, drop); break;
+    }
+  }
+  if (g.diag) {
+    const int t = warp_sum_i(__popc(undecided));
+    if (lane == 0) atomicAdd(g.diag + 2, (unsigned long long)t);
+  }
+}
+
 template <int D, int JC, int ST>
 __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, int lane, const int *__restrict__ mem,
                                             const int *__restrict__ vreg, const float *__restrict__ omega,
@@ -1469,7 +2100,8 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
                                             float *__restrict__ bufB, float *__restrict__ wts,
                                             float *__restrict__ rr_s, const float *__restrict__ gy,
                                             const float *__restrict__ ge, const int64_t *__restrict__ gb,
-                                            const int64_t *__restrict__ vgl, float *alpha_out) {
+                                            const int64_t *__restrict__ vgl, float *alpha_out,
+                                            unsigned long long *diag) {
   constexpr int P = ipow(JC, D);
   constexpr int MS = CubeShape<D, JC>::MS;
   static_assert(MS == (P | 1), "register filter layout");
@@ -1508,6 +2140,25 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   // guide group into bufB; for Poisson data also T_patch^2 m_v into bufA
   gather(bufB, Sg);
   __syncwarp();
+  // stage-1 hard threshold: group norm and variance-map total (s_P times
+  // the positive part of y_g) for the FP32 error band of the decision
+  // (ht_decide32), from the gathered values
+  float eX = 0.f, eS0 = 0.f;
+  if (!stage2 && !g.soft) {
+    float n2 = 0.f, sm = 0.f;
+    for (int e = lane; e < n * P; e += 32) {
+      const float gv = bufB[(e / P) * MS + e % P];
+      n2 = fmaf(gv, gv, n2);
+      sm += fmaxf(gv, 0.f);
+    }
+    n2 = warp_sum(n2);
+    eX = 1.9073e-6f * sqrtf(n2);
+    if (g.poisson) {
+      sm = warp_sum(sm) * g.s_p;
+      const float a2 = n == 1 ? 1.f : 0.5f;
+      eS0 = 9.537e-7f * sm * a2 * g.ht_t2;
+    }
+  }
   if (g.poisson && lane < n) {
     float x[P];
     const float *row = bufB + lane * MS;
@@ -1521,10 +2172,13 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   row_dct(bufB, F{});
   __syncwarp();
   if (!stage2) {
-    const float lam = g.lambda * 1.0001f, lam2 = lam * lam;
-#define BMND_OP(NN) col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2)
+    const float lam2 = g.lambda * g.lambda;
+    // one column per lane (P <= 32): the undecided planes of column `lane`
+    unsigned undecided = 0u;
+#define BMND_OP(NN) undecided = col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2, eX, eS0)
     BMND_COLUMNS(BMND_OP)
 #undef BMND_OP
+    if (__any_sync(0xffffffffu, undecided != 0u)) rf_ht_settle<MS>(g, n, lane, undecided, mem, vreg, Sg, bufA, bufB);
   } else {
 #define BMND_OP(NN) col_wiener_gain<NN, MS>(g, bufA, bufB, v)
     BMND_COLUMNS(BMND_OP)
@@ -1658,13 +2312,19 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_tile;
+  __shared__ int s_emin;           // lowest set-bit exponent of the staged guide values
+  __shared__ unsigned s_vmax;      // largest |value| (float bits)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   DJob *sj = reinterpret_cast<DJob *>(smem);
   int cur_job = -1;
   SmemLayout L;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(counter, 1);
+      s_emin = INT_MAX;
+      s_vmax = 0u;
+    }
     __syncthreads();
     const int gt = s_tile;
     if (gt >= total_tiles) break;
@@ -1795,6 +2455,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     const float *gsrc = sj->guide, *ysrc = sj->y, *esrc = sj->eta;
     const int RS = g.region + RPAD;
     bool nonneg_t = true;
+    int emin_t = INT_MAX;
+    unsigned vmax_t = 0u;
     for (int e = threadIdx.x; e < RS; e += blockDim.x) {
       float vg = 0.f, vy = 0.f, ve = 0.f;
       if (e < g.region) {
@@ -1829,8 +2491,46 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         if (mc2 && !g.lean) Se[e] = ve;
       }
       nonneg_t = nonneg_t && vg >= 0.f;
+      if (vg != 0.f) {
+        // vg = mant 2^(ex - 150) with a 24-bit mantissa: the exponent of its
+        // lowest set bit
+        const unsigned bits = __float_as_uint(vg) & 0x7fffffffu;
+        const int ex = (int)(bits >> 23);
+        const unsigned mant = (bits & 0x7fffffu) | (ex ? 0x800000u : 0u);
+        emin_t = min(emin_t, (ex ? ex : 1) - 150 + __ffs(mant) - 1);
+        vmax_t = max(vmax_t, bits);
+      }
+    }
+    if (!mc2) {
+      if (emin_t != INT_MAX) atomicMin(&s_emin, emin_t);
+      if (vmax_t) atomicMax(&s_vmax, vmax_t);
     }
     const bool tile_nonneg = __syncthreads_and(nonneg_t) != 0;
+    // Exact tile (stage-1 SSD, s_P = 2^k, integral gamma): the staged values
+    // are multiples of q0 = 2^emin of magnitude at most V q0.  Differences,
+    // squares, the SSD, the bias sum, s_P times it and the score are then
+    // multiples of u = min(q0^2, q0 s_P) below 2^23 u, all exact in FP32:
+    // P (2V)^2 q0^2 for the SSD and gamma 2 P V q0 s_P for gamma B.
+    bool tile_exact = false;
+    if (g.exact_ok && !mc2 && !stage2) {
+      if (s_vmax == 0u) {
+        tile_exact = true;
+      } else {
+        const double q0 = ldexp(1.0, s_emin);
+        const double V = (double)__uint_as_float(s_vmax) / q0;
+        const double r = g.s_p64 / q0;
+        const double unit_rel = r < 1.0 ? r : 1.0;  // u / q0^2
+        const double big = (4.0 * g.P * V * V + g.gamma64 * 2.0 * g.P * V * r) / unit_rel;
+        tile_exact = big < 8388608.0 && r * 16777216.0 >= 1.0;
+      }
+    }
+    // integer span of the tile's guide values for the exact scores
+    int tile_emin = 0, tile_span = 0;
+    const float tile_vmax = __uint_as_float(s_vmax);
+    if (!mc2 && s_vmax != 0u) {
+      tile_emin = s_emin;
+      tile_span = (int)(s_vmax >> 23) - 126 - s_emin;  // |v| < 2^(exponent + 1)
+    }
 
     const int nref = sj->ref_count[tile];
     const int rounds = (nref + NW - 1) / NW;
@@ -1849,7 +2549,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           for (int d = D - 1; d >= 0; --d) { rr[d] = rem % g.C[d] + g.rad[d]; rem /= g.C[d]; }
         }
         if (!mc2) {
-          n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg);
+          n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg, tile_exact, tile_emin,
+                                        tile_span, tile_vmax, g.diag);
           if (sj->groups) {
             for (int m = lane; m < g.M; m += 32)
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
@@ -1945,10 +2646,10 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             int which;
             if constexpr (SH::rf)
               which = filter_group_rf<D, JL, ST>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
-                                             sj->y, sj->eta, gb, L.vgl, &alpha);
+                                             sj->y, sj->eta, gb, L.vgl, &alpha, g.diag);
             else
               which = filter_group<D, JL, ST>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
-                                          rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha);
+                                          rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha, g.diag);
             syn = which ? bufA : bufB;
             if (!mc2 && cached && sj->groups) {
               // first sweep of a mass-conserving stage: keep the synthesis

@@ -104,7 +104,33 @@ struct DGeom {
   int kex;
   float mt, beta_p, kappa, inv_sp;
   const float2 *mom;
+  // Decisions in double precision.  Matching ranks and accepts candidates,
+  // and the hard threshold keeps coefficients, by comparisons that the FP32
+  // fast path can only take where its error bound separates the two sides;
+  // the rest are re-evaluated in double precision with these scalars as
+  // the definitions have them: s_P, gamma, the Gaussian bias 2 P sigma^2
+  // (0 for Poisson noise), tau, lambda and sigma^2; dct64 holds the
+  // orthonormal DCT-II matrices of sizes 1..32 at gen_off(J).  ku bounds the
+  // error of an FP32 SSD score per unit of its magnitude (ssd + gamma B);
+  // ht_t2 is the largest squared entry of the spatial transform.  exact_ok:
+  // stage-1 SSD with s_P a power of two and an integral gamma, where tiles
+  // of dyadic data score exactly in FP32.
+  double s_p64, gamma64, gbias64, tau64, lambda64, var64;
+  const double *dct64;
+  float ku, ht_t2;
+  int exact_ok;
+  int pad_dd;
+  // counters of the double-precision decisions (or null): [0] candidates
+  // rescored, [1] full double-precision searches, [2] coefficients decided
+  // in double precision at the hard threshold
+  unsigned long long *diag;
 };
+
+// Layout of the transform tables in device memory: the float DCT table
+// (2 GEN_TOTAL floats, see above) and at TAB64_OFFSET bytes the double
+// matrices (GEN_TOTAL doubles, same offsets).
+constexpr int TAB64_OFFSET = ((2 * GEN_TOTAL * 4) + 255) & ~255;
+constexpr int TAB_BYTES = TAB64_OFFSET + GEN_TOTAL * 8;
 
 constexpr int MOMENT_NMAX = 4096;
 

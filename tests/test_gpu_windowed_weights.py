@@ -69,7 +69,7 @@ def test_denoise_windowed_mass_conserving(ctx, oracle, case):
     import torch
     import paper_2609_34622_b300.bmnd as bm
     name, y, x, cfg = case
-    ref, _ = oracle.denoise(_op(oracle, y, cfg, 3), y)
+    ref = PT.oracle_two_stages_f32_pilot(oracle, _op(oracle, y, cfg, 3), y)
     out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
     ctx.bmnd_denoise(_cuda(y), out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], cfg["group_size"], 2,
                      3, bm.params(weight_domain="windowed_synthesis"))

@@ -262,3 +262,59 @@ def test_contributions_symmetric_nonnegative(oracle, metric):
         assert a == pytest.approx(b, rel=1e-12, abs=1e-15)
         assert a > 0.0
         assert oracle.phi(metric, r, r) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_exact_sum_is_fsum(oracle):
+    """The oracle's summation of Poisson contributions equals Python's
+    math.fsum (Shewchuk's exact summation rounded once) on sums that a
+    sequential double sum gets wrong, and does not depend on term order."""
+    rng = np.random.default_rng(4)
+    for k in range(100):
+        x = rng.standard_normal(int(rng.integers(1, 70))) * 10.0 ** int(rng.integers(-12, 12))
+        x = np.concatenate([x, [1e16, 1.0, -1e16], x[:2] * 1e-20])
+        assert oracle.exact_sum(x) == math.fsum(x)
+        assert oracle.exact_sum(x[rng.permutation(len(x))]) == oracle.exact_sum(x)
+    assert oracle.exact_sum([1e16, 1.0, -1e16]) == 1.0
+
+
+@pytest.mark.parametrize("metric,a,b", [
+    ("ssd", (29, 3, 2, 2, 4, 13, 24, 19), (2, 13, 2, 4, 3, 24, 19, 29)),
+    ("poisson_deviance", (9, 8, 27, 24, 25, 5, 12, 11), (12, 9, 27, 25, 11, 8, 5, 24)),
+    ("pearson", (0, 28, 17, 6, 23, 17, 2, 20), (0, 20, 28, 17, 2, 17, 23, 6)),
+    ("anscombe_ssd", (21, 19, 18, 6, 28, 11, 15, 9), (18, 21, 19, 11, 28, 15, 9, 6))])
+def test_permuted_patches_tie_exactly(oracle, metric, a, b):
+    """Two candidates whose per-entry terms are a permutation of each other
+    tie in real arithmetic; their scores must be equal, so that the smaller
+    index ranks first (App. A group order).  Guide: the reference counts 7 on
+    all 8 entries at origin 0, a candidate at origin 8 and a permutation of it
+    at origin 16, s_P = 0.1 (raw counts not exact in binary).  SSD: gamma = 0
+    (Eq. ssd); the Poisson distances: standardized policy, every candidate
+    accepted.  The pairs are chosen so that a sequential double-precision
+    sum splits the tie (checked here)."""
+    s_p = 0.1
+    P = 8
+    ref = np.full(P, 7.0)
+    a, b = np.array(a, float), np.array(b, float)
+    g = (np.concatenate([ref, a, b]) * s_p).astype(np.float32).astype(np.float64)
+    counts = g / s_p
+
+    def seqsum(v):
+        t = 0.0
+        for x in v:
+            t += x
+        return t
+
+    if metric == "ssd":
+        seq = [seqsum((g[o:o + P] - g[:P]) ** 2) for o in (P, 2 * P)]
+        p = oracle.params(g.shape, (P,), (1,), (33,), ("poisson", s_p), (32, 32), gamma_ht=0.0, tau_ht=1e9,
+                          group_transform="dct")
+    else:
+        seq = [seqsum([oracle.phi(metric, r, c) for r, c in zip(counts[:P], counts[o:o + P])]) for o in (P, 2 * P)]
+        p = oracle.params(g.shape, (P,), (1,), (33,), ("poisson", s_p), (32, 32), group_transform="dct", match_metric=metric,
+                          match_policy="candidate_standardized", match_t=1e9)
+    assert seq[0] != seq[1]
+    mem, sc = oracle.match_ref(p, g, 1, 0)
+    scores = dict(zip(mem[1:], sc[1:]))
+    assert P in scores and 2 * P in scores
+    assert scores[P] == scores[2 * P]
+    assert list(mem).index(P) < list(mem).index(2 * P)
