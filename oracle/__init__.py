@@ -111,6 +111,8 @@ def _load():
         _lib.or_phi.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib.or_phi.restype = ctypes.c_double
         _lib.or_moments.argtypes = [ctypes.c_int, ctypes.c_int, d, d]
+        _lib.or_raw_count_of.argtypes = [P(_Params), ctypes.c_double]
+        _lib.or_raw_count_of.restype = ctypes.c_double
         _lib.or_exact_sum.argtypes = [d, ctypes.c_int64]
         _lib.or_exact_sum.restype = ctypes.c_double
         _lib.or_moment_table_f32.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_float), P(ctypes.c_float)]
@@ -345,3 +347,9 @@ def exact_sum(x) -> float:
     """The oracle's exact summation (Shewchuk expansions, rounded once)."""
     a = _f64(x).ravel()
     return _load().or_exact_sum(_dptr(a), len(a))
+
+
+def raw_count(p: _Params, v: float) -> float:
+    """Eq. (raw-counts) with the integer reading: the nearest integer when
+    y / s_P lies within a relative 2^-20 of it, else [y / s_P]_+."""
+    return _load().or_raw_count_of(ctypes.byref(p), float(v))

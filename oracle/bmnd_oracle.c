@@ -543,8 +543,20 @@ static int or_count_index(double x)
     return (int)rint(x);
 }
 
-/* Eq. (raw-counts): [p / s_P]_+. */
-static double or_raw_count(const or_params *p, double v) { return pos(v / p->s_p); }
+/* Eq. (raw-counts): [p / s_P]_+.  READING: the raw counts of Poisson data
+ * are the integers K of y = s_P K; a float32 observation carries a relative
+ * rounding of 2^-24, so a value of y / s_P within a relative 2^-20 of an
+ * integer (at least 1) is that integer.  Other values are kept as they are. */
+static double or_raw_count(const or_params *p, double v)
+{
+    double r = pos(v / p->s_p);
+    double k = rint(r);
+    double tol = ldexp(k > 1.0 ? k : 1.0, -20);
+    return fabs(r - k) <= tol ? k : r;
+}
+
+/* Exported for the tests: the raw count of one observed value. */
+double or_raw_count_of(const or_params *p, double v) { return or_raw_count(p, v); }
 
 /* Acceptance threshold of one reference in sum units (P d_m), from the
  * reference patch alone (entries pr[off[i]]):

@@ -65,6 +65,8 @@ struct bmnd_ctx {
   // finite-count moment tables (mu, v) of the Poisson matching distances,
   // n = 0..BMND_MOMENT_NMAX, built on first use
   float2 *mom[4] = {nullptr, nullptr, nullptr, nullptr};
+  // fixed-point tables of the Poisson distances for count data (PFIX_*)
+  long long *pfix[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -323,15 +325,15 @@ double contribution(int metric, double r, double c) {
 // Pascal's rule, w_n(x) = (w_{n-1}(x) + w_{n-1}(x-1)) / 2.  n = 0 has the
 // single allocation (0, 0); at n = 1 both allocations contribute equally, so
 // v = 0 exactly.  A variance that rounding makes negative becomes 0.
-void moment_table(int metric, int count, std::vector<float2> &out) {
-  out.assign(count, make_float2(0.f, 0.f));
+void moment_table64(int metric, int count, std::vector<double2> &out) {
+  out.assign(count, make_double2(0.0, 0.0));
   std::vector<double> w(count + 1, 0.0);
   w[0] = 1.0;
   for (int n = 1; n < count; ++n) {
     for (int x = n; x >= 1; --x) w[x] = 0.5 * (w[x] + w[x - 1]);
     w[0] *= 0.5;
     if (n == 1) {
-      out[1] = make_float2((float)contribution(metric, 1.0, 0.0), 0.f);
+      out[1] = make_double2(contribution(metric, 1.0, 0.0), 0.0);
       continue;
     }
     double m1 = 0, m2 = 0;
@@ -341,7 +343,40 @@ void moment_table(int metric, int count, std::vector<float2> &out) {
       m1 += w[x] * f;
       m2 += w[x] * f * f;
     }
-    out[n] = make_float2((float)m1, (float)std::max(m2 - m1 * m1, 0.0));
+    out[n] = make_double2(m1, std::max(m2 - m1 * m1, 0.0));
+  }
+}
+
+void moment_table(int metric, int count, std::vector<float2> &out) {
+  std::vector<double2> m;
+  moment_table64(metric, count, m);
+  out.resize(count);
+  for (int n = 0; n < count; ++n) out[n] = make_float2((float)m[n].x, (float)m[n].y);
+}
+
+// Fixed-point tables of one Poisson distance (layout PFIX_* of the kernel
+// header): the per-entry contributions of Eqs. (deviance), (pearson),
+// (anscombe-distance) at integer counts in closed form, and the moments.
+void fixed_tables(int metric, std::vector<long long> &t) {
+  t.assign(PFIX_TOTAL, 0);
+  const double two32 = 4294967296.0;
+  for (int k = 0; k <= PFIX_K; ++k) {
+    const double K = (double)k;
+    if (metric == BMND_METRIC_DEVIANCE) {
+      t[PFIX_A + k] = k > 0 ? std::llround(K * std::log(2.0 * K) * two32) : 0;
+      t[PFIX_B + k] = k > 1 ? std::llround(K * std::log(K) * two32) : 0;
+    } else if (metric == BMND_METRIC_PEARSON) {
+      t[PFIX_A + k] = k > 1 ? (long long)(((unsigned __int128)1 << 64) / (unsigned)k)
+                            : (k == 1 ? (long long)~0ull : 0);
+    } else {
+      t[PFIX_A + k] = std::llround(2.0 * std::sqrt(K + 0.375) * 17592186044416.0);  // 2^44
+    }
+  }
+  std::vector<double2> m;
+  moment_table64(metric, BMND_MOMENT_NMAX + 1, m);
+  for (int n = 0; n <= BMND_MOMENT_NMAX; ++n) {
+    t[PFIX_MU + n] = std::llround(m[n].x * two32);
+    t[PFIX_V + n] = std::llround(m[n].y * two32);
   }
 }
 
@@ -360,6 +395,19 @@ bmnd_status ensure_moments(bmnd_ctx *ctx, int metric) {
     return fail(ctx, BMND_ECUDA, "upload of the moment table failed");
   }
   ctx->mom[metric] = d;
+  std::vector<long long> t;
+  fixed_tables(metric, t);
+  long long *dt = nullptr;
+  if (cudaMalloc(&dt, t.size() * sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, BMND_ENOMEM, "cudaMalloc of the fixed-point tables failed");
+  }
+  if (cudaMemcpy(dt, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dt);
+    return fail(ctx, BMND_ECUDA, "upload of the fixed-point tables failed");
+  }
+  ctx->pfix[metric] = dt;
   return BMND_OK;
 }
 
@@ -461,6 +509,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     bmnd_status rc = ensure_moments(ctx, pl.metric);
     if (rc != BMND_OK) return rc;
     g.mom = ctx->mom[pl.metric];
+    g.pfix = ctx->pfix[pl.metric];
   }
   if (cube_side(D, g.j, pl.gtrans, pl.kex) && g.P <= 32) {
     // specialized kernels with members in registers: unpadded rows, odd
@@ -635,6 +684,9 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
     g.mt = (float)pr.match_t;
     g.beta_p = (float)(pr.beta_s * g.P);
     g.kappa = (float)pr.kappa_s;
+    g.mt64 = pr.match_t;
+    g.beta_p64 = pr.beta_s * (double)g.P;
+    g.kappa64 = pr.kappa_s;
     g.inv_sp = (float)(1.0 / nz.poisson_scale);
   }
   g.lambda = (float)pr.lambda_ht;
@@ -651,12 +703,23 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   g.gamma64 = g.metric == BMND_METRIC_SSD ? gamma : 0.0;
   g.gbias64 = g.poisson ? 0.0 : 2.0 * (double)g.P * nz.sigma * nz.sigma;
   g.tau64 = tau;
+  if (g.metric != BMND_METRIC_SSD) {
+    if (g.policy == BMND_POLICY_FIXED) {
+      const double tf = pr.tau_ht > 0 ? pr.tau_ht : 1.0 + pr.match_t * std::sqrt(2.0 / g.P);
+      g.tau64 = tf * g.P;
+    } else if (g.policy == BMND_POLICY_STANDARDIZED) {
+      g.tau64 = pr.match_t;
+    }
+  }
   g.lambda64 = pr.lambda_ht;
   g.var64 = g.poisson ? 0.0 : nz.sigma * nz.sigma;
   // |s32 - s| <= (P + 6) 2^-24 (ssd + gamma B) for the FP32 score (one
   // rounding per entry in the SSD and the bias sums, a few in the
   // combination), with margin
   g.ku = (float)((g.P + 8) * std::ldexp(1.0, -24) * 1.05);
+  // Poisson distances on count data: exact integer sums, so a float key is
+  // off by its own rounding only (the standardized one by a few roundings)
+  if (g.metric != BMND_METRIC_SSD) g.ku = (float)std::ldexp(1.0, g.policy == BMND_POLICY_STANDARDIZED ? -20 : -22);
   double t2 = 1.0;
   for (int a = 0; a < g.D; ++a) t2 *= g.j[a] >= 2 ? 2.0 / g.j[a] : 1.0;
   g.ht_t2 = (float)t2;
@@ -1081,6 +1144,8 @@ bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
   if (ctx->staged) cudaEventDestroy(ctx->staged);
   for (auto m : ctx->mom)
+    if (m) cudaFree(m);
+  for (auto m : ctx->pfix)
     if (m) cudaFree(m);
   delete ctx;
   return BMND_OK;

@@ -780,6 +780,151 @@ __device__ __noinline__ float metric_threshold(const DGeom &g, const float *p, c
   return __fadd_rn(__fadd_rn(ms, __fmul_rn(g.mt, __fsqrt_rn(vs))), allow);
 }
 
+// Poisson distances on count data in exact integer arithmetic.  When every
+// staged value of a tile is s_P times an integer count K <= PFIX_K / 2 (to
+// within float rounding; Eq. raw-counts), the per-entry contributions come
+// from fixed-point tables (units 2^-32) and a candidate's sums are exact
+// 64-bit integers: they depend only on the multiset of its terms, and two
+// candidates compare as the sums of their contributions rounded to the
+// tables' 2^-33 compare.
+
+// The count K of a staged value v (v * float(1 / s_P) rounded).
+__device__ __forceinline__ int count_of(float v, float inv) { return max(__float2int_rn(v * inv), 0); }
+
+// phi_m(r, c) of Eq. (varphi) at integer counts, units 2^-32:
+// deviance 2 (r ln 2r + c ln 2c - n ln n), Pearson (r - c)^2 / n,
+// Anscombe (A(c) - A(r))^2 / 2 with A(K) = 2 sqrt(K + 3/8).
+template <int METRIC>
+__device__ __forceinline__ long long phi_fix(const long long *__restrict__ T, int r, int c) {
+  const int n = r + c;
+  if (METRIC == 1) return 2 * (__ldg(T + PFIX_A + r) + __ldg(T + PFIX_A + c) - __ldg(T + PFIX_B + n));
+  if (METRIC == 2) {
+    if (n == 0) return 0;
+    const unsigned long long d = (unsigned long long)abs(r - c);
+    return (long long)__umul64hi((d * d) << 32, (unsigned long long)__ldg(T + PFIX_A + n));
+  }
+  const long long dA = __ldg(T + PFIX_A + c) - __ldg(T + PFIX_A + r);  // units 2^-44
+  const unsigned long long ad = (unsigned long long)(dA < 0 ? -dA : dA);
+  const unsigned long long lo = ad * ad, hi = __umul64hi(ad, ad);    // (dA)^2, units 2^-88
+  return (long long)((hi << 7) | (lo >> 57));                         // / 2, units 2^-32
+}
+
+// Exact sums of the KB candidates q + b (b < KB) against the reference p:
+// acc = sum phi, and for the standardized policy ms / vs = sum of the
+// moments at the pooled counts (units 2^-32).
+template <int METRIC, bool STD, int KB>
+__device__ __forceinline__ void metric_block_fix(const DGeom &g, const float *p, const float *q, const int *rowoff,
+                                                 long long (&acc)[KB], long long (&ms)[KB], long long (&vs)[KB]) {
+  const float inv = g.inv_sp;
+  const long long *T = g.pfix;
+#pragma unroll
+  for (int b = 0; b < KB; ++b) { acc[b] = 0; ms[b] = 0; vs[b] = 0; }
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = p + rowoff[r], *qr = q + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const int rv = count_of(pr[i], inv);
+#pragma unroll
+      for (int b = 0; b < KB; ++b) {
+        const int cv = count_of(qr[i + b], inv);
+        acc[b] += phi_fix<METRIC>(T, rv, cv);
+        if (STD) {
+          const int n = min(rv + cv, MOMENT_NMAX);
+          ms[b] += __ldg(T + PFIX_MU + n);
+          vs[b] += __ldg(T + PFIX_V + n);
+        }
+      }
+    }
+  }
+}
+
+// The score of candidates from their exact sums: P d_m (fixed and reference
+// policies) or Z_m of Eq. (standardized-distance), in float for the list
+// (key) or in double for a decision.
+__device__ __forceinline__ float pm_key(int policy, long long acc, long long ms, long long vs) {
+  if (policy != 2) return __ll2float_rn(acc) * 2.3283064365386963e-10f;
+  if (vs <= 0) return 0.f;
+  return __ll2float_rn(acc - ms) * 1.52587890625e-05f * rsqrtf(__ll2float_rn(vs));
+}
+__device__ __forceinline__ double pm_score64(int policy, long long acc, long long ms, long long vs) {
+  if (policy != 2) return ldexp(__ll2double_rn(acc), -32);
+  if (vs <= 0) return 0.0;
+  return ldexp(__ll2double_rn(acc - ms), -16) / sqrt(__ll2double_rn(vs));
+}
+
+template <int KB>
+__device__ __forceinline__ void metric_keys_fix(const DGeom &g, const float *p, const float *q, const int *rowoff,
+                                                float (&key)[KB]) {
+  long long acc[KB], ms[KB], vs[KB];
+  const bool st = g.policy == 2;
+  switch (g.metric) {
+    case 1:
+      if (st) metric_block_fix<1, true, KB>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<1, false, KB>(g, p, q, rowoff, acc, ms, vs);
+      break;
+    case 2:
+      if (st) metric_block_fix<2, true, KB>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<2, false, KB>(g, p, q, rowoff, acc, ms, vs);
+      break;
+    default:
+      if (st) metric_block_fix<3, true, KB>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<3, false, KB>(g, p, q, rowoff, acc, ms, vs);
+      break;
+  }
+#pragma unroll
+  for (int b = 0; b < KB; ++b) key[b] = pm_key(g.policy, acc[b], ms[b], vs[b]);
+}
+
+// Double-precision score of one candidate (count data).
+__device__ __noinline__ double pm_exact64(const DGeom &g, const float *p, const float *q, const int *rowoff) {
+  long long acc[1], ms[1], vs[1];
+  const bool st = g.policy == 2;
+  switch (g.metric) {
+    case 1:
+      if (st) metric_block_fix<1, true, 1>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<1, false, 1>(g, p, q, rowoff, acc, ms, vs);
+      break;
+    case 2:
+      if (st) metric_block_fix<2, true, 1>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<2, false, 1>(g, p, q, rowoff, acc, ms, vs);
+      break;
+    default:
+      if (st) metric_block_fix<3, true, 1>(g, p, q, rowoff, acc, ms, vs);
+      else metric_block_fix<3, false, 1>(g, p, q, rowoff, acc, ms, vs);
+      break;
+  }
+  return pm_score64(g.policy, acc[0], ms[0], vs[0]);
+}
+
+// Reference finite-count threshold of Eq. (reference-threshold) in sum
+// units, P T_ref = sum mu(2 r_i) + t sqrt(sum v(2 r_i)) + beta_s P r-bar^kappa,
+// from exact sums over the reference patch; in float (t32) and double (t64).
+__device__ __noinline__ void pm_threshold(const DGeom &g, const float *p, const int *rowoff, float *t32,
+                                          double *t64) {
+  const float inv = g.inv_sp;
+  const long long *T = g.pfix;
+  long long ms = 0, vs = 0, rs = 0;
+  for (int r = 0; r < g.rows; ++r) {
+    const float *pr = p + rowoff[r];
+    for (int i = 0; i < g.jL; ++i) {
+      const int rv = count_of(pr[i], inv);
+      const int n = min(2 * rv, MOMENT_NMAX);
+      ms += __ldg(T + PFIX_MU + n);
+      vs += __ldg(T + PFIX_V + n);
+      rs += rv;
+    }
+  }
+  if (t32) {
+    const float rbar = (float)rs / (float)g.P;
+    *t32 = __ll2float_rn(ms) * 2.3283064365386963e-10f +
+           g.mt * sqrtf(__ll2float_rn(vs) * 2.3283064365386963e-10f) + g.beta_p * pow_kappa(rbar, g.kappa);
+  }
+  if (t64) {
+    const double rbar = (double)rs / (double)g.P;
+    *t64 = ldexp(__ll2double_rn(ms), -32) + (double)g.mt64 * sqrt(ldexp(__ll2double_rn(vs), -32)) +
+           g.beta_p64 * pow(rbar, g.kappa64);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // block matching of one reference (Sec. 4.2 / 4.4, App. A group rules)
 // ---------------------------------------------------------------------------
@@ -906,6 +1051,13 @@ __device__ __forceinline__ double score_decide(const DGeom &g, const float *__re
   return span <= 51 ? ssd_score_exact(g, S, rowoff, rb, cb, emin, span) : ssd_score64_call(g, S, rowoff, rb, cb);
 }
 
+// Double-precision score of a candidate for a decision: SSD (score_decide)
+// or, on count data, a Poisson distance (pm_exact64).
+__device__ __forceinline__ double cand_score64(const DGeom &g, const float *__restrict__ S, const int *rowoff, int rb,
+                                               int cb, int emin, int span, bool pm) {
+  return pm ? pm_exact64(g, S + rb, S + cb, rowoff) : score_decide(g, S, rowoff, rb, cb, emin, span);
+}
+
 // Every candidate of a window (window indices 0..ncand-1, region offsets
 // from the window origin lo and extents W) scored in double precision;
 // returns this lane's entry of the sorted list of the 32 best by (score,
@@ -913,7 +1065,7 @@ __device__ __forceinline__ double score_decide(const DGeom &g, const float *__re
 template <int D>
 __device__ __noinline__ void full_window(const DGeom &g, const float *__restrict__ S, const int *rowoff, int lane,
                                          int rbase, int ridx, int ncand, const int *lo, const int *W, int emin,
-                                         int span, double &fk, int &fi) {
+                                         int span, bool pm, double &fk, int &fi) {
   fk = DBL_MAX;
   fi = INT_MAX;
   for (int c0 = 0; c0 < ncand; c0 += 32) {
@@ -928,7 +1080,7 @@ __device__ __noinline__ void full_window(const DGeom &g, const float *__restrict
         rem /= W[d];
         off += (lo[d] + x) * g.rst[d];
       }
-      sc = score_decide(g, S, rowoff, rbase, off, emin, span);
+      sc = cand_score64(g, S, rowoff, rbase, off, emin, span, pm);
       wi = c;
     }
     warp_sort(sc, wi, lane);
@@ -963,7 +1115,7 @@ template <int D>
 __device__ __noinline__ int decide_refine(const DGeom &g, const float *__restrict__ S, const int *rr,
                                           const int *org, const int *rowoff, int lane, int rbase, int ridx,
                                           int ncand, int nl, int KK, bool resc, bool full, int emin, int span,
-                                          float lk, int &li) {
+                                          bool pm, float lk, int &li) {
   const unsigned FULL = 0xffffffffu;
   int lo[D], W[D];
 #pragma unroll
@@ -976,7 +1128,7 @@ __device__ __noinline__ int decide_refine(const DGeom &g, const float *__restric
   }
   double key = lane < nl ? (double)lk : DBL_MAX;
   if (full) {
-    full_window<D>(g, S, rowoff, lane, rbase, ridx, ncand, lo, W, emin, span, key, li);
+    full_window<D>(g, S, rowoff, lane, rbase, ridx, ncand, lo, W, emin, span, pm, key, li);
     if (g.diag && lane == 0) atomicAdd(g.diag + 1, 1ull);
   } else {
     int off = 0;
@@ -989,21 +1141,25 @@ __device__ __noinline__ int decide_refine(const DGeom &g, const float *__restric
         off += (lo[d] + c) * g.rst[d];
       }
     }
-    if (resc) key = score_decide(g, S, rowoff, rbase, off, emin, span);
+    if (resc) key = cand_score64(g, S, rowoff, rbase, off, emin, span, pm);
     if (g.diag) {
       const int nr = __popc(__ballot_sync(FULL, resc));
       if (lane == 0) atomicAdd(g.diag, (unsigned long long)nr);
     }
     warp_sort(key, li, lane);
   }
-  // acceptance: score < tau (App. A), in double precision
-  return __popc(__ballot_sync(FULL, lane < KK && key < g.tau64));
+  // acceptance: score < tau (App. A; Sec. 4.3 for the Poisson distances),
+  // in double precision
+  double t64 = g.tau64;
+  if (pm && g.policy == 1) pm_threshold(g, S + rbase, rowoff, nullptr, &t64);
+  return __popc(__ballot_sync(FULL, lane < KK && key < t64));
 }
 
 template <int D>
 __device__ __forceinline__ int decide_group(const DGeom &g, const float *__restrict__ S, const int *rr, const int *org,
                                             const int *rowoff, int lane, int rbase, int ridx, int ncand, float Bm,
-                                            float thr, bool exact, int emin, int span, float lk, int &li) {
+                                            float thr, bool exact, int emin, int span, bool pm, float tau32,
+                                            float tbr, float lk, int &li) {
   const unsigned FULL = 0xffffffffu;
   const int K = g.M - 1;
   const int navail = ncand - 1;
@@ -1011,7 +1167,7 @@ __device__ __forceinline__ int decide_group(const DGeom &g, const float *__restr
   const int KK = min(K, nl);
   // tau bracketed in float: below tlo certainly accepted, at or above thi
   // certainly not
-  const float tlo = g.tau - fabsf(g.tau) * 2.4e-7f, thi = g.tau + fabsf(g.tau) * 2.4e-7f;
+  const float tlo = tau32 - fabsf(tau32) * tbr, thi = tau32 + fabsf(tau32) * tbr;
   if (exact || KK <= 0) {
     // exact FP32 scores: only a score within a float step of tau needs the
     // double-precision comparison
@@ -1052,7 +1208,8 @@ __device__ __forceinline__ int decide_group(const DGeom &g, const float *__restr
   const float hull = __shfl_sync(FULL, pmax, KK - 1);
   const bool full = outlb <= hull;
   if (full || __any_sync(FULL, resc))
-    return decide_refine<D>(g, S, rr, org, rowoff, lane, rbase, ridx, ncand, nl, KK, resc, full, emin, span, lk, li);
+    return decide_refine<D>(g, S, rr, org, rowoff, lane, rbase, ridx, ncand, nl, KK, resc, full, emin, span, pm, lk,
+                            li);
   return __popc(__ballot_sync(FULL, lane < KK && lk < tlo));
 }
 
@@ -1063,7 +1220,7 @@ template <int D, int JL, int KB, int ST>
 // the FP32 scores are exact (decide_group).
 __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
                           const int *org, const int *rowoff, int lane, int *mem, bool nonneg, bool exact,
-                          int emin, int span, float vmaxf, unsigned long long *diag) {
+                          int emin, int span, float vmaxf, bool counts, unsigned long long *diag) {
   int lo[D], W[D];
   int64_t ncand = 1;
 #pragma unroll
@@ -1093,8 +1250,14 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
   // Poisson matching distances in stage 1 (Secs. 4.2-4.3): the generic
   // kernels, or the cubic-patch kernels instantiated with ST = 3
   const bool pmetric = (JL == 0 || ST == 3) && ST != 2 && g.metric != 0;
+  // count data: exact integer sums (metric_keys_fix) and double-precision
+  // decisions; otherwise the FP32 scores decide
+  const bool pfix = pmetric && counts && g.pfix != nullptr;
   float tau = g.tau;
-  if (pmetric && g.policy == 1) tau = metric_threshold(g, S + rbase, rowoff);
+  if (pmetric && g.policy == 1) {
+    if (pfix) pm_threshold(g, S + rbase, rowoff, &tau, nullptr);
+    else tau = metric_threshold(g, S + rbase, rowoff);
+  }
   const float gbias = g.poisson ? 0.f : __fmul_rn(__fmul_rn(2.f, (float)g.P), g.var_g);
   float lk = FLT_MAX;
   int li = INT_MAX;
@@ -1120,7 +1283,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
       Bm = 2.f * (float)g.P * g.var_g;
     }
   }
-  const float kmar = (exact || pmetric) ? 0.f : 3.f * g.ku;
+  const float kmar = (exact || (pmetric && !pfix)) ? 0.f : 3.f * g.ku;
   int iters = (total + 31) / 32;
   for (int it = 0; it < iters; ++it) {
     int c = it * 32 + lane;
@@ -1148,7 +1311,8 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
 #pragma unroll
       for (int b = 0; b < KB; ++b) { acc[b] = 0.f; bs[b] = 0.f; }
       const int jl = JL > 0 ? JL : g.jL;
-      if (pmetric) metric_scores<KB>(g, S + rbase, S + cbase, rowoff, acc);
+      if (pfix) metric_keys_fix<KB>(g, S + rbase, S + cbase, rowoff, acc);
+      else if (pmetric) metric_scores<KB>(g, S + rbase, S + cbase, rowoff, acc);
       for (int r = 0; r < (pmetric ? 0 : g.rows); ++r) {
         const float *prow = S + rbase + rowoff[r];
         const float *qrow = S + cbase + rowoff[r];
@@ -1306,10 +1470,14 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
   int K = g.M - 1;
   int navail = (int)ncand - 1;
   int take;
-  if (pmetric) {
+  if (pmetric && !pfix) {
     take = min(warp_sum_i(nacc), K);
   } else {
-    take = decide_group<D>(g, S, rr, org, rowoff, lane, rbase, ridx, (int)ncand, Bm, thr, exact, emin, span, lk, li);
+    // tau bracket: the float tau of the host (relative 2^-22), or the FP32
+    // reference threshold of pm_threshold (relative 2^-18)
+    const float tbr = pfix && g.policy == 1 ? 3.8147e-6f : 2.4e-7f;
+    take = decide_group<D>(g, S, rr, org, rowoff, lane, rbase, ridx, (int)ncand, Bm, thr, exact, emin, span, pfix,
+                           tau, tbr, lk, li);
   }
   if (1 + take < g.min_group) take = min(min(g.min_group - 1, K), navail);
   int count = 1 + take;
@@ -2457,6 +2625,11 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     bool nonneg_t = true;
     int emin_t = INT_MAX;
     unsigned vmax_t = 0u;
+    // stage-1 Poisson distance: is every staged value s_P times a count
+    // K <= PFIX_K / 2 (to a relative 2^-21: float storage and the product
+    // with float(1 / s_P) stay below 2^-22)?
+    const bool want_counts = !mc2 && !stage2 && g.metric != 0 && g.pfix != nullptr;
+    bool counts_t = true;
     for (int e = threadIdx.x; e < RS; e += blockDim.x) {
       float vg = 0.f, vy = 0.f, ve = 0.f;
       if (e < g.region) {
@@ -2491,6 +2664,10 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         if (mc2 && !g.lean) Se[e] = ve;
       }
       nonneg_t = nonneg_t && vg >= 0.f;
+      if (want_counts && vg > 0.f) {
+        const float rc = vg * g.inv_sp, kc = rintf(rc);
+        counts_t = counts_t && kc <= (float)(PFIX_K / 2) && fabsf(rc - kc) <= 4.76837158e-7f * fmaxf(kc, 1.f);
+      }
       if (vg != 0.f) {
         // vg = mant 2^(ex - 150) with a 24-bit mantissa: the exponent of its
         // lowest set bit
@@ -2506,6 +2683,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
       if (vmax_t) atomicMax(&s_vmax, vmax_t);
     }
     const bool tile_nonneg = __syncthreads_and(nonneg_t) != 0;
+    const bool tile_counts = __syncthreads_and(want_counts && counts_t) != 0;
     // Exact tile (stage-1 SSD, s_P = 2^k, integral gamma): the staged values
     // are multiples of q0 = 2^emin of magnitude at most V q0.  Differences,
     // squares, the SSD, the bias sum, s_P times it and the score are then
@@ -2550,7 +2728,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
         if (!mc2) {
           n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg, tile_exact, tile_emin,
-                                        tile_span, tile_vmax, g.diag);
+                                        tile_span, tile_vmax, tile_counts, g.diag);
           if (sj->groups) {
             for (int m = lane; m < g.M; m += 32)
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;

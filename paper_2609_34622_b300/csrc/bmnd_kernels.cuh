@@ -120,6 +120,12 @@ struct DGeom {
   float ku, ht_t2;
   int exact_ok;
   int pad_dd;
+  // Poisson distances on count data in exact integer arithmetic: pfix
+  // holds fixed-point tables (units 2^-32) of the per-entry contributions
+  // and the finite-count moments (layout at PFIX_*), and count_tol the
+  // relative distance from an integer within which y / s_P is a count.
+  const long long *pfix;
+  double mt64, beta_p64, kappa64;  // t, beta_s P, kappa_s in double
   // counters of the double-precision decisions (or null): [0] candidates
   // rescored, [1] full double-precision searches, [2] coefficients decided
   // in double precision at the hard threshold
@@ -133,6 +139,19 @@ constexpr int TAB64_OFFSET = ((2 * GEN_TOTAL * 4) + 255) & ~255;
 constexpr int TAB_BYTES = TAB64_OFFSET + GEN_TOTAL * 8;
 
 constexpr int MOMENT_NMAX = 4096;
+
+// Fixed-point tables of a Poisson distance for count data (int64, units
+// 2^-32 unless stated): at PFIX_A, indexed by a count K <= PFIX_K:
+// deviance K ln(2K), Pearson floor(2^64 / K) (K >= 1), Anscombe
+// 2 sqrt(K + 3/8) in units 2^-44; at PFIX_B the deviance's K ln K; at PFIX_MU
+// and PFIX_V the moments mu(n), v(n), n <= MOMENT_NMAX.  Counts up to
+// PFIX_K / 2 per entry, so pooled counts stay within the tables.
+constexpr int PFIX_K = 16384;
+constexpr int PFIX_A = 0;
+constexpr int PFIX_B = PFIX_K + 1;
+constexpr int PFIX_MU = 2 * (PFIX_K + 1);
+constexpr int PFIX_V = PFIX_MU + MOMENT_NMAX + 1;
+constexpr int PFIX_TOTAL = PFIX_V + MOMENT_NMAX + 1;
 
 struct DJob {
   DGeom g;

@@ -9,6 +9,11 @@ import numpy as np
 # near-ties (scores closer than 1e-5 relative to their magnitude), >= 99.9%
 # of output voxels within 1e-4 of the peak intensity, PSNR within 0.01 dB.
 NEAR_TIE_REL = 1e-5
+# Poisson distances on count data: the kernels' integer sums of fixed-point
+# table values are within P 2^-33 of the exact sums, so a near-tie there is
+# a difference below 1e-8 (|score| + 1): in practice a tie in real
+# arithmetic between different multisets of contributions
+POISSON_TIE_REL = 1e-8
 VOXEL_ABS = 1e-4
 VOXEL_FRAC = 0.999
 PSNR_DB = 0.01
@@ -55,9 +60,72 @@ def candidate_scores(guide, ref_lin, patch, search, noise, gamma):
     return out
 
 
-def group_agreement(gpu, orc, guide, patch, search, noise, gamma, tau, max_explain=200):
+def raw_counts(guide, s_p):
+    """Eq. (raw-counts) with the integer reading of the oracle: y / s_P, the
+    nearest integer when within a relative 2^-20 of it."""
+    r = np.maximum(np.asarray(guide, np.float64) / s_p, 0.0)
+    k = np.rint(r)
+    return np.where(np.abs(r - k) <= np.ldexp(np.maximum(k, 1.0), -20), k, r)
+
+
+def poisson_phi(metric, r, c):
+    """phi_m(r, c) of Eq. (varphi) in FP64 (numpy, elementwise)."""
+    r = np.asarray(r, np.float64)
+    c = np.asarray(c, np.float64)
+    n = r + c
+    if metric == "poisson_deviance":
+        with np.errstate(divide="ignore", invalid="ignore"):
+            a = np.where(r > 0, r * np.log(np.where(r > 0, 2 * r, 1) / np.where(n > 0, n, 1)), 0.0)
+            b = np.where(c > 0, c * np.log(np.where(c > 0, 2 * c, 1) / np.where(n > 0, n, 1)), 0.0)
+        return np.where(n > 0, 2 * (a + b), 0.0)
+    if metric == "pearson":
+        return np.where(n > 0, (r - c) ** 2 / np.where(n > 0, n, 1), 0.0)
+    d = 2 * np.sqrt(c + 0.375) - 2 * np.sqrt(r + 0.375)
+    return 0.5 * d * d
+
+
+def poisson_candidate_scores(guide, ref_lin, patch, search, s_p, metric, policy, moments, t=1.0, beta=0.1,
+                             kappa=1.0, tau_fixed=None):
+    """FP64 scores and magnitudes of every candidate of one reference under a
+    Poisson distance (Sec. 4.2-4.3), and the acceptance threshold; moments(n)
+    gives (mu, v) at a pooled count (capped at 4096)."""
+    k = raw_counts(guide, s_p)
+    shape = k.shape
+    ref = np.unravel_index(int(ref_lin), shape)
+    ell = [L - j for L, j in zip(shape, patch)]
+    rad = [(w - 1) // 2 for w in search]
+    pr = k[tuple(slice(a, a + j) for a, j in zip(ref, patch))].ravel()
+    P = pr.size
+    if policy == "fixed":
+        thr = P * (tau_fixed if tau_fixed else 1 + t * np.sqrt(2.0 / P))
+    elif policy == "candidate_standardized":
+        thr = t
+    else:
+        mv = [moments(int(min(round(2 * x), 4096))) for x in pr]
+        thr = sum(m for m, _ in mv) + t * np.sqrt(sum(v for _, v in mv)) + beta * P * np.mean(pr) ** kappa
+    out = {}
+    ranges = [range(max(r - a, 0), min(r + a, e) + 1) for r, a, e in zip(ref, rad, ell)]
+    for cpos in itertools.product(*ranges):
+        q = k[tuple(slice(a, a + j) for a, j in zip(cpos, patch))].ravel()
+        phi = poisson_phi(metric, pr, q)
+        acc = float(np.sum(phi))
+        if policy == "candidate_standardized":
+            mv = [moments(int(min(round(a + b), 4096))) for a, b in zip(pr, q)]
+            vs = sum(v for _, v in mv)
+            sc = (acc - sum(m for m, _ in mv)) / np.sqrt(vs) if vs > 0 else 0.0
+            mag = abs(sc) + 1e-30
+        else:
+            sc, mag = acc, acc + 1e-30
+        out[int(np.ravel_multi_index(cpos, shape))] = (sc, mag)
+    return out, thr
+
+
+def group_agreement(gpu, orc, guide, patch, search, noise, gamma, tau, max_explain=200, scorer=None,
+                    rel=NEAR_TIE_REL, tol=0.0):
     """Compare per-reference groups.  gpu/orc: (origins[R], groups[R, M], counts[R])
-    sorted by origin.  Returns (n_exact, n_near_tie, n_bad, bad_examples)."""
+    sorted by origin.  scorer(ref) -> ({origin: (score, magnitude)}, tau)
+    replaces the SSD scores (candidate_scores) for other distances.  Returns
+    (n_exact, n_near_tie, n_bad, bad_examples)."""
     go, gg, gc = gpu
     oo, og, oc = orc
     assert np.array_equal(go, oo), "reference origins differ"
@@ -72,18 +140,21 @@ def group_agreement(gpu, orc, guide, patch, search, noise, gamma, tau, max_expla
         if n_tie + n_bad >= max_explain:
             n_bad += 1
             continue
-        sc = candidate_scores(guide, oo[r], patch, search, noise, gamma)
+        if scorer is None:
+            sc = candidate_scores(guide, oo[r], patch, search, noise, gamma)
+        else:
+            sc, tau = scorer(oo[r])
         ok = True
         for k in range(1, min(len(a), len(b))):
             if a[k] != b[k]:
                 sa, ma = sc[a[k]]
                 sb, mb = sc[b[k]]
-                if abs(sa - sb) > NEAR_TIE_REL * max(ma, mb):
+                if abs(sa - sb) > rel * max(ma, mb) + tol:
                     ok = False
         if len(a) != len(b):
             # a different count is only legitimate if some candidate sits at
             # the acceptance threshold
-            near_tau = any(abs(s - tau) <= NEAR_TIE_REL * m for k2, (s, m) in sc.items() if k2 != oo[r])
+            near_tau = any(abs(s - tau) <= rel * m + tol for k2, (s, m) in sc.items() if k2 != oo[r])
             ok = ok and near_tau
         if ok:
             n_tie += 1
@@ -155,3 +226,103 @@ def end_to_end_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm=None, what="")
     assert within >= VOXEL_FRAC, "%s: only %.5f of the compared voxels within %g" % (what, within, VOXEL_ABS)
     assert abs(psnr(got, x) - psnr(ref64, x)) <= PSNR_DB
     return frac_cmp, within
+
+
+def groups_of(ctx, guide_cuda, cfg, stage, prm=None):
+    """The library's groups (origins, groups, counts) sorted by origin."""
+    M = cfg["group_size"][stage - 1]
+    o, g, c = ctx.bmnd_match(guide_cuda, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], M, stage, prm)
+    o, g, c = o.cpu().numpy(), g.cpu().numpy(), c.cpu().numpy()
+    order = np.argsort(o)
+    return o[order], g[order], c[order]
+
+
+def differing_members(gpu, og, oc):
+    """Member origins (both sides) of the references whose groups differ."""
+    _, gg, gc = gpu
+    out = []
+    for r in range(len(gc)):
+        a = list(gg[r, :gc[r]])
+        b = list(og[r, :oc[r]])
+        if a != b:
+            out += a + b
+    return out
+
+
+def dilate(mask, widths):
+    """Boolean dilation of mask by +-widths[d] along every axis d."""
+    out = mask.copy()
+    for d, w in enumerate(widths):
+        acc = out.copy()
+        for s in range(1, w + 1):
+            acc[tuple(slice(s, None) if a == d else slice(None) for a in range(out.ndim))] |= \
+                out[tuple(slice(None, -s) if a == d else slice(None) for a in range(out.ndim))]
+            acc[tuple(slice(None, -s) if a == d else slice(None) for a in range(out.ndim))] |= \
+                out[tuple(slice(s, None) if a == d else slice(None) for a in range(out.ndim))]
+        out = acc
+    return out
+
+
+def assert_voxels_on(got, ref, mask, what=""):
+    """The voxel contract on the voxels of mask."""
+    if not mask.any():
+        return 1.0
+    frac = voxel_report(np.asarray(got)[mask], np.asarray(ref)[mask])[0]
+    assert frac >= VOXEL_FRAC, "%s: only %.5f of the compared voxels within %g" % (what, frac, VOXEL_ABS)
+    return frac
+
+
+def stage1_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, what=""):
+    """Stage 1 under a Poisson distance: groups identical except at near-ties
+    of the oracle's FP64 scores (scorer), the voxel contract outside the
+    patches of the groups that differ (either choice at a near-tie is
+    correct, and they synthesize different patches), PSNR within 0.01 dB.
+    Returns (fraction of voxels compared, number of differing groups)."""
+    ref, _, og, oc = oracle.stage(p, y, None, 1, want_den=True, want_groups=True)
+    M = cfg["group_size"][0]
+    gpu = groups_of(ctx, cuda(y), cfg, 1, prm)
+    oo = oracle.schedule(p)
+    ne, nt, nb, bad = group_agreement(gpu, (oo, og[:, :M], oc), y, cfg["patch"], cfg["search"], cfg["noise"],
+                                      0.0, 0.0, max_explain=len(oo), scorer=scorer, rel=POISSON_TIE_REL,
+                                      tol=POISSON_TIE_REL)
+    assert nb == 0, bad
+    mask = ~footprint_mask(y.shape, cfg["patch"], differing_members(gpu, og[:, :M], oc))
+    assert_voxels_on(got, ref, mask, what)
+    assert abs(psnr(got, x) - psnr(ref, x)) <= PSNR_DB
+    return float(mask.mean()), nt
+
+
+def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, what=""):
+    """Both stages under a Poisson distance (stage 1) and SSD on the pilot
+    (stage 2): stage-1 groups as in stage1_poisson_contract; the voxel
+    contract against the oracle's stages (float32 pilot) outside the patches
+    of the stage-1 groups that differ, dilated by the stage-2 search radius
+    and patch (where the two pilots differ and stage-2 matching reads them),
+    and outside the patches of the stage-2 groups that differ; PSNR within
+    0.01 dB of the oracle's double-precision run."""
+    import torch
+    opilot = oracle.stage(p, y, None, 1).astype(np.float32)
+    ref = oracle.stage(p, y, opilot.astype(np.float64), 2)
+    ref64, _ = oracle.denoise(p, y)
+    _, _, og1, oc1 = oracle.stage(p, y, None, 1, want_den=True, want_groups=True)
+    M1, M2 = cfg["group_size"]
+    gpu1 = groups_of(ctx, cuda(y), cfg, 1, prm)
+    oo = oracle.schedule(p)
+    _, _, nb, bad = group_agreement(gpu1, (oo, og1[:, :M1], oc1), y, cfg["patch"], cfg["search"], cfg["noise"],
+                                    0.0, 0.0, max_explain=len(oo), scorer=scorer, rel=POISSON_TIE_REL,
+                                    tol=POISSON_TIE_REL)
+    assert nb == 0, bad
+    gpilot = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
+    ctx.bmnd_stage(cuda(y), None, gpilot, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], M1, 1,
+                   p.mass_conserve & 1, prm)
+    gpu2 = groups_of(ctx, gpilot, cfg, 2, prm)
+    _, _, og2, oc2 = oracle.stage(p, y, opilot.astype(np.float64), 2, want_den=True, want_groups=True)
+    a1 = footprint_mask(y.shape, cfg["patch"], differing_members(gpu1, og1[:, :M1], oc1))
+    reach = [(w - 1) // 2 + j for w, j in zip(cfg["search"], cfg["patch"])]
+    bad_area = dilate(a1, reach) | footprint_mask(y.shape, cfg["patch"], differing_members(gpu2, og2[:, :M2], oc2))
+    if p.mass_conserve:
+        bad_area = dilate(bad_area, list(cfg["patch"]))
+    mask = ~bad_area
+    assert_voxels_on(got, ref, mask, what)
+    assert abs(psnr(got, x) - psnr(ref64, x)) <= PSNR_DB
+    return float(mask.mean())

