@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the B300 BMND denoiser: denoised voxels/s, both stages.
 
-One step = one pass of both stages over one synthetic batch resident in HBM.
-Default workload: the 1-D ECG-like signal of 262144 samples (Poisson, peak 50,
-patch 32, step 4, search 129, groups 16/32).  Other workloads: --workload c1
-(2-D 64x64), c3 (32 images of 512x512 in one batched call), c4 (3-D 128^3
-with mass conservation).
+Default workload: the 2-D batch (16 images of 512x512 with Poisson counts at
+peaks 1, 2, 5, 10, 30 and the same 16 with Gaussian noise sigma 25/255;
+patch 8x8, step 3, search 39x39, groups 16/32), all 32 images denoised in one
+batched call.  One step = one such call with the inputs resident in HBM.
+The line carries the plain path (one call per image) beside it, and the
+serving mix (512 requests, Poisson arrivals at 200/s) served by the request
+server and by the plain path, with p50/p99 latency.  Other workloads:
+--workload c1 (2-D 64x64), c2 (1-D 262144 samples), c4 (3-D 128^3 with mass
+conservation), c5 (the serving mix alone), schedules (Sec. 9.3 analysis).
 
 Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on
 the launching stream; L2 is flushed (256 MiB write) before every timed step,
@@ -314,7 +318,7 @@ def run_schedules(args, local: int, impl: str):
     ctx.close()
 
 
-def run_c5(args, local: int):
+def serving_mix(args, local: int) -> dict:
     """Serving mix: 512 requests with Poisson-process arrivals at 200/s, served
     by the library's request server (memory-budgeted admission, continuous
     batching) and, for comparison, by the plain path (one array per call, in
@@ -384,30 +388,37 @@ def run_c5(args, local: int):
     def q(v, f):
         v = sorted(v)
         return v[min(len(v) - 1, int(round(f * (len(v) - 1))))]
-    value = total_vox / served_span
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * served_span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving mix: %d requests, Poisson arrivals at 200/s, 40%% 1-D (8k-262k), "
-                                   "45%% 2-D (64^2-1024^2), 15%% 3-D (32^3-128^3), Poisson peaks 1-50"
-                                   % len(reqs), "voxels": total_vox, "budget_gb": args.budget_gb},
-            "served": {"voxels_per_s": value, "p50_ms": q(lat, 0.5), "p99_ms": q(lat, 0.99),
+    return {"workload": "serving mix: %d requests, Poisson arrivals at 200/s, 40%% 1-D (8k-262k), "
+                        "45%% 2-D (64^2-1024^2), 15%% 3-D (32^3-128^3), Poisson peaks 1-50" % len(reqs),
+            "voxels": total_vox, "budget_gb": args.budget_gb,
+            "served": {"voxels_per_s": total_vox / served_span, "p50_ms": q(lat, 0.5), "p99_ms": q(lat, 0.99),
                        "span_s": served_span, "steps": st["steps"], "mean_jobs_per_step": st["mean_jobs_per_step"]},
             "plain": {"voxels_per_s": total_vox / plain_span, "p50_ms": q(plat, 0.5), "p99_ms": q(plat, 0.99),
                       "span_s": plain_span},
             "saturated": {"note": "all requests submitted at once, host arrays in and out",
                           "served_voxels_per_s": total_vox / served_burst,
                           "plain_voxels_per_s": total_vox / plain_burst}}
+
+
+def run_c5(args, local: int):
+    """The serving mix alone as the line's workload (value: served voxels/s)."""
+    sv = serving_mix(args, local)
+    line = {"metric": METRIC, "value": sv["served"]["voxels_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * sv["served"]["span_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": sv["workload"], "voxels": sv["voxels"], "budget_gb": sv["budget_gb"]},
+            "served": sv["served"], "plain": sv["plain"], "saturated": sv["saturated"]}
     print(json.dumps(line))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: 20 for the batch, 300 else)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "schedules"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "schedules"])
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-mix run of the default line")
     ap.add_argument("--requests", type=int, default=512, help="serving mix size (c5)")
     ap.add_argument("--budget-gb", type=int, default=40, help="server memory budget (c5)")
     ap.add_argument("--edge", type=int, default=128, help="volume edge of the 3-D workload (c4)")
@@ -427,6 +438,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = 20 if args.workload == "c3" else 300
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -543,6 +556,13 @@ def main():
     for _ in range(args.warmup):
         step(ys, outs)
     torch.cuda.synchronize()
+    fp32_peak = bm.bmnd_fp32_fma_peak(local)
+    hbm_peak, hbm_peak_measured = 6400.0, False
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        hbm_peak_measured = True
+    except (OSError, KeyError, ValueError):
+        pass
 
     # ---- matching alone: the match-only stage launches of bmnd_match ----
     match_frac = {}
@@ -597,22 +617,22 @@ def main():
         torch.cuda.synchronize()
         plain_ms = sum(a.elapsed_time(b) for a, b in evp)
 
-    # ---- end to end: pinned host input -> device -> both stages -> host ----
+    # ---- end to end through the C ABI with host buffers: the host-array
+    # batch call copies pinned host inputs in, runs both stages, copies the
+    # results back and returns when they are in host memory ----
     hy = [torch.from_numpy(j.y).pin_memory() for j in jobs]
     ho = [torch.empty(j.y.shape, dtype=torch.float32).pin_memory() for j in jobs]
-    dy = [torch.empty_like(y) for y in ys]
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    hyn = [h.numpy() for h in hy]
+    hon = [h.numpy() for h in ho]
+    ctx.bmnd_denoise_batch_host(hyn, hon, cfgs, prm, stream=stream)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
     for k in range(args.steps):
         flush.fill_(float(k))
-        ev2[k][0].record(stream)
-        for h, d in zip(hy, dy):
-            d.copy_(h, non_blocking=True)
-        step(dy, outs)
-        for h, o in zip(ho, outs):
-            h.copy_(o, non_blocking=True)
-        ev2[k][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.bmnd_denoise_batch_host(hyn, hon, cfgs, prm, stream=stream)
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
 
     dev_ms, e2e_ms, value, e2e_val = replica_totals(dev_ms, e2e_ms, vox_step, args.steps, world,
                                                     dist if dist else None, dev)
@@ -624,7 +644,19 @@ def main():
     stage_flop = flops[1] * n1 + flops[2] * n2
     achieved = stage_flop / (stage_ms / 1e3) / 1e12 if stage_ms > 0 else None
     mhz = clk["sm_mhz"] or 2032.0
-    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    peak_nominal = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    peak = fp32_peak if fp32_peak else peak_nominal
+    # reduce kernel: reads every tile's partial (float2 per region cell) and
+    # writes the estimate (and eta when mass conservation runs a second sweep)
+    red_bytes = 0.0
+    for j, c in zip(jobs, cfgs):
+        for s_ in range(1, c["stages"] + 1):
+            gm = c["group_size"][s_ - 1]
+            inf = ctx.bmnd_plan_info(j.y.shape, c["patch"], c["step"], c["search"], (gm, gm), 1, 0, prm)
+            mc = (c["mass_conserve"] >> (s_ - 1)) & 1
+            red_bytes += (1 + mc) * (8.0 * inf["tiles"] * inf["region"] + 4.0 * j.y.size) + mc * 4.0 * j.y.size
+    nred, ms_red = kstats["reduce"]
+    red_gbs = red_bytes * args.steps / (ms_red / 1e3) / 1e9 if ms_red > 0 else None
     launches = sum(v[0] for v in kstats.values()) + kstats["schedule"][0]  # schedule = mark + compact
     step_ms_total = sum(v[1] for v in kstats.values())
 
@@ -638,12 +670,15 @@ def main():
                              if tuned else "planner")},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * vox_step, "d2h_bytes_per_step": 4 * vox_step},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * vox_step, "d2h_bytes_per_step": 4 * vox_step,
+                "path": "bmnd_denoise_batch_host: pinned host arrays in and out, copies inside the call, "
+                        "host wall clock per call"},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": captured_traffic(args.workload),
-                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median sampled SM clock)" % mhz,
+                     "peak_basis": ("measured FP32 FMA throughput (bmnd_fp32_fma_peak, this run); nominal "
+                                    "148 SMs x 128 lanes x 2 flop x %.0f MHz = %.1f TFLOP/s" % (mhz, peak_nominal)),
                      "stage_kernel_ms_per_step": stage_ms / args.steps,
                      "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
                      "share_of_step": stage_ms / step_ms_total if step_ms_total else None,
@@ -652,7 +687,12 @@ def main():
                                  "selection; algorithmic FLOPs of the scores only",
                          "stage1_tflops": match_frac[1], "stage2_tflops": match_frac[2],
                          "stage1_frac": match_frac[1] / peak if match_frac[1] else None,
-                         "stage2_frac": match_frac[2] / peak if match_frac[2] else None}},
+                         "stage2_frac": match_frac[2] / peak if match_frac[2] else None},
+                     "reduce": {"kernel": "k_reduce", "bound": "hbm", "bytes_per_step": red_bytes,
+                                "achieved_gbs": red_gbs, "peak_gbs": hbm_peak,
+                                "frac": red_gbs / hbm_peak if red_gbs and hbm_peak else None,
+                                "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)" if hbm_peak_measured
+                                else "fallback 6400 GB/s"}},
     }
     if args.ht_rule != "hard":
         line["config"]["ht_rule"] = args.ht_rule
@@ -670,10 +710,12 @@ def main():
                             "stage_kernel_ms_per_step": stage_ms / args.steps,
                             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
                             "share_of_step": stage_ms / step_ms_total if step_ms_total else None}
+    line["roofline"]["fp32_peak_measured_tflops"] = fp32_peak
     if plain_ms is not None:
         line["plain"] = {"value": vox_step * args.steps / (plain_ms / 1e3), "unit": UNIT,
                          "ms_per_step": plain_ms / args.steps,
                          "path": "one bmnd_denoise call per array, same stream, same timing"}
+        line["config"]["batched"] = "one bmnd_denoise_batch call over all %d arrays per step" % len(jobs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, sdesc = oracle_sample(args.workload, jobs)
         v, el, reps, cores = time_oracle(sample, 10.0, matching=(args.match_metric, args.match_policy),
@@ -681,9 +723,11 @@ def main():
                                          cov_planes=args.cov_planes)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%s, both stages, %d repetition(s), %.1f s" % (sdesc, reps, el)}
+    ctx.close()
+    if rank == 0 and world == 1 and args.workload == "c3" and not args.no_serving:
+        line["serving"] = serving_mix(args, local)
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 

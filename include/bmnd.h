@@ -281,6 +281,36 @@ typedef struct {
 bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
                                const bmnd_params *params, void *stream);
 
+/* bmnd_denoise_batch with host arrays (the paper has no counterpart: a
+ * convenience for callers whose data live in host memory).  jobs[i].y and
+ * jobs[i].out are HOST pointers (float32, C-order; pinned memory makes the
+ * copies asynchronous DMA, pageable memory is staged by the driver).  The
+ * call copies every y to context-owned device buffers (grown on use, held
+ * until bmnd_destroy), runs bmnd_denoise_batch on them on `stream`, copies
+ * every result back and waits for the stream: on return the outputs are
+ * in host memory.  Errors: as bmnd_denoise_batch; BMND_ENOMEM when the
+ * device buffers cannot be allocated; BMND_ECUDA on a failed copy. */
+bmnd_status bmnd_denoise_batch_host(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
+                                    const bmnd_params *params, void *stream);
+
+/* Plan of one array (diagnostics; no counterpart in the paper): info[0] the
+ * number of tiles, info[1] the cells of a tile's region (the partial each
+ * tile writes and the reduce kernel reads, float2 each), info[2] the
+ * reference capacity of a tile, info[3] the number of non-singleton axes,
+ * info[4..7] the tile core along those axes (0 past them).  Arguments as
+ * bmnd_denoise_ex; nothing is launched.  Errors: those of bmnd_denoise_ex's
+ * argument checks. */
+bmnd_status bmnd_plan_info(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
+                           const int *search, const int *group_size, int stages, int mass_conserve,
+                           const bmnd_params *params, int64_t info[8]);
+
+/* FP32 FMA throughput of a device in TFLOP/s (measurement only; no
+ * counterpart in the paper): a kernel of independent fused multiply-add
+ * chains on every SM, timed with CUDA events (best of three after a
+ * warm-up), 2 flops per FMA.  It allocates and frees a small output array.
+ * Errors: BMND_EINVAL (bad device or null tflops), BMND_ENOMEM, BMND_ECUDA. */
+bmnd_status bmnd_fp32_fma_peak(int device, double *tflops);
+
 /* Per-kernel timing, for measurement only (the paper has no counterpart).
  * With profiling enabled, every kernel launched by the context is bracketed by
  * CUDA events recorded on the launch stream.  bmnd_kernel_stats() synchronizes

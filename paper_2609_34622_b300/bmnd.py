@@ -78,7 +78,8 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
            "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune",
-           "bmnd_match_moments", "bmnd_coverage", "bmnd_decision_stats"]
+           "bmnd_match_moments", "bmnd_coverage", "bmnd_decision_stats", "bmnd_denoise_batch_host",
+           "bmnd_plan_info", "bmnd_fp32_fma_peak"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
 
 _lib = None
@@ -124,6 +125,10 @@ def load(path: str = LIB_PATH):
     lib.bmnd_autotune.argtypes = common + [ip, ctypes.c_int, ctypes.c_int, P(bmnd_params), vp, vp, ip]
     lib.bmnd_graph_destroy.argtypes = [vp]
     lib.bmnd_decision_stats.argtypes = [vp, ctypes.c_int, P(ctypes.c_uint64)]
+    lib.bmnd_denoise_batch_host.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
+    lib.bmnd_plan_info.argtypes = [vp, ctypes.c_int, i64p, ip, ip, ip, ip, ctypes.c_int, ctypes.c_int,
+                                   P(bmnd_params), i64p]
+    lib.bmnd_fp32_fma_peak.argtypes = [ctypes.c_int, P(ctypes.c_double)]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.bmnd_match_moments.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp]
     lib.bmnd_coverage.argtypes = [vp, ctypes.c_int, i64p, ip, ip, P(bmnd_params), vp, i64p,
@@ -370,6 +375,45 @@ class Context:
         return outs
 
 
+    def bmnd_denoise_batch_host(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
+        """ys/outs: lists of C-contiguous float32 numpy arrays (host memory;
+        pinned tensors' numpy views work too); returns when outs hold the
+        results."""
+        n = len(ys)
+        arr = (bmnd_job * n)()
+        for i, (y, o, c) in enumerate(zip(ys, outs, cfgs)):
+            if not (y.dtype == np.float32 and o.dtype == np.float32 and y.flags.c_contiguous
+                    and o.flags.c_contiguous and y.shape == o.shape):
+                raise ValueError("y[%d] / out[%d] must be C-contiguous float32 arrays of one shape" % (i, i))
+            j = arr[i]
+            j.y, j.out = y.ctypes.data, o.ctypes.data
+            j.ndim = y.ndim
+            for a, sz in enumerate(y.shape):
+                j.shape[a] = int(sz)
+                j.patch[a] = int(c["patch"][a])
+                j.step[a] = int(c["step"][a])
+                j.search[a] = int(c["search"][a])
+            j.noise = noise(c["noise"])
+            gs = c.get("group_size", (16, 32))
+            j.group_size[0], j.group_size[1] = int(gs[0]), int(gs[1])
+            j.stages = int(c.get("stages", 2))
+            j.mass_conserve = int(c.get("mass_conserve", 0))
+        st = self._lib.bmnd_denoise_batch_host(self.handle, n, arr, ctypes.byref(prm) if prm is not None else None,
+                                               _stream(stream))
+        self._check(st)
+        return outs
+
+    def bmnd_plan_info(self, shape, patch, step, search, group_size=(16, 32), stages=2, mass_conserve=0,
+                       prm: bmnd_params | None = None) -> dict:
+        info = (ctypes.c_int64 * 8)()
+        st = self._lib.bmnd_plan_info(self.handle, len(shape), _ints(shape, ctypes.c_int64), _ints(patch),
+                                      _ints(step), _ints(search), _ints(group_size), int(stages), int(mass_conserve),
+                                      ctypes.byref(prm) if prm is not None else None, info)
+        self._check(st)
+        D = int(info[3])
+        return {"tiles": int(info[0]), "region": int(info[1]), "capacity": int(info[2]), "axes": D,
+                "core": tuple(int(info[4 + a]) for a in range(D))}
+
     def bmnd_set_profiling(self, enable: bool):
         self._check(self._lib.bmnd_set_profiling(self.handle, int(bool(enable))))
 
@@ -522,3 +566,13 @@ def exported_symbols(path: str = LIB_PATH) -> list[str]:
     """Names of include/bmnd.h entry points present in the library (no GPU needed)."""
     lib = ctypes.CDLL(path)
     return [n for n in EXPORTS if hasattr(lib, n)]
+
+
+def bmnd_fp32_fma_peak(device: int = 0) -> float:
+    """Measured FP32 FMA throughput of a device, TFLOP/s."""
+    lib = load()
+    v = ctypes.c_double()
+    st = lib.bmnd_fp32_fma_peak(int(device), ctypes.byref(v))
+    if st != OK:
+        raise BmndError(st, "bmnd_fp32_fma_peak failed")
+    return v.value

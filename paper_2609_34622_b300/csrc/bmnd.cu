@@ -26,6 +26,7 @@ void launch_export(int D, const DJob *jobs, int ntiles, const int64_t *tile_off,
 void launch_sched(const SGeom &s, unsigned char *flags, const DJob *jobs, int ntiles, int *ref_local,
                   int *ref_count, cudaStream_t st);
 void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t st);
+void launch_fma_peak(float *out, int blocks, int threads, int iters);
 void launch_sched_mark(const SGeom &s, unsigned char *flags, cudaStream_t st);
 void launch_coverage(const CovGeom &c, const unsigned char *flags, int32_t *cov, unsigned long long *sums,
                      cudaStream_t st);
@@ -67,6 +68,9 @@ struct bmnd_ctx {
   float2 *mom[4] = {nullptr, nullptr, nullptr, nullptr};
   // fixed-point tables of the Poisson distances for count data (PFIX_*)
   long long *pfix[4] = {nullptr, nullptr, nullptr, nullptr};
+  // device copies of host arrays for bmnd_denoise_batch_host (grown on use)
+  float *hio = nullptr;
+  size_t hio_floats = 0;
 };
 
 namespace {
@@ -1139,6 +1143,7 @@ bmnd_status bmnd_destroy(bmnd_ctx *ctx) {
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->tab) cudaFree(ctx->tab);
   if (ctx->diag) cudaFree(ctx->diag);
+  if (ctx->hio) cudaFree(ctx->hio);
   if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->djobs) cudaFree(ctx->djobs);
   if (ctx->hjobs) cudaFreeHost(ctx->hjobs);
@@ -1567,6 +1572,114 @@ bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
                   stages, jb.mass_conserve & (stages == 2 ? 3 : 1)};
   }
   return run_jobs(ctx, plans, io, pr, 1, stages, nullptr, (cudaStream_t)stream);
+}
+
+bmnd_status bmnd_denoise_batch_host(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs, const bmnd_params *params,
+                                    void *stream) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (n_jobs < 1 || !jobs) return fail(ctx, BMND_EINVAL, "no jobs");
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> n(n_jobs);
+  size_t total = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    const bmnd_job &jb = jobs[i];
+    if (!jb.y || !jb.out) return fail(ctx, BMND_EINVAL, "job %d: null y or out", i);
+    if (jb.ndim < 1 || jb.ndim > BMND_MAX_NDIM) return fail(ctx, BMND_EINVAL, "job %d: bad ndim", i);
+    int64_t c = 1;
+    for (int d = 0; d < jb.ndim; ++d) {
+      if (jb.shape[d] < 1) return fail(ctx, BMND_EINVAL, "job %d: bad shape", i);
+      c *= jb.shape[d];
+    }
+    n[i] = c;
+    total += 2 * (size_t)((c + 63) & ~(int64_t)63);
+  }
+  if (total > ctx->hio_floats) {
+    CU(cudaStreamSynchronize(st));
+    if (ctx->hio) CU(cudaFree(ctx->hio));
+    ctx->hio = nullptr;
+    ctx->hio_floats = 0;
+    if (cudaMalloc(&ctx->hio, total * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BMND_ENOMEM, "cudaMalloc of %zu bytes for the host path failed", total * sizeof(float));
+    }
+    ctx->hio_floats = total;
+  }
+  std::vector<bmnd_job> dj(jobs, jobs + n_jobs);
+  size_t off = 0;
+  for (int i = 0; i < n_jobs; ++i) {
+    float *dy = ctx->hio + off, *dout = dy + ((n[i] + 63) & ~(int64_t)63);
+    off += 2 * (size_t)((n[i] + 63) & ~(int64_t)63);
+    CU(cudaMemcpyAsync(dy, jobs[i].y, n[i] * sizeof(float), cudaMemcpyHostToDevice, st));
+    dj[i].y = dy;
+    dj[i].out = dout;
+  }
+  bmnd_status rc = bmnd_denoise_batch(ctx, n_jobs, dj.data(), params, stream);
+  if (rc != BMND_OK) return rc;
+  for (int i = 0; i < n_jobs; ++i)
+    CU(cudaMemcpyAsync(jobs[i].out, dj[i].out, n[i] * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return BMND_OK;
+}
+
+bmnd_status bmnd_plan_info(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *patch, const int *step,
+                           const int *search, const int *group_size, int stages, int mass_conserve,
+                           const bmnd_params *params, int64_t info[8]) {
+  if (!ctx || !info || !group_size) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  Plan pl;
+  bmnd_status rc = make_plan(ctx, ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr, pl);
+  if (rc != BMND_OK) return rc;
+  info[0] = pl.g.ntiles;
+  info[1] = pl.g.region;
+  info[2] = pl.g.cap;
+  info[3] = pl.D;
+  for (int a = 0; a < 4; ++a) info[4 + a] = a < pl.D ? pl.g.C[a] : 0;
+  return BMND_OK;
+}
+
+bmnd_status bmnd_fp32_fma_peak(int device, double *tflops) {
+  if (!tflops) return BMND_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return BMND_EINVAL;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return BMND_ECUDA;
+  float *out = nullptr;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) {
+    cudaGetLastError();
+    return BMND_ENOMEM;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(a);
+    launch_fma_peak(out, blocks, threads, iters);
+    cudaEventRecord(b);
+    e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && rep > 0) {
+      const double flop = 2.0 * (double)FMA_PEAK_CHAINS * iters * blocks * threads;
+      best = std::max(best, (float)(flop / (ms * 1e-3) / 1e12));
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BMND_ECUDA;
+  }
+  *tflops = best;
+  return BMND_OK;
 }
 
 }  // extern "C"

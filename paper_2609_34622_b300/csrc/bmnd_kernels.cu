@@ -3124,6 +3124,28 @@ stage_fn select_stage_kernel(int D, int jL, int kb, int minb, int stage) {
   return nullptr;
 }
 
+// FP32 FMA throughput: 8 independent chains per thread, 16 FMAs each per
+// iteration (FMA_PEAK_CHAINS per iteration), the result kept alive.
+__global__ void __launch_bounds__(256) k_fma_peak(float *out, int iters) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+  const float b = 0.9999999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+void launch_fma_peak(float *out, int blocks, int threads, int iters) { k_fma_peak<<<blocks, threads>>>(out, iters); }
+
 void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t st) {
   k_ref_base<<<1, 1024, 0, st>>>(count, ntiles, ref_base);
 }

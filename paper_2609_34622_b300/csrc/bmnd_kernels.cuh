@@ -140,6 +140,9 @@ constexpr int TAB_BYTES = TAB64_OFFSET + GEN_TOTAL * 8;
 
 constexpr int MOMENT_NMAX = 4096;
 
+// FP32 throughput probe: independent FMA chains per thread
+constexpr int FMA_PEAK_CHAINS = 8 * 16;
+
 // Fixed-point tables of a Poisson distance for count data (int64, units
 // 2^-32 unless stated): at PFIX_A, indexed by a count K <= PFIX_K:
 // deviance K ln(2K), Pearson floor(2^64 / K) (K >= 1), Anscombe

@@ -12,7 +12,7 @@ def test_header_symbols_exported():
     B.build()
     import paper_2609_34622_b300.bmnd as bm
     hdr = open(os.path.join(ROOT, "include", "bmnd.h")).read()
-    declared = sorted(set(re.findall(r"\b(bmnd_[a-z_]+)\s*\(", hdr)))
+    declared = sorted(set(re.findall(r"\b(bmnd_[a-z0-9_]+)\s*\(", hdr)))
     assert declared, "no declarations found"
     assert set(declared) == set(bm.EXPORTS)
     assert bm.exported_symbols() == bm.EXPORTS
