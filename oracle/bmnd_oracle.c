@@ -682,13 +682,19 @@ int or_match_ref(const or_params *p, const double *g, int stage, int64_t ref_lin
              * sums over the patch entries are exact (xsum, as for the
              * Poisson distances), so a score depends only on the multiset of
              * its terms and patches whose terms are a permutation of each
-             * other tie exactly, as in real arithmetic */
+             * other tie exactly, as in real arithmetic.  Each square enters
+             * exactly too, as its rounded value plus the remainder fma(d, d,
+             * -d^2): the difference of two float32 values is exact in
+             * double, its square may need more than 53 bits.  The SSD is
+             * then the exact real SSD of the inputs, rounded once */
             or_xsum ssd, bias;
             xsum_init(&ssd);
             xsum_init(&bias);
             for (int64_t i = 0; i < P; ++i) {
                 double pi = g[ref_lin + off[i]], qi = g[lin + off[i]];
-                xsum_add(&ssd, (qi - pi) * (qi - pi));
+                double d = qi - pi, h = d * d;
+                xsum_add(&ssd, h);
+                xsum_add(&ssd, fma(d, d, -h));
                 if (p->noise_kind == 1) xsum_add(&bias, pos(pi + qi));
             }
             double B = p->noise_kind == 1 ? p->s_p * xsum_value(&bias) : 2.0 * (double)P * p->sigma * p->sigma;

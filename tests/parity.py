@@ -292,14 +292,17 @@ def stage1_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, w
     return float(mask.mean()), nt
 
 
-def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, what=""):
-    """Both stages under a Poisson distance (stage 1) and SSD on the pilot
-    (stage 2): stage-1 groups as in stage1_poisson_contract; the voxel
-    contract against the oracle's stages (float32 pilot) outside the patches
-    of the stage-1 groups that differ, dilated by the stage-2 search radius
-    and patch (where the two pilots differ and stage-2 matching reads them),
+def two_stage_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm=None, scorer=None, what=""):
+    """Both stages: stage-1 groups identical except at near-ties of the
+    oracle's FP64 scores (scorer for a Poisson distance, else SSD with the
+    noise-bias correction); the voxel contract against the oracle's stages
+    (float32 pilot between them) outside the patches of the stage-1 groups
+    that differ, dilated by the stage-2 search radius and patch (where the
+    two pilots differ and stage-2 matching reads them; by one more patch with
+    mass conservation, whose correction spreads over overlapping groups),
     and outside the patches of the stage-2 groups that differ; PSNR within
-    0.01 dB of the oracle's double-precision run."""
+    0.01 dB of the oracle's double-precision run.  Returns the fraction of
+    voxels compared."""
     import torch
     opilot = oracle.stage(p, y, None, 1).astype(np.float32)
     ref = oracle.stage(p, y, opilot.astype(np.float64), 2)
@@ -308,9 +311,15 @@ def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer
     M1, M2 = cfg["group_size"]
     gpu1 = groups_of(ctx, cuda(y), cfg, 1, prm)
     oo = oracle.schedule(p)
-    _, _, nb, bad = group_agreement(gpu1, (oo, og1[:, :M1], oc1), y, cfg["patch"], cfg["search"], cfg["noise"],
-                                    0.0, 0.0, max_explain=len(oo), scorer=scorer, rel=POISSON_TIE_REL,
-                                    tol=POISSON_TIE_REL)
+    P = int(np.prod(cfg["patch"]))
+    if scorer is None:
+        _, _, nb, bad = group_agreement(gpu1, (oo, og1[:, :M1], oc1), y.astype(np.float64), cfg["patch"],
+                                        cfg["search"], cfg["noise"], 3.0, 3000.0 * P / 255.0 ** 2,
+                                        max_explain=len(oo))
+    else:
+        _, _, nb, bad = group_agreement(gpu1, (oo, og1[:, :M1], oc1), y, cfg["patch"], cfg["search"], cfg["noise"],
+                                        0.0, 0.0, max_explain=len(oo), scorer=scorer, rel=POISSON_TIE_REL,
+                                        tol=POISSON_TIE_REL)
     assert nb == 0, bad
     gpilot = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
     ctx.bmnd_stage(cuda(y), None, gpilot, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], M1, 1,
@@ -318,6 +327,14 @@ def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer
     gpu2 = groups_of(ctx, gpilot, cfg, 2, prm)
     _, _, og2, oc2 = oracle.stage(p, y, opilot.astype(np.float64), 2, want_den=True, want_groups=True)
     a1 = footprint_mask(y.shape, cfg["patch"], differing_members(gpu1, og1[:, :M1], oc1))
+    if not a1.any():
+        # identical stage-1 groups: the two pilots differ by float rounding
+        # only, so the stage-2 groups must agree except at near-ties of the
+        # oracle's scores on its own pilot (SSD, tau of the Wiener stage)
+        _, _, nb2, bad2 = group_agreement(gpu2, (oo, og2[:, :M2], oc2), opilot.astype(np.float64),
+                                          cfg["patch"], cfg["search"], cfg["noise"], 0.0, 400.0 * P / 255.0 ** 2,
+                                          max_explain=len(oo))
+        assert nb2 == 0, bad2
     reach = [(w - 1) // 2 + j for w, j in zip(cfg["search"], cfg["patch"])]
     bad_area = dilate(a1, reach) | footprint_mask(y.shape, cfg["patch"], differing_members(gpu2, og2[:, :M2], oc2))
     if p.mass_conserve:
@@ -326,3 +343,8 @@ def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer
     assert_voxels_on(got, ref, mask, what)
     assert abs(psnr(got, x) - psnr(ref64, x)) <= PSNR_DB
     return float(mask.mean())
+
+
+def two_stage_poisson_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, what=""):
+    """two_stage_contract under a Poisson distance in stage 1."""
+    return two_stage_contract(ctx, oracle, p, y, x, cfg, got, cuda, prm, scorer, what)

@@ -269,3 +269,23 @@ def test_full_size_1d_sampled(ctx, oracle):
     g2 = out.cpu().numpy().astype(np.float64)[pts]
     assert np.sum(np.abs(g1 - r1) > 1e-4) <= 1, np.abs(g1 - r1).max()
     assert np.sum(np.abs(g2 - r2) > 1e-4) <= 1, np.abs(g2 - r2).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("mode", ["noise_floor", "variance_scaled"])
+def test_stage2_pilot_power_modes(ctx, oracle, case, mode):
+    """Def. "Pilot-power modes": the Wiener gain with a = 1 (noise floor) and
+    a = s_v (variance scaled), stage 2 on the same pilot, under the voxel
+    contract."""
+    import torch
+    import paper_2609_34622_b300.bmnd as bm
+    name, y, x, cfg = case
+    p = _oparams(oracle, y, cfg, power_mode=mode)
+    pilot = oracle.stage(p, y, None, 1).astype(np.float32)
+    ref = oracle.stage(p, y, pilot.astype(np.float64), 2)
+    out = torch.empty(y.shape, dtype=torch.float32, device="cuda:0")
+    ctx.bmnd_stage(_cuda(y), _cuda(pilot), out, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"],
+                   cfg["group_size"][1], 2, 0, bm.params(power_mode=mode))
+    got = out.cpu().numpy()
+    PT.assert_voxels(got, ref, 1.0, what="%s %s" % (name, mode))
+    assert abs(PT.psnr(got, x) - PT.psnr(ref, x)) <= PT.PSNR_DB

@@ -756,3 +756,26 @@ def test_shared_source_variance_monte_carlo(oracle):
     var = oracle.filter_group(p, 1, x, None, members)["var"].ravel()
     big = var > 0.05 * var.max()
     np.testing.assert_allclose(emp[big], var[big], rtol=0.08)
+
+
+def test_ssd_is_the_exact_sum_rounded_once(oracle):
+    """Eq. (ssd) with exact summation: the oracle's score of every candidate
+    equals the exact rational SSD of the float32 inputs rounded once to
+    double (fractions.Fraction), on data spanning 2^-20 to 2^4, where the
+    squares need more than 53 bits and a sum of rounded squares would miss."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    y = (rng.uniform(0, 16, 24) * np.where(rng.uniform(size=24) < 0.3, 2.0 ** -24, 1.0)).astype(np.float32)
+    yd = y.astype(np.float64)
+    p = oracle.params(y.shape, (4,), (1,), (21,), ("gaussian", 0.0), (16, 16), gamma_ht=0.0, tau_ht=1e30,
+                      group_transform="dct")
+    mem, sc = oracle.match_ref(p, yd, 1, 10)
+    misses = 0
+    for m, s in zip(mem[1:], sc[1:]):
+        exact = sum((Fraction(float(yd[m + i])) - Fraction(float(yd[10 + i]))) ** 2 for i in range(4))
+        assert s == float(exact), (m, s, float(exact))
+        rounded = 0.0
+        for i in range(4):
+            rounded += (yd[m + i] - yd[10 + i]) ** 2
+        misses += rounded != float(exact)
+    assert misses > 0
