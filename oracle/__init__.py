@@ -65,6 +65,7 @@ class _Params(ctypes.Structure):
         ("ht_rule", ctypes.c_int),
         ("weight_domain", ctypes.c_int),
         ("cov_planes", ctypes.c_int),
+        ("spatial_ht", ctypes.c_int),
     ]
 
 
@@ -77,6 +78,7 @@ METRICS = {"ssd": 0, "poisson_deviance": 1, "pearson": 2, "anscombe_ssd": 3}
 POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardized": 2}
 HT_RULES = {"hard": 0, "soft": 1}
 WEIGHT_DOMAINS = {"coefficient": 0, "windowed_synthesis": 1}
+SPATIAL_TRANSFORMS = {"dct": 0, "bior1.5": 1}
 NMAX = 4096  # moment tables cover pooled counts 0..NMAX (larger counts use NMAX)
 
 _lib = None
@@ -97,7 +99,9 @@ def _load():
         _lib.or_denoise.argtypes = [P(_Params), d, d, d]
         _lib.or_stage_points.argtypes = [P(_Params), d, d, ctypes.c_int, ctypes.c_int64, i64, d]
         _lib.or_filter_group.argtypes = [P(_Params), ctypes.c_int, d, d, ctypes.c_int, i64, d, d, d, d, d]
-        _lib.or_group_transform.argtypes = [P(_Params), ctypes.c_int, d, ctypes.c_int]
+        _lib.or_group_transform.argtypes = [P(_Params), ctypes.c_int, ctypes.c_int, d, ctypes.c_int]
+        _lib.or_bior15_matrix.argtypes = [ctypes.c_int, d]
+        _lib.or_bior15_synthesis.argtypes = [ctypes.c_int, d]
         _lib.or_dct_matrix.argtypes = [ctypes.c_int, d]
         _lib.or_haar_matrix.argtypes = [ctypes.c_int, d]
         _lib.or_kaiser.argtypes = [ctypes.c_int, ctypes.c_double, d]
@@ -174,6 +178,9 @@ def params(shape, patch, step, search, noise=("poisson", 1.0), group_size=(16, 3
     # leading group-axis planes with the shared-source variance (Sec. 5;
     # App. A lists 4, the CUDA path implements 0 = the diagonal model)
     p.cov_planes = int(kw.pop("cov_planes", 0))
+    # spatial transform of the hard-threshold stage (App. A: bior1.5; the
+    # DCT is the default here; stage 2 always uses the DCT)
+    p.spatial_ht = SPATIAL_TRANSFORMS[kw.pop("spatial_transform", "dct")]
     if kw:
         raise TypeError("unknown oracle parameters: %s" % sorted(kw))
     return p
@@ -280,13 +287,30 @@ def filter_group(p: _Params, stage: int, y, pilot, members):
     return dict(Y=Y.reshape(sh), var=var.reshape(sh), C=C.reshape(sh), p=pt.reshape(sh), w=w)
 
 
-def group_transform(p: _Params, x, mode: int = 0):
-    """mode 0: T x, 1: T^T x, 2: (T.^2) x for a group tensor x of shape
-    (count, *patch)."""
+def group_transform(p: _Params, x, mode: int = 0, stage: int = 1):
+    """The group transform of stage `stage` on a group tensor x of shape
+    (count, *patch): mode 0: T x, 1: U x with U = T^{-1} the synthesis,
+    2: (T.^2) x, 3: U^T x."""
     lib = _load()
     a = _f64(x).copy()
-    lib.or_group_transform(ctypes.byref(p), a.shape[0], _dptr(a), mode)
+    lib.or_group_transform(ctypes.byref(p), stage, a.shape[0], _dptr(a), mode)
     return a
+
+
+def bior15_matrix(n: int) -> np.ndarray:
+    """bior1.5 analysis matrix of a periodic length-n axis (n a power of
+    two), full depth, coefficients coarsest first."""
+    a = np.empty(n * n)
+    _load().or_bior15_matrix(n, _dptr(a))
+    return a.reshape(n, n)
+
+
+def bior15_synthesis(n: int) -> np.ndarray:
+    """bior1.5 synthesis matrix (columns: patches synthesized from unit
+    coefficients), built from the synthesis filters."""
+    a = np.empty(n * n)
+    _load().or_bior15_synthesis(n, _dptr(a))
+    return a.reshape(n, n)
 
 
 def dct_matrix(n: int) -> np.ndarray:

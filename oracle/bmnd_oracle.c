@@ -14,9 +14,10 @@
  *   - block matching: Def. "Gaussian SSD matching statistic" (Eq. ssd),
  *     Props. "Gaussian / Scaled-Poisson SSD noise bias", Def. "Noise-bias-
  *     corrected SSD" (Sec. 4.4); group rules of App. A;
- *   - group transform T = (group-axis transform) (x) DCT_{j_0} (x) ... built as
- *     explicit orthonormal matrices and applied as mode products (Def. "Patch-
- *     group observation model");
+ *   - group transform T = (group-axis transform) (x) S_{j_0} (x) ... built as
+ *     explicit matrices and applied as mode products (Def. "Patch-group
+ *     observation model"), S the orthonormal DCT or, in stage 1 when
+ *     selected, the biorthogonal bior1.5 of App. A with its own synthesis;
  *   - coefficient variances: Lemma "Covariance propagation", Cor. "White-noise
  *     transform variance", Prop. "Diagonal Poisson variance propagation",
  *     Def. "Poisson variance map";
@@ -88,6 +89,8 @@ typedef struct or_params {
                            /* domain (Sec. 7.3), both stages                   */
     int cov_planes;        /* k_ex: leading group-axis planes with the         */
                            /* shared-source variance (Sec. 5; 0 = diagonal)    */
+    int spatial_ht;        /* spatial transform of stage 1: 0 DCT, 1 bior1.5   */
+                           /* (App. A); stage 2 always uses the DCT            */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -162,6 +165,85 @@ void or_haar_matrix(int n, double *H)
     }
 }
 
+/* Biorthogonal spline wavelet bior1.5: the Cohen-Daubechies-Feauveau pair
+ * with the box (Haar) synthesis scaling function and five vanishing moments
+ * of the synthesis wavelet (N = 1, N~ = 5; the filter table of this family in
+ * I. Daubechies, "Ten Lectures on Wavelets", SIAM 1992, Sec. 8.3), the
+ * spatial transform of the hard-threshold stage in App. A.  Filters, tap
+ * index k:
+ *   analysis lowpass   ht[k] = (sqrt(2)/2) / 128 x (3, -3, -22, 22, 128, 128,
+ *                              22, -22, -3, 3) for k = -4..5,
+ *   analysis highpass  gt[0] = sqrt(2)/2, gt[1] = -sqrt(2)/2,
+ *   synthesis lowpass  h[0] = h[1] = sqrt(2)/2,
+ *   synthesis highpass g[k] = (-1)^k ht[1 - k] for k = -4..5.
+ * READING: the paper names the transform but not its boundary handling or
+ * depth; as in the DCT and Haar matrices, a patch axis of length n = 2^m is
+ * transformed by itself: periodic extension, one level maps x (length l) to
+ *   a[i] = sum_k ht[k] x[(2i + k) mod l],  d[i] = sum_k gt[k] x[(2i + k) mod l],
+ * repeated on a down to length 1 (full depth), coefficients ordered
+ * [a_m, d_m, d_{m-1}, ..., d_1] (coarsest first, as the Haar rows).  The
+ * transform is not orthonormal: the synthesis U = T^{-1} is the inverse
+ * cascade x[i] = sum_j h[i - 2j] a[j] + g[i - 2j] d[j] (indices mod l),
+ * built here from the synthesis filters on its own. */
+static const double bior15_taps[10] = {3, -3, -22, 22, 128, 128, 22, -22, -3, 3};
+
+static double bior15_ht(int k)
+{
+    return (k < -4 || k > 5) ? 0.0 : bior15_taps[k + 4] * (sqrt(0.5) / 128.0);
+}
+
+static double bior15_gt(int k) { return k == 0 ? sqrt(0.5) : (k == 1 ? -sqrt(0.5) : 0.0); }
+static double bior15_h(int k) { return (k == 0 || k == 1) ? sqrt(0.5) : 0.0; }
+static double bior15_g(int k) { return ((k & 1) ? -1.0 : 1.0) * bior15_ht(1 - k); }
+
+static int pmod(int a, int l) { int r = a % l; return r < 0 ? r + l : r; }
+
+/* Analysis matrix T (n x n, row k = coefficient k), n a power of two. */
+void or_bior15_matrix(int n, double *T)
+{
+    double *x = (double *)malloc(sizeof(double) * 2 * (size_t)n), *y = x + n;
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) x[i] = i == col ? 1.0 : 0.0;
+        /* coefficients land in x: [a | d] of the current length l */
+        for (int l = n; l >= 2; l /= 2) {
+            for (int i = 0; i < l / 2; ++i) {
+                double a = 0.0, d = 0.0;
+                for (int k = -4; k <= 5; ++k) {
+                    a += bior15_ht(k) * x[pmod(2 * i + k, l)];
+                    d += bior15_gt(k) * x[pmod(2 * i + k, l)];
+                }
+                y[i] = a;
+                y[l / 2 + i] = d;
+            }
+            memcpy(x, y, sizeof(double) * (size_t)l);
+        }
+        for (int k = 0; k < n; ++k) T[(size_t)k * n + col] = x[k];
+    }
+    free(x);
+}
+
+/* Synthesis matrix U (n x n, column k = the patch synthesized from unit
+ * coefficient k) by the inverse cascade with the synthesis filters. */
+void or_bior15_synthesis(int n, double *U)
+{
+    double *x = (double *)malloc(sizeof(double) * 2 * (size_t)n), *y = x + n;
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) x[i] = i == col ? 1.0 : 0.0;
+        for (int l = 2; l <= n; l *= 2) {
+            /* x[0 .. l/2) approximations, x[l/2 .. l) details of length
+             * l/2; every tap k of the filters at 2j + k (mod l), so taps
+             * that wrap more than once around a short period all count */
+            for (int i = 0; i < l; ++i) y[i] = 0.0;
+            for (int j = 0; j < l / 2; ++j)
+                for (int k = -4; k <= 5; ++k)
+                    y[pmod(2 * j + k, l)] += bior15_h(k) * x[j] + bior15_g(k) * x[l / 2 + j];
+            memcpy(x, y, sizeof(double) * (size_t)l);
+        }
+        for (int i = 0; i < n; ++i) U[(size_t)i * n + col] = x[i];
+    }
+    free(x);
+}
+
 /* Modified Bessel function of the first kind, order 0, by its power series
  * sum_k ((x/2)^k / k!)^2. */
 double or_bessel_i0(double x)
@@ -191,31 +273,53 @@ void or_kaiser(int n, double beta, double *w)
 
 /* The factors of T = A_0 (x) A_1 (x) ... (x) A_D acting on a group tensor of
  * shape (n, j_0, ..., j_{D-1}) stored in C order: A_0 is the group-axis
- * transform (Haar or DCT of size n), A_{1+d} the DCT of size j_d. */
+ * transform (Haar or DCT of size n), A_{1+d} the spatial transform of axis d
+ * (the DCT of size j_d, or bior1.5 in stage 1 when selected).  B_a is the
+ * synthesis factor: the transpose for the orthonormal Haar and DCT, the
+ * synthesis matrix of bior1.5, so U = T^{-1} = B_0 (x) ... (x) B_D. */
 typedef struct {
     int nd;                 /* D + 1 */
     int dims[OR_MAXD + 1];
     double *A[OR_MAXD + 1]; /* dims[a] x dims[a] each */
+    double *B[OR_MAXD + 1];
 } or_factors;
 
-static void factors_build(const or_params *p, int n, or_factors *f)
+static void transpose_into(int n, const double *A, double *B)
+{
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) B[c * n + r] = A[r * n + c];
+}
+
+static void factors_build(const or_params *p, int stage, int n, or_factors *f)
 {
     f->nd = p->ndim + 1;
     f->dims[0] = n;
     f->A[0] = (double *)malloc(sizeof(double) * n * n);
+    f->B[0] = (double *)malloc(sizeof(double) * n * n);
     if (p->group_transform == 0) or_haar_matrix(n, f->A[0]);
     else or_dct_matrix(n, f->A[0]);
+    transpose_into(n, f->A[0], f->B[0]);
     for (int d = 0; d < p->ndim; ++d) {
         int j = p->patch[d];
         f->dims[1 + d] = j;
         f->A[1 + d] = (double *)malloc(sizeof(double) * j * j);
-        or_dct_matrix(j, f->A[1 + d]);
+        f->B[1 + d] = (double *)malloc(sizeof(double) * j * j);
+        if (stage == 1 && p->spatial_ht == 1) {
+            or_bior15_matrix(j, f->A[1 + d]);
+            or_bior15_synthesis(j, f->B[1 + d]);
+        } else {
+            or_dct_matrix(j, f->A[1 + d]);
+            transpose_into(j, f->A[1 + d], f->B[1 + d]);
+        }
     }
 }
 
 static void factors_free(or_factors *f)
 {
-    for (int a = 0; a < f->nd; ++a) free(f->A[a]);
+    for (int a = 0; a < f->nd; ++a) {
+        free(f->A[a]);
+        free(f->B[a]);
+    }
 }
 
 /* x <- (A along axis `axis`) x, where mode = 0: A, 1: A^T, 2: A.^2 (entrywise
@@ -244,14 +348,18 @@ static void mode_product(double *x, const int *dims, int nd, int axis,
     memcpy(x, tmp, sizeof(double) * (size_t)tot);
 }
 
-/* Apply T (mode 0), T^T = T^{-1} (mode 1) or T.^2 (mode 2) to a group tensor.
- * For a Kronecker product the entrywise square is the Kronecker product of
- * the entrywise squares, so mode 2 is the squared transform used for
- * sigma_k^2 = sum_i T_ki^2 m_v(u_i). */
+/* Apply to a group tensor: mode 0 T, 1 U = T^{-1} (the synthesis), 2 T.^2,
+ * 3 U^T.  For a Kronecker product the entrywise square is the Kronecker
+ * product of the entrywise squares, so mode 2 is the squared transform used
+ * for sigma_k^2 = sum_i T_ki^2 m_v(u_i). */
 static void apply_T(const or_factors *f, double *x, int mode, double *tmp)
 {
-    for (int a = 0; a < f->nd; ++a)
-        mode_product(x, f->dims, f->nd, a, f->A[a], mode, tmp);
+    for (int a = 0; a < f->nd; ++a) {
+        if (mode == 0) mode_product(x, f->dims, f->nd, a, f->A[a], 0, tmp);
+        else if (mode == 1) mode_product(x, f->dims, f->nd, a, f->B[a], 0, tmp);
+        else if (mode == 2) mode_product(x, f->dims, f->nd, a, f->A[a], 2, tmp);
+        else mode_product(x, f->dims, f->nd, a, f->B[a], 1, tmp);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -741,31 +849,29 @@ typedef struct {
 
 /* Diagonal of the windowed synthesis metric (Def. "Windowed synthesis
  * metrics", Eq. patch-synthesis-metric) for the separable group transform
- * U = V (x) U_s, with V the group-axis inverse and U_s the spatial inverse
- * (the Kronecker product of the axis DCT^T), and W_p the Kaiser window of
- * the overlap-add: (H_{g,j})_{kk} = |V_jl|^2 omq[q] for k = (l, q), with
+ * U = V (x) U_s, with V the group-axis inverse and U_s the spatial synthesis
+ * (the Kronecker product of the axis synthesis factors B_d), and W_p the
+ * Kaiser window of the overlap-add: (H_{g,j})_{kk} = |V_jl|^2 omq[q] for
+ * k = (l, q), with
  *   omq[q] = sum_p |(U_s)_pq|^2 w_p^2
  * over the P entries p of a patch, written here as that full sum (the
- * entries of U_s formed as products of the axis DCT entries). */
-static void synthesis_window_energy(const or_params *p, double *omq)
+ * entries of U_s formed as products of the axis synthesis entries). */
+static void synthesis_window_energy(const or_params *p, const or_factors *f, double *omq)
 {
     int64_t P = prod_patch(p);
-    double C[OR_MAXD][1024], k1[OR_MAXD][256];
-    for (int d = 0; d < p->ndim; ++d) {
-        or_dct_matrix(p->patch[d], C[d]);
-        or_kaiser(p->patch[d], p->kaiser_beta, k1[d]);
-    }
+    double k1[OR_MAXD][256];
+    for (int d = 0; d < p->ndim; ++d) or_kaiser(p->patch[d], p->kaiser_beta, k1[d]);
     for (int64_t q = 0; q < P; ++q) {
         double e = 0.0;
         for (int64_t i = 0; i < P; ++i) {
-            /* (U_s)_iq = prod_d DCT_d[q_d][i_d]; w_i = prod_d kaiser_d[i_d] */
+            /* (U_s)_iq = prod_d B_d[i_d][q_d]; w_i = prod_d kaiser_d[i_d] */
             int64_t ri = i, rq = q;
             double u = 1.0, w = 1.0;
             for (int d = p->ndim - 1; d >= 0; --d) {
                 int id = (int)(ri % p->patch[d]), qd = (int)(rq % p->patch[d]);
                 ri /= p->patch[d];
                 rq /= p->patch[d];
-                u *= C[d][qd * p->patch[d] + id];
+                u *= f->B[1 + d][id * p->patch[d] + qd];
                 w *= k1[d][id];
             }
             e += u * u * w * w;
@@ -788,7 +894,7 @@ static int cmp_src(const void *a, const void *b)
  * group-axis planes l < k_ex: sigma_k^2 = sum over the distinct source
  * locations u of the group of |t_ku|^2 m_v(u), with the effective weights
  * t_ku = sum of T_ki over the entries i taken from u (Def. "Effective
- * transform weights"), T_ki = A0[l][m] prod_d DCT_d[q_d][p_d] for entry
+ * transform weights"), T_ki = A0[l][m] prod_d A_d[q_d][p_d] for entry
  * i = (member m, patch entry p).  mv[i] holds m_v(u_i).  READING: the
  * "leading transform indices" are the first k_ex planes of the group-axis
  * transform (App. A and B count exact covariance planes). */
@@ -844,7 +950,7 @@ static void filter_group(const or_params *p, int stage, const double *y,
     int n = G->count;
     int64_t d = (int64_t)n * P;
     or_factors f;
-    factors_build(p, n, &f);
+    factors_build(p, stage, n, &f);
     double *Y = work, *S2 = work + d, *Gm = work + 2 * d, *tmp = work + 3 * d;
     /* gather the observation group and the variance-map group */
     for (int m = 0; m < n; ++m)
@@ -870,7 +976,7 @@ static void filter_group(const or_params *p, int stage, const double *y,
      * factor omq[q] of the metric's diagonal; the coefficient domain is
      * omq = 1 (H = I) */
     double omq[1024];
-    if (p->weight_domain == 1) synthesis_window_energy(p, omq);
+    if (p->weight_domain == 1) synthesis_window_energy(p, &f, omq);
     else for (int64_t q = 0; q < P; ++q) omq[q] = 1.0;
     double r[64];
     for (int l = 0; l < n; ++l) r[l] = 0.0;
@@ -942,14 +1048,14 @@ static void filter_group(const or_params *p, int stage, const double *y,
         G->w[j] = R > 0.0 ? 1.0 / R : 1.0;
     }
     memcpy(G->p, G->C, sizeof(double) * (size_t)d);
-    apply_T(&f, G->p, 1, tmp);  /* p = U C, U = T^{-1} = T^T */
+    apply_T(&f, G->p, 1, tmp);  /* p = U C, U = T^{-1} */
     factors_free(&f);
 }
 
 /* Mass-conservation correction of one group (Sec. 8): zeta = w omega / eta,
  * h = U^T zeta, d_g = zeta^T y_g - h^T C, m = U^{-1} 1, C_mc = C +
  * d_g / (zeta^T 1) m, and the synthesized corrected group U C_mc into G->p. */
-static void mc_correct_group(const or_params *p, const double *y, const double *eta,
+static void mc_correct_group(const or_params *p, int stage, const double *y, const double *eta,
                              const double *omega, const int64_t *off, or_group *G,
                              double *work)
 {
@@ -957,7 +1063,7 @@ static void mc_correct_group(const or_params *p, const double *y, const double *
     int n = G->count;
     int64_t d = (int64_t)n * P;
     or_factors f;
-    factors_build(p, n, &f);
+    factors_build(p, stage, n, &f);
     double *zeta = work, *h = work + d, *m = work + 2 * d, *tmp = work + 3 * d;
     double zy = 0.0, z1 = 0.0;
     for (int j = 0; j < n; ++j)
@@ -969,7 +1075,7 @@ static void mc_correct_group(const or_params *p, const double *y, const double *
             z1 += z;
         }
     memcpy(h, zeta, sizeof(double) * (size_t)d);
-    apply_T(&f, h, 0, tmp);            /* h = U^T zeta = T zeta */
+    apply_T(&f, h, 3, tmp);            /* h = U^T zeta */
     for (int64_t k = 0; k < d; ++k) m[k] = 1.0;
     apply_T(&f, m, 0, tmp);            /* m = U^{-1} 1 = T 1 */
     double hC = 0.0;
@@ -1049,7 +1155,7 @@ int64_t or_stage(const or_params *p, const double *y, const double *pilot, int s
                     or_group *G = &grp[c];
                     G->count = or_match_ref(p, guide, stage, refs[base + c], M, G->members, scores);
                     filter_group(p, stage, y, pilot, off, G, work);
-                    if (sweep == 1) mc_correct_group(p, y, den, omega, off, G, work);
+                    if (sweep == 1) mc_correct_group(p, stage, y, den, omega, off, G, work);
                 }
                 free(work);
             }
@@ -1174,7 +1280,7 @@ int or_filter_group(const or_params *p, int stage, const double *y, const double
     if (Y_out || var_out) {
         /* recompute T y_g and the variances for inspection */
         or_factors f;
-        factors_build(p, count, &f);
+        factors_build(p, stage, count, &f);
         double *tmp = work;
         if (Y_out) {
             for (int m = 0; m < count; ++m)
@@ -1204,12 +1310,13 @@ int or_filter_group(const or_params *p, int stage, const double *y, const double
     return 0;
 }
 
-/* Group transform of an arbitrary group tensor (mode 0: T, 1: T^T, 2: T.^2). */
-int or_group_transform(const or_params *p, int count, double *x, int mode)
+/* Group transform of stage `stage` on an arbitrary group tensor (mode 0: T,
+ * 1: U = T^{-1}, 2: T.^2, 3: U^T). */
+int or_group_transform(const or_params *p, int stage, int count, double *x, int mode)
 {
     int64_t d = (int64_t)count * prod_patch(p);
     or_factors f;
-    factors_build(p, count, &f);
+    factors_build(p, stage, count, &f);
     double *tmp = (double *)malloc(sizeof(double) * (size_t)d);
     apply_T(&f, x, mode, tmp);
     free(tmp);

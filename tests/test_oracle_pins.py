@@ -779,3 +779,184 @@ def test_ssd_is_the_exact_sum_rounded_once(oracle):
             rounded += (yd[m + i] - yd[10 + i]) ** 2
         misses += rounded != float(exact)
     assert misses > 0
+
+
+# ---------------------------------------------------------------------------
+# bior1.5 spatial transform of the hard-threshold stage (App. A)
+# ---------------------------------------------------------------------------
+
+def _bior_hand(n):
+    """bior1.5 analysis matrices derived by hand (periodic, full depth,
+    coarsest first).  n = 2 and n = 4: the wrapped lowpass taps pair up to the
+    Haar filter, so the matrix is the Haar matrix.  n = 8: the level-1
+    approximations are a1[i] = (x[2i] + x[2i+1] + c (x[2i+2] - x[2i+3]
+    - x[2i-2] + x[2i-1])) / sqrt 2 with c = 22/128 (indices mod 8; the taps
+    +-3/128 cancel on a period of 8), and the coarser levels are Haar steps
+    on them."""
+    r2 = math.sqrt(2.0)
+    if n == 2:
+        return np.array([[1, 1], [1, -1]]) / r2
+    if n == 4:
+        return np.array([[.5, .5, .5, .5], [.5, .5, -.5, -.5], [1 / r2, -1 / r2, 0, 0], [0, 0, 1 / r2, -1 / r2]])
+    c = 11.0 / 64.0
+    T = np.zeros((8, 8))
+    T[0] = 1 / math.sqrt(8)
+    T[1] = np.array([1 - 2 * c, 1 + 2 * c, 1 + 2 * c, 1 - 2 * c, -1 + 2 * c, -1 - 2 * c, -1 - 2 * c, -1 + 2 * c]) / (2 * r2)
+    T[2] = np.array([1 + c, 1 - c, c - 1, -c - 1, -c, c, -c, c]) / 2
+    T[3] = np.array([-c, c, -c, c, 1 + c, 1 - c, c - 1, -c - 1]) / 2
+    for i in range(4):
+        T[4 + i, 2 * i], T[4 + i, 2 * i + 1] = 1 / r2, -1 / r2
+    return T
+
+
+@pytest.mark.parametrize("n", [2, 4, 8])
+def test_bior15_hand_values(oracle, n):
+    """App. A's bior1.5 on periodic patch axes of 2, 4 and 8 samples against
+    the hand derivation above."""
+    np.testing.assert_allclose(oracle.bior15_matrix(n), _bior_hand(n), atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32])
+def test_bior15_perfect_reconstruction(oracle, n):
+    """The synthesis cascade (from the synthesis filters alone) inverts the
+    analysis cascade on both sides: U T = T U = I, the biorthogonality of the
+    pair; T is not orthonormal for n >= 8 (rows of norm != 1)."""
+    T, U = oracle.bior15_matrix(n), oracle.bior15_synthesis(n)
+    np.testing.assert_allclose(U @ T, np.eye(n), atol=1e-13)
+    np.testing.assert_allclose(T @ U, np.eye(n), atol=1e-13)
+    if n >= 8:
+        assert np.max(np.abs(np.linalg.norm(T, axis=1) - 1)) > 0.02
+        assert np.max(np.abs(U - T.T)) > 0.05
+    # DC row 1/sqrt n; every detail row annihilates constants
+    np.testing.assert_allclose(T[0], 1 / math.sqrt(n), atol=1e-15)
+    np.testing.assert_allclose(T[1:].sum(axis=1), 0.0, atol=1e-14)
+
+
+def test_bior15_synthesis_wavelet_vanishing_moments(oracle):
+    """The family's defining property (N~ = 5): the synthesis highpass g has
+    five vanishing moments, sum_k g[k] k^p = 0 for p = 0..4 (and not for
+    p = 5).  g is read from the synthesis matrix of a 32-sample axis: the
+    column of the finest detail d_1[j] holds g[k] at 2j + k, k = -4..5."""
+    U = oracle.bior15_synthesis(32)
+    j = 8
+    col = U[:, 16 + j]
+    k = np.arange(-4, 6)
+    g = col[2 * j + k]
+    assert np.count_nonzero(np.abs(col) > 1e-15) == 10
+    mom = [np.sum(g * k.astype(float) ** p) for p in range(6)]
+    np.testing.assert_allclose(mom[:5], 0.0, atol=1e-13)
+    assert abs(mom[5]) > 1.0
+    # and the synthesis lowpass is the box: the column of a_m is constant
+    np.testing.assert_allclose(U[:, 0], 1 / math.sqrt(32), atol=1e-15)
+
+
+def _bior_group(oracle, **kw):
+    rng = np.random.default_rng(21)
+    x = rng.uniform(0.1, 1.0, size=(24, 24))
+    s_p = 0.05
+    y = rng.poisson(x / s_p) * s_p
+    p = oracle.params((24, 24), (8, 8), (3, 3), (9, 9), ("poisson", s_p), (8, 8), spatial_transform="bior1.5", **kw)
+    members = np.array([np.ravel_multi_index(c, (24, 24)) for c in [(3, 3), (5, 12), (14, 1), (10, 10)]])
+    offs = [np.ravel_multi_index((a, b), (24, 24)) for a in range(8) for b in range(8)]
+    u = np.array([[m + o for o in offs] for m in members]).ravel()
+    A = _bior_hand(8)
+    T = np.kron(oracle.haar_matrix(4), np.kron(A, A))
+    return p, y, members, u, T, s_p
+
+
+def test_bior15_group_coefficients_and_variances(oracle):
+    """Stage 1 with the bior1.5 spatial transform: Y = T y_g and sigma_k^2 =
+    sum_i T_ki^2 m_v(u_i) (Lemma "Covariance propagation", Prop. "Diagonal
+    Poisson variance propagation") with T = Haar (x) A (x) A from the hand
+    matrix A; at lambda = 0 the filter returns the group itself (synthesis =
+    exact inverse); stage 2 keeps the DCT."""
+    p, y, members, u, T, s_p = _bior_group(oracle)
+    g = oracle.filter_group(p, 1, y, None, members)
+    yg = y.ravel()[u]
+    np.testing.assert_allclose(g["Y"].ravel(), T @ yg, atol=1e-12)
+    np.testing.assert_allclose(g["var"].ravel(), (T * T) @ (s_p * yg), rtol=1e-12)
+    p0, *_ = _bior_group(oracle, lambda_ht=0.0)
+    g0 = oracle.filter_group(p0, 1, y, None, members)
+    np.testing.assert_allclose(g0["p"].ravel(), yg, atol=1e-12)
+    g2 = oracle.filter_group(p, 2, y, y, members)
+    Td = _full_T(oracle, 4, (8, 8))
+    np.testing.assert_allclose(g2["Y"].ravel(), Td @ yg, atol=1e-12)
+
+
+def test_bior15_coefficient_domain_patch_weights(oracle):
+    """Variance model, patch scope, with a non-orthonormal spatial transform:
+    the coefficient-domain surrogate R_j = sum_l |V_jl|^2 sum_q a_lq
+    sigma_lq^2 (Def. "Coefficient-domain hard-thresholding weighting models")
+    from the diagonal variances, checked with full matrices."""
+    p, y, members, u, T, s_p = _bior_group(oracle)
+    g = oracle.filter_group(p, 1, y, None, members)
+    a = (g["C"].ravel() != 0).astype(float)
+    S2 = (T * T) @ (s_p * y.ravel()[u])
+    V = oracle.haar_matrix(4).T
+    r = (a * S2).reshape(4, 64).sum(axis=1)
+    R = (V * V) @ r
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-12)
+
+
+@pytest.mark.parametrize("scope", ["patch", "group"])
+def test_bior15_windowed_weights_full_matrices(oracle, scope):
+    """Windowed synthesized-domain weights with the bior1.5 synthesis: R =
+    tr(H A Sigma A^H), H = U^H Q_j^H W_p^H W_p Q_j U with U = the inverse of
+    the hand-built T (numpy) and W_p the Kaiser window (numpy, beta 2)."""
+    p, y, members, u, T, s_p = _bior_group(oracle, weight_domain="windowed_synthesis", weight_scope=scope)
+    g = oracle.filter_group(p, 1, y, None, members)
+    a = (g["C"].ravel() != 0).astype(float)
+    S2 = (T * T) @ (s_p * y.ravel()[u])
+    U = np.linalg.inv(T)
+    w1 = np.kaiser(8, 2.0)
+    wp = np.outer(w1, w1).ravel()
+    Mx = np.diag(a * S2)
+    R = []
+    for j in range(4):
+        Q = np.zeros((64, 256))
+        Q[:, j * 64:(j + 1) * 64] = np.eye(64)
+        L = np.diag(wp) @ Q @ U
+        R.append(np.trace(L.T @ L @ Mx))
+    R = np.array(R) if scope == "patch" else np.full(4, np.sum(R))
+    np.testing.assert_allclose(g["w"], 1.0 / R, rtol=1e-11)
+
+
+def test_bior15_identity_and_mass_conservation(oracle):
+    """Whole denoiser with the bior1.5 stage-1 transform: identity at sigma =
+    0, lambda = 0 (exact synthesis); Thm. "Mass conservation after normalized
+    overlap-add" with the two-sweep correction, whose residual needs the
+    synthesis adjoint U^T, not T (Def. "Aggregation-aware constant-synthesis
+    correction")."""
+    rng = np.random.default_rng(9)
+    y = rng.uniform(0, 1, size=(26, 30))
+    p = oracle.params(y.shape, (8, 8), (3, 3), (9, 9), ("gaussian", 0.0), (8, 16), lambda_ht=0.0,
+                      spatial_transform="bior1.5")
+    out, pilot = oracle.denoise(p, y)
+    np.testing.assert_allclose(pilot, y, atol=1e-12)
+    x = synth.disc_rect_image((30, 28), rng)
+    yp = rng.poisson(x / 0.2) * 0.2
+    p = oracle.params(yp.shape, (8, 8), (3, 3), (9, 9), ("poisson", 0.2), (8, 16), mass_conserve=3,
+                      spatial_transform="bior1.5")
+    out, pilot = oracle.denoise(p, yp)
+    assert pilot.sum() == pytest.approx(yp.sum(), rel=1e-12)
+    assert out.sum() == pytest.approx(yp.sum(), rel=1e-12)
+    p0 = oracle.params(yp.shape, (8, 8), (3, 3), (9, 9), ("poisson", 0.2), (8, 16), mass_conserve=3)
+    out0, pilot0 = oracle.denoise(p0, yp)
+    assert np.max(np.abs(pilot - pilot0)) > 1e-3
+
+
+def test_bior15_shared_source_all_planes(oracle):
+    """Partial shared-source variance with the bior1.5 spatial factors: with
+    every plane exact, sigma_k^2 = (T Sigma_g T^T)_kk for the repeated-voxel
+    covariance (Eq. shared-voxel-group-covariance), full matrices from the
+    hand-built T."""
+    p, y, _, _, _, s_p = _bior_group(oracle, cov_planes=4)
+    members = np.array([np.ravel_multi_index(c, (24, 24)) for c in [(3, 3), (4, 5), (6, 3), (9, 9)]])
+    offs = [np.ravel_multi_index((a, b), (24, 24)) for a in range(8) for b in range(8)]
+    u = np.array([[m + o for o in offs] for m in members]).ravel()
+    A = _bior_hand(8)
+    T = np.kron(oracle.haar_matrix(4), np.kron(A, A))
+    g = oracle.filter_group(p, 1, y, None, members)
+    mv = s_p * np.maximum(y.ravel()[u], 0)
+    Sigma = np.where(u[:, None] == u[None, :], mv[:, None], 0.0)
+    np.testing.assert_allclose(g["var"].ravel(), np.diag(T @ Sigma @ T.T), rtol=1e-11, atol=1e-14)
