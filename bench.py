@@ -183,7 +183,7 @@ def oracle_sample(name: str, jobs):
 
 
 def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd", "fixed"), ht_rule="hard",
-                weight_domain="coefficient", cov_planes=0):
+                weight_domain="coefficient", cov_planes=0, spatial="dct"):
     import oracle
     oracle.build()
     vox, t0, reps = 0, time.perf_counter(), 0
@@ -191,7 +191,7 @@ def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd",
         for j in jobs:
             p = oracle.params(j.y.shape, j.patch, j.step, j.search, j.noise, j.group_size, j.stages,
                               j.mass_conserve, match_metric=matching[0], match_policy=matching[1], ht_rule=ht_rule,
-                              weight_domain=weight_domain, cov_planes=cov_planes)
+                              weight_domain=weight_domain, cov_planes=cov_planes, spatial_transform=spatial)
             oracle.denoise(p, j.y)
             vox += j.y.size
         reps += 1
@@ -443,6 +443,8 @@ def main():
                     help="stage-1 thresholding rule (Def. \"Coefficient thresholding\")")
     ap.add_argument("--weight-domain", default="coefficient", choices=["coefficient", "windowed_synthesis"],
                     help="aggregation-weight domain of both stages (Sec. 7.3)")
+    ap.add_argument("--spatial-transform", default="dct", choices=["dct", "bior1.5"],
+                    help="spatial transform of the hard-threshold stage (App. A lists bior1.5)")
     ap.add_argument("--cov-planes", type=int, default=0,
                     help="group-axis planes with the partial shared-source Poisson variance (Sec. 5)")
     args = ap.parse_args()
@@ -467,10 +469,12 @@ def main():
         vox = sum(j.y.size for j in sample)
         matching = (args.match_metric, args.match_policy)
         for _ in range(args.warmup):
-            time_oracle(sample, 0.0, 1, matching, args.ht_rule, args.weight_domain, args.cov_planes)
+            time_oracle(sample, 0.0, 1, matching, args.ht_rule, args.weight_domain, args.cov_planes,
+                        args.spatial_transform)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            time_oracle(sample, 0.0, 1, matching, args.ht_rule, args.weight_domain, args.cov_planes)
+            time_oracle(sample, 0.0, 1, matching, args.ht_rule, args.weight_domain, args.cov_planes,
+                        args.spatial_transform)
         el = time.perf_counter() - t0
         import oracle
         val = vox * args.steps / el
@@ -513,9 +517,11 @@ def main():
     vox_step = sum(j.y.size for j in jobs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     pmetric = args.match_metric != "ssd"
-    variant = pmetric or args.ht_rule != "hard" or args.weight_domain != "coefficient" or args.cov_planes > 0
+    variant = (pmetric or args.ht_rule != "hard" or args.weight_domain != "coefficient" or args.cov_planes > 0
+               or args.spatial_transform != "dct")
     prm = (bm.params(match_metric=args.match_metric, match_policy=args.match_policy, ht_rule=args.ht_rule,
-                     weight_domain=args.weight_domain, cov_planes=args.cov_planes) if variant else None)
+                     weight_domain=args.weight_domain, cov_planes=args.cov_planes,
+                     spatial_transform=args.spatial_transform) if variant else None)
 
     def step(yy, oo):
         if len(jobs) == 1:
@@ -716,6 +722,8 @@ def main():
         line["config"]["weight_domain"] = args.weight_domain
     if args.cov_planes > 0:
         line["config"]["cov_planes"] = args.cov_planes
+    if args.spatial_transform != "dct":
+        line["config"]["spatial_transform"] = args.spatial_transform
     if pmetric:
         # the FLOP model above is the SSD path's; the Poisson distances spend
         # divisions, logarithms and square roots per entry pair that it does
@@ -736,7 +744,7 @@ def main():
         sample, sdesc = oracle_sample(args.workload, jobs)
         v, el, reps, cores = time_oracle(sample, 10.0, matching=(args.match_metric, args.match_policy),
                                          ht_rule=args.ht_rule, weight_domain=args.weight_domain,
-                                         cov_planes=args.cov_planes)
+                                         cov_planes=args.cov_planes, spatial=args.spatial_transform)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%s, both stages, %d repetition(s), %.1f s" % (sdesc, reps, el)}
     ctx.close()

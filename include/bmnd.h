@@ -72,6 +72,8 @@ enum { BMND_POLICY_FIXED = 0, BMND_POLICY_REFERENCE = 1, BMND_POLICY_STANDARDIZE
 enum { BMND_HT_HARD = 0, BMND_HT_SOFT = 1 };
 /* Aggregation-weight domain (Sec. 7.3). */
 enum { BMND_DOMAIN_COEFFICIENT = 0, BMND_DOMAIN_WINDOWED = 1 };
+/* Spatial transform of the hard-threshold stage (App. A). */
+enum { BMND_SPATIAL_DCT = 0, BMND_SPATIAL_BIOR15 = 1 };
 /* The finite-count moment tables cover pooled counts 0..BMND_MOMENT_NMAX; a
  * pooled count above it uses the moments at BMND_MOMENT_NMAX. */
 #define BMND_MOMENT_NMAX 4096
@@ -92,7 +94,17 @@ enum { BMND_DOMAIN_COEFFICIENT = 0, BMND_DOMAIN_WINDOWED = 1 };
  *   match_metric SSD (App. A); match_policy fixed; match_t 3.0; beta_s 0.1
  *     and kappa_s 1.0 (Sec. 9.4); ht_rule hard (App. A); weight_domain
  *     coefficient (App. A); cov_planes 0 (the diagonal variance model; App. A
- *     lists 4 exact covariance planes).
+ *     lists 4 exact covariance planes); spatial_transform DCT (App. A lists
+ *     bior1.5 for the hard-threshold stage).
+ *
+ * spatial_transform = BMND_SPATIAL_BIOR15 transforms the patch axes of stage
+ * 1 by the biorthogonal spline wavelet bior1.5 (App. A, "Transforms" row):
+ * periodic extension, full depth on every patch axis, whose sides must be
+ * powers of two (BMND_EINVAL otherwise); coefficient variances are
+ * sum_i T_ki^2 m_v(u_i) with the non-orthonormal analysis T (Lemma
+ * "Covariance propagation"), the inverse is its synthesis matrix, and the
+ * windowed weighting models use that synthesis.  Stage 2 keeps the DCT.  It
+ * runs in the generic kernels.
  *
  * cov_planes = k_ex > 0 (scaled-Poisson noise only, at most 32) gives the
  * coefficients of the first k_ex planes of the group-axis transform, in both
@@ -131,10 +143,15 @@ enum { BMND_DOMAIN_COEFFICIENT = 0, BMND_DOMAIN_WINDOWED = 1 };
  *                 nearest integer, plus beta_s r-bar^kappa_s;
  *   standardized: candidates ranked and accepted by Z_m < t of Eq.
  *                 (standardized-distance), n_i = r_i + c_i rounded.
- * Stage 2 keeps plain SSD on the pilot with tau_wie (App. B).  Scores and
- * thresholds are formed in float32 with every operation rounded once (the
- * logarithm by the artanh series), so that equal inputs give equal groups
- * on every run. */
+ * Stage 2 keeps plain SSD on the pilot with tau_wie (App. B).
+ *
+ * Decisions.  Every ranking and acceptance comparison of matching, and the
+ * hard threshold |Y_k| > lambda sigma_k, is the comparison of the
+ * double-precision definition: scores are screened in float32 with an error
+ * bound, and what the bound cannot separate is re-evaluated exactly (integer
+ * sums for dyadic data and for the Poisson distances on count data) or in
+ * double precision; groups and kept coefficients therefore differ from those
+ * of the definition only at ties in real arithmetic. */
 typedef struct {
     double lambda_ht;
     double gamma_ht;
@@ -159,6 +176,7 @@ typedef struct {
     int ht_rule;
     int weight_domain;
     int cov_planes;
+    int spatial_transform;
 } bmnd_params;
 
 void bmnd_default_params(bmnd_params *p);

@@ -29,6 +29,7 @@ MATCH_POLICIES = {"fixed": 0, "reference_finite_count": 1, "candidate_standardiz
 MOMENT_NMAX = 4096
 HT_RULES = {"hard": 0, "soft": 1}
 WEIGHT_DOMAINS = {"coefficient": 0, "windowed_synthesis": 1}
+SPATIAL_TRANSFORMS = {"dct": 0, "bior1.5": 1}
 
 
 class BmndError(RuntimeError):
@@ -51,7 +52,8 @@ class bmnd_params(ctypes.Structure):
                 ("weight_model", ctypes.c_int), ("weight_scope", ctypes.c_int),
                 ("match_metric", ctypes.c_int), ("match_policy", ctypes.c_int),
                 ("match_t", ctypes.c_double), ("beta_s", ctypes.c_double), ("kappa_s", ctypes.c_double),
-                ("ht_rule", ctypes.c_int), ("weight_domain", ctypes.c_int), ("cov_planes", ctypes.c_int)]
+                ("ht_rule", ctypes.c_int), ("weight_domain", ctypes.c_int), ("cov_planes", ctypes.c_int),
+                ("spatial_transform", ctypes.c_int)]
 
 
 class bmnd_job(ctypes.Structure):
@@ -151,7 +153,8 @@ def params(**kw) -> bmnd_params:
     load().bmnd_default_params(ctypes.byref(p))
     maps = dict(schedule=SCHEDULES, power_mode=POWER_MODES, group_transform=GROUP_TRANSFORMS,
                 weight_model=WEIGHT_MODELS, weight_scope=WEIGHT_SCOPES, match_metric=MATCH_METRICS,
-                match_policy=MATCH_POLICIES, ht_rule=HT_RULES, weight_domain=WEIGHT_DOMAINS)
+                match_policy=MATCH_POLICIES, ht_rule=HT_RULES, weight_domain=WEIGHT_DOMAINS,
+                spatial_transform=SPATIAL_TRANSFORMS)
     for k, v in kw.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]

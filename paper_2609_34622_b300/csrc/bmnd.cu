@@ -116,6 +116,62 @@ double kaiser_at(int n, int i, double beta) {
   return bessel_i0(beta * std::sqrt(a > 0 ? a : 0.0)) / bessel_i0(beta);
 }
 
+// bior1.5 analysis matrix T and synthesis matrix U = T^{-1} of a periodic
+// axis of J = 2^m samples (row-major J x J), full depth, coefficients
+// coarsest first, as products of one dense matrix per level:
+// T = W_m ... W_1 and U = V_1 ... V_m, where level s acts on the leading
+// l = J / 2^(s-1) entries (the current approximation) and keeps the details
+// of the finer levels in place.  Level s maps x to [a | d] with
+// a[i] = sum_k lo[k] x[(2i + k) mod l] and d[i] = sum_k hi[k] x[(2i + k) mod l];
+// its synthesis puts slo[k] a[i] + shi[k] d[i] back at (2i + k) mod l.
+// Filters (tap k): analysis lowpass (sqrt 2 / 256) x (3, -3, -22, 22, 128,
+// 128, 22, -22, -3, 3) at k = -4..5 and highpass (1, -1) / sqrt 2 at
+// k = 0, 1; synthesis lowpass (1, 1) / sqrt 2 at k = 0, 1 and highpass
+// shi[k] = (-1)^k lo[1 - k] -- the Cohen-Daubechies-Feauveau biorthogonal
+// spline pair with a box synthesis scaling function and five vanishing
+// moments of the synthesis wavelet (I. Daubechies, "Ten Lectures on
+// Wavelets", 1992, Sec. 8.3).
+void bior15_matrices(int J, std::vector<double> &T, std::vector<double> &U) {
+  static const double taps[10] = {3, -3, -22, 22, 128, 128, 22, -22, -3, 3};
+  auto lo = [&](int k) { return (k < -4 || k > 5) ? 0.0 : taps[k + 4] * std::sqrt(2.0) / 256.0; };
+  auto hi = [&](int k) { return k == 0 ? std::sqrt(0.5) : (k == 1 ? -std::sqrt(0.5) : 0.0); };
+  auto slo = [&](int k) { return (k == 0 || k == 1) ? std::sqrt(0.5) : 0.0; };
+  auto shi = [&](int k) { return ((k & 1) ? -1.0 : 1.0) * lo(1 - k); };
+  auto eye = [&](std::vector<double> &A) {
+    A.assign((size_t)J * J, 0.0);
+    for (int i = 0; i < J; ++i) A[(size_t)i * J + i] = 1.0;
+  };
+  auto mul = [&](const std::vector<double> &A, const std::vector<double> &B) {
+    std::vector<double> C((size_t)J * J, 0.0);
+    for (int r = 0; r < J; ++r)
+      for (int k = 0; k < J; ++k) {
+        const double a = A[(size_t)r * J + k];
+        if (a != 0.0)
+          for (int c = 0; c < J; ++c) C[(size_t)r * J + c] += a * B[(size_t)k * J + c];
+      }
+    return C;
+  };
+  eye(T);
+  eye(U);
+  std::vector<double> W, V;
+  for (int l = J; l >= 2; l /= 2) {
+    eye(W);
+    eye(V);
+    for (int r = 0; r < l; ++r)
+      for (int c = 0; c < l; ++c) W[(size_t)r * J + c] = V[(size_t)r * J + c] = 0.0;
+    for (int i = 0; i < l / 2; ++i)
+      for (int k = -4; k <= 5; ++k) {
+        const int c = ((2 * i + k) % l + l) % l;
+        W[(size_t)i * J + c] += lo(k);
+        W[(size_t)(l / 2 + i) * J + c] += hi(k);
+        V[(size_t)c * J + i] += slo(k);
+        V[(size_t)c * J + l / 2 + i] += shi(k);
+      }
+    T = mul(W, T);
+    U = mul(U, V);
+  }
+}
+
 std::mutex g_const_mu;
 bool g_const_ready[64] = {false};
 
@@ -158,6 +214,14 @@ void fill_tables(std::vector<unsigned char> &img) {
         t[GEN_TOTAL + off + k * J + i] = (float)(v * v);
         t64[off + k * J + i] = v;
       }
+    if (J & (J - 1)) continue;
+    std::vector<double> T, U;
+    bior15_matrices(J, T, U);
+    for (int e = 0; e < J * J; ++e) {
+      t[TAB_BIOR + off + e] = (float)T[e];
+      t[TAB_BIOR + GEN_TOTAL + off + e] = (float)U[e];
+      t64[GEN_TOTAL + off + e] = T[e];
+    }
   }
 }
 
@@ -207,6 +271,7 @@ struct Plan {
   int gtrans;            // group transform (Haar / DCT)
   int metric;            // stage-1 matching distance (BMND_METRIC_*)
   int kex;               // shared-source variance planes (0 = diagonal)
+  int spatial;           // stage-1 spatial transform (BMND_SPATIAL_*)
   int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
@@ -223,9 +288,9 @@ struct Plan {
 // patches (side jL on every axis) of the sizes instantiated with the kernels,
 // with a Haar group transform and the diagonal variance model; 0 selects the
 // generic kernel of the rank.
-int cube_side(int D, const int *j, int gtrans, int kex) {
+int cube_side(int D, const int *j, int gtrans, int kex, int spatial) {
   const int jL = j[D - 1];
-  if (gtrans != BMND_GROUP_HAAR || kex > 0) return 0;
+  if (gtrans != BMND_GROUP_HAAR || kex > 0 || spatial != BMND_SPATIAL_DCT) return 0;
   for (int a = 0; a < D; ++a)
     if (j[a] != jL) return 0;
   if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
@@ -305,7 +370,7 @@ std::string tune_key(int ndim, const int64_t *shape, const int *patch, const int
   }
   snprintf(b, sizeof(b), "g%d,%d s%d m%d t%d sc%d p%d w%d,%d d%d", group_size[0], stages == 2 ? group_size[1] : 0,
            stages, mass_conserve, pr.group_transform, pr.schedule, pr.passes, pr.weight_model, pr.weight_scope,
-           pr.match_metric + 16 * pr.cov_planes);
+           pr.match_metric + 16 * pr.cov_planes + 1024 * pr.spatial_transform);
   k += b;
   return k;
 }
@@ -452,6 +517,12 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   if (pr.ht_rule < 0 || pr.ht_rule > 1) return fail(ctx, BMND_EINVAL, "unknown thresholding rule");
   if (pr.weight_domain < 0 || pr.weight_domain > 1) return fail(ctx, BMND_EINVAL, "unknown weight domain");
   if (pr.cov_planes < 0 || pr.cov_planes > MMAX) return fail(ctx, BMND_EINVAL, "cov_planes not in [0, %d]", MMAX);
+  if (pr.spatial_transform != BMND_SPATIAL_DCT && pr.spatial_transform != BMND_SPATIAL_BIOR15)
+    return fail(ctx, BMND_EINVAL, "unknown spatial transform");
+  if (pr.spatial_transform == BMND_SPATIAL_BIOR15)
+    for (int d = 0; d < ndim; ++d)
+      if (patch[d] & (patch[d] - 1))
+        return fail(ctx, BMND_EINVAL, "bior1.5 needs power-of-two patch sides (patch[%d] = %d)", d, patch[d]);
   if (pr.match_metric < 0 || pr.match_metric > 3) return fail(ctx, BMND_EINVAL, "unknown matching distance");
   if (pr.match_policy < 0 || pr.match_policy > 2) return fail(ctx, BMND_EINVAL, "unknown matching policy");
   if (pr.match_metric != BMND_METRIC_SSD && (!(pr.match_t >= 0) || !(pr.beta_s >= 0) || !(pr.kappa_s > 0)))
@@ -480,19 +551,6 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     g.ell[a] = shape[d] - patch[d];
     g.P *= patch[d];
     for (int i = 0; i < JMAX; ++i) g.kaiser[a][i] = i < patch[d] ? (float)kaiser_at(patch[d], i, pr.kaiser_beta) : 0.f;
-    // windowed synthesis metric factor of axis a (Def. "Windowed synthesis
-    // metrics"): sum_p DCT(q, p)^2 kaiser(p)^2 for the orthonormal DCT-II
-    const int J = patch[d];
-    for (int q = 0; q < JMAX; ++q) {
-      double e = 0.0;
-      if (q < J)
-        for (int i = 0; i < J; ++i) {
-          const double c = dct_entry(J, q, i);
-          const double k = kaiser_at(J, i, pr.kaiser_beta);
-          e += c * c * k * k;
-        }
-      g.wsyn[a][q] = (float)e;
-    }
   }
   {
     int64_t s = 1;
@@ -507,6 +565,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.gtrans = pr.group_transform;
   pl.metric = pr.match_metric;
   pl.kex = pr.cov_planes;
+  pl.spatial = pr.spatial_transform;
   g.dct64 = ctx->tab64;
   g.diag = ctx->diag;
   if (pl.metric != BMND_METRIC_SSD) {
@@ -515,7 +574,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     g.mom = ctx->mom[pl.metric];
     g.pfix = ctx->pfix[pl.metric];
   }
-  if (cube_side(D, g.j, pl.gtrans, pl.kex) && g.P <= 32) {
+  if (cube_side(D, g.j, pl.gtrans, pl.kex, pl.spatial) && g.P <= 32) {
     // specialized kernels with members in registers: unpadded rows, odd
     // member stride (whole members and whole entry columns are read)
     g.LS = g.jL;
@@ -724,8 +783,35 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
   // Poisson distances on count data: exact integer sums, so a float key is
   // off by its own rounding only (the standardized one by a few roundings)
   if (g.metric != BMND_METRIC_SSD) g.ku = (float)std::ldexp(1.0, g.policy == BMND_POLICY_STANDARDIZED ? -20 : -22);
+  // spatial transform: bior1.5 in stage 1 when selected (App. A), else the
+  // DCT.  ht_t2 bounds the squared entries of the spatial transform (2 / J
+  // per DCT axis); the dense non-orthonormal bior1.5 path gets a 4x wider
+  // FP32 hard-threshold band.  Windowed synthesis metric factor of axis a
+  // (Def. "Windowed synthesis metrics"): sum_p S(p, q)^2 kaiser(p)^2 over
+  // the synthesis S of the axis (S = DCT^T).
+  g.spatial = stage == 1 && pr.spatial_transform == BMND_SPATIAL_BIOR15 ? 1 : 0;
+  g.sp64 = g.dct64 ? g.dct64 + (g.spatial ? GEN_TOTAL : 0) : nullptr;
+  g.ht_band = g.spatial ? 4.f : 1.f;
   double t2 = 1.0;
-  for (int a = 0; a < g.D; ++a) t2 *= g.j[a] >= 2 ? 2.0 / g.j[a] : 1.0;
+  for (int a = 0; a < g.D; ++a) {
+    const int J = g.j[a];
+    std::vector<double> T, U;
+    if (g.spatial) bior15_matrices(J, T, U);
+    double mx = 0.0;
+    for (int q = 0; q < JMAX; ++q) {
+      double e = 0.0;
+      if (q < J)
+        for (int i = 0; i < J; ++i) {
+          const double c = g.spatial ? U[(size_t)i * J + q] : dct_entry(J, q, i);
+          const double k = kaiser_at(J, i, pr.kaiser_beta);
+          e += c * c * k * k;
+          const double f = g.spatial ? T[(size_t)q * J + i] : c;
+          mx = std::max(mx, f * f);
+        }
+      g.wsyn[a][q] = (float)e;
+    }
+    t2 *= g.spatial ? mx : (J >= 2 ? 2.0 / J : 1.0);
+  }
   g.ht_t2 = (float)t2;
   int ex = 0;
   const bool pow2 = g.poisson && std::frexp(nz.poisson_scale, &ex) == 0.5;
@@ -734,7 +820,7 @@ void fill_stage(DGeom &g, int stage, int M, const bmnd_noise &nz, const bmnd_par
 }
 
 // Patch side of the specialized stage kernel for a plan (0: generic).
-int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans, pl.kex); }
+int kernel_jl(const Plan &pl) { return cube_side(pl.D, pl.g.j, pl.gtrans, pl.kex, pl.spatial); }
 
 // Kernel stage of a plan's stage s: 3 selects the stage-1 kernels with a
 // Poisson matching distance.
@@ -1048,6 +1134,7 @@ void bmnd_default_params(bmnd_params *p) {
   p->ht_rule = BMND_HT_HARD;
   p->weight_domain = BMND_DOMAIN_COEFFICIENT;
   p->cov_planes = 0;
+  p->spatial_transform = BMND_SPATIAL_DCT;
 }
 
 bmnd_status bmnd_create(bmnd_ctx **out, int device, size_t scratch_budget_bytes) {

@@ -534,13 +534,17 @@ __device__ __forceinline__ void dct_patch(float (&x)[ipow(JC, D)]) {
   }
 }
 
-// Shared-memory matrices of one patch axis: [forward | transposed | squared].
+// Shared-memory matrices of one patch axis: [forward F | synthesis S |
+// squared F.^2 | F^T]; mode 0..3 selects one (S = F^T for the DCT).
 __device__ __forceinline__ const float *axis_matrix(const float *mats, const int *moff, int a, int J, int mode) {
-  return mats + moff[a] + (mode == 0 ? 0 : (mode == 1 ? J * J : 2 * J * J));
+  return mats + moff[a] + mode * J * J;
 }
 
-// Separable group transform T = (group axis) (x) DCT_j0 (x) ... on a warp's
-// shared group buffer of n members.  mode 0: T, 1: T^T = T^{-1}, 2: T.^2.
+// Separable group transform T = (group axis) (x) F_j0 (x) ... on a warp's
+// shared group buffer of n members, F the orthonormal DCT or bior1.5
+// (g.spatial).  mode 0: T, 1: the synthesis T^{-1} (T^T for the DCT),
+// 2: T.^2.  The DCT runs as register butterflies on power-of-two axes;
+// bior1.5 and other lengths as dense products with the shared matrices.
 template <int D, int JC>
 __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
                             const float *mats, const int *moff, const float *tab) {
@@ -578,7 +582,7 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
     const float *M = axis_matrix(mats, moff, a, ja, mode);
     const int nl = n * per, st = bs[a];
     const bool vec4 = a == D - 1 && (LS & 3) == 0;
-    if ((ja & (ja - 1)) == 0) {
+    if ((ja & (ja - 1)) == 0 && !g.spatial) {
       // power-of-two length: register butterflies, one lane per line
 #pragma unroll 1
       for (int l = lane; l < nl; l += 32) {
@@ -595,7 +599,12 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
       continue;
     }
     switch (ja) {
+      case 2: xform_lines<2>(buf, nl, base_of, st, M, lane); break;
       case 3: xform_lines<3>(buf, nl, base_of, st, M, lane); break;
+      case 4: xform_lines<4>(buf, nl, base_of, st, M, lane); break;
+      case 8: xform_lines<8>(buf, nl, base_of, st, M, lane); break;
+      case 16: xform_lines<16>(buf, nl, base_of, st, M, lane); break;
+      case 32: xform_lines<32>(buf, nl, base_of, st, M, lane); break;
       case 5: xform_lines<5>(buf, nl, base_of, st, M, lane); break;
       case 6: xform_lines<6>(buf, nl, base_of, st, M, lane); break;
       case 7: xform_lines<7>(buf, nl, base_of, st, M, lane); break;
@@ -1642,7 +1651,7 @@ __device__ __noinline__ bool ht_keep64(const DGeom &g, int n, int l, int q, cons
     double f = 1.0;
     for (int d = D - 1; d >= 0; --d) {
       const int J = g.j[d];
-      f *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + p % J);
+      f *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + p % J);
       p /= J;
     }
     return f;
@@ -1657,12 +1666,14 @@ __device__ __noinline__ bool ht_keep64(const DGeom &g, int n, int l, int q, cons
       const double y = Sg[mem[m] + vreg[p]];
       ys = fma(f, y, ys);
       if (g.poisson) vs = fma(f * f, g.s_p64 * (y > 0.0 ? y : 0.0), vs);
+      else if (g.spatial) vs = fma(f * f, g.var64, vs);
     }
     Y = fma(a, ys, Y);
     V = fma(a * a, vs, V);
   }
   if (!g.poisson) {
-    V = g.var64;
+    // white noise: sigma^2 (orthonormal) or sigma^2 sum_i T_ki^2 (bior1.5)
+    if (!g.spatial) V = g.var64;
   } else if (l < g.kex) {
     for (int m = 0; m < n; ++m) {
       const double am = group_axis_entry64(g, n, l, m);
@@ -1686,8 +1697,8 @@ __device__ __noinline__ bool ht_keep64(const DGeom &g, int n, int l, int q, cons
             const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
             r /= ext[d];
             const int J = g.j[d];
-            f1 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd);
-            f2 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd - dl[d]);
+            f1 *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + pd);
+            f2 *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + pd - dl[d]);
             off += pd * g.rst[d];
           }
           const double y = Sg[off];
@@ -1730,12 +1741,13 @@ __device__ __noinline__ bool ht_keep64_warp(const DGeom &g, int n, int l, int q,
     double f = a;
     for (int d = D - 1, r = p; d >= 0; --d) {
       const int J = g.j[d];
-      f *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + r % J);
+      f *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + r % J);
       r /= J;
     }
     const double y = Sg[mem[m] + vreg[p]];
     Y = fma(f, y, Y);
     if (g.poisson) V = fma(f * f, g.s_p64 * (y > 0.0 ? y : 0.0), V);
+    else if (g.spatial) V = fma(f * f, g.var64, V);
   }
   if (g.poisson && l < g.kex) {
     // shared-source terms, member pairs over the lanes
@@ -1758,8 +1770,8 @@ __device__ __noinline__ bool ht_keep64_warp(const DGeom &g, int n, int l, int q,
           const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
           r /= ext[d];
           const int J = g.j[d];
-          f1 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd);
-          f2 *= __ldg(g.dct64 + gen_off(J) + qc[d] * J + pd - dl[d]);
+          f1 *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + pd);
+          f2 *= __ldg(g.sp64 + gen_off(J) + qc[d] * J + pd - dl[d]);
           off += pd * g.rst[d];
         }
         const double y = Sg[off];
@@ -1770,7 +1782,9 @@ __device__ __noinline__ bool ht_keep64_warp(const DGeom &g, int n, int l, int q,
   }
   Y = warp_sum_d(Y);
   V = warp_sum_d(V);
-  if (!g.poisson) V = g.var64;
+  // white noise: sigma^2 for an orthonormal transform, sigma^2 sum_i T_ki^2
+  // for bior1.5 (Lemma "Covariance propagation")
+  if (!g.poisson && !g.spatial) V = g.var64;
   const double t = g.lambda64 * sqrt(V > 0.0 ? V : 0.0);
   return fabs(Y) - t > 1e-12 * t;
 }
@@ -1930,7 +1944,11 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
   //   stage 2: T^2 m_v (Poisson) | T gamma_g | gains, weights | T y_g | G Y, T^T C
   const float lam2 = g.lambda * g.lambda;
   float *syn = stage2 ? bufA : bufB;
-  const int first = g.poisson ? 0 : 1;
+  // coefficient variances by the squared transform: Poisson noise, and white
+  // noise under the non-orthonormal bior1.5 (sigma^2 sum_i T_ki^2); else
+  // sigma^2 itself (Cor. "White-noise transform variance")
+  const bool varT = g.poisson || g.spatial;
+  const int first = varT ? 0 : 1;
   const int last = stage2 ? 4 : 3;
   // stage-1 hard threshold: group norm and variance-map total for the FP32
   // error band of the decision (ht_decide32)
@@ -1947,7 +1965,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         const float gv = Sg[mem[m] + vreg[v]];
         const int a = m * MS + vbuf[v];
         bufB[a] = gv;
-        const float mv = g.s_p * fmaxf(gv, 0.f);
+        const float mv = g.poisson ? g.s_p * fmaxf(gv, 0.f) : g.var_g;
         bufA[a] = mv;
         n2 = fmaf(gv, gv, n2);
         sm += mv;
@@ -1956,7 +1974,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       tb = bufA;
       tmode = 2;
     } else if (ph == 1) {
-      if (!g.poisson) {
+      if (!varT) {
         BMND_FOR_ENTRIES({
           const float gv = Sg[mem[m] + vreg[v]];
           bufB[m * MS + vbuf[v]] = gv;
@@ -1976,8 +1994,8 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         n2 = warp_sum(n2);
         sm = warp_sum(sm);
         const float a2 = n == 1 ? 1.f : (g.gtrans == 0 ? 0.5f : 2.f / (float)n);
-        eX = 1.9073e-6f * sqrtf(n2);
-        eS0 = 9.537e-7f * sm * a2 * g.ht_t2 * (g.kex > 0 ? 16.f : 1.f);
+        eX = 1.9073e-6f * g.ht_band * sqrtf(n2);
+        eS0 = 9.537e-7f * g.ht_band * sm * a2 * g.ht_t2 * (g.kex > 0 ? 16.f : 1.f);
       }
       // undecided hard-threshold coefficients of this lane, by visit number
       // (entries lane + 32 k); kept until settled below
@@ -1986,7 +2004,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       // ---- shrinkage; per-coefficient weight terms into bufA ----
       BMND_FOR_ENTRIES({
         const int a = m * MS + vbuf[v];
-        const float s2 = g.poisson ? bufA[a] : g.var_g;
+        const float s2 = varT ? bufA[a] : g.var_g;
         const float X = bufB[a];
         float wterm;
         if (!stage2 && g.soft) {
@@ -2565,12 +2583,17 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         int o = 0;
         for (int a = 0; a < D; ++a) {
           const int J = g.j[a];
-          const float *F = tab + gen_off(J), *Q = tab + GEN_TOTAL + gen_off(J);
+          // [F | S | F.^2 | F^T]: the DCT with S = F^T, or bior1.5 with its
+          // synthesis matrix
+          const float *F = tab + (g.spatial ? TAB_BIOR : 0) + gen_off(J);
+          const float *S = tab + TAB_BIOR + GEN_TOTAL + gen_off(J);
           for (int e = threadIdx.x; e < J * J; e += blockDim.x) {
             int k = e / J, i = e - k * J;
-            L.mats[o + e] = __ldg(F + e);
-            L.mats[o + J * J + e] = __ldg(F + i * J + k);
-            L.mats[o + 2 * J * J + e] = __ldg(Q + e);
+            const float f = __ldg(F + e), ft = __ldg(F + i * J + k);
+            L.mats[o + e] = f;
+            L.mats[o + J * J + e] = g.spatial ? __ldg(S + e) : ft;
+            L.mats[o + 2 * J * J + e] = f * f;
+            L.mats[o + 3 * J * J + e] = ft;
           }
           o += mat_block(J);
         }

@@ -48,10 +48,12 @@ __host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean, in
   return (5 * MMAX * 4 + ((nbuf * M * MS + 1) & ~1) * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
 }
 
-// Floats reserved in shared memory for the three J x J matrices of one patch
-// axis, rounded up to 4 so that every block starts on a 16-byte boundary (the
-// line transforms read rows of sizes divisible by 4 as float4).
-__host__ __device__ constexpr int mat_block(int J) { return (3 * J * J + 3) & ~3; }
+// Floats reserved in shared memory for the four J x J matrices of one patch
+// axis -- forward F, synthesis S (F^T for the orthonormal DCT), the entrywise
+// square of F and F^T -- rounded up to 4 so that every block starts on a
+// 16-byte boundary (the line transforms read rows of sizes divisible by 4 as
+// float4).
+__host__ __device__ constexpr int mat_block(int J) { return (4 * J * J + 3) & ~3; }
 
 // Per-array geometry of one stage, with singleton axes removed.
 struct DGeom {
@@ -119,7 +121,14 @@ struct DGeom {
   const double *dct64;
   float ku, ht_t2;
   int exact_ok;
-  int pad_dd;
+  // spatial transform of this stage: 0 the orthonormal DCT-II, 1 bior1.5
+  // (stage 1 only, App. A) from dense shared-memory matrices; sp64: its
+  // double forward matrices (gen_off layout); ht_band: widening of the FP32
+  // hard-threshold error band for the dense non-orthonormal transform
+  int spatial;
+  const double *sp64;
+  float ht_band;
+  int pad_sp;
   // Poisson distances on count data in exact integer arithmetic: pfix
   // holds fixed-point tables (units 2^-32) of the per-entry contributions
   // and the finite-count moments (layout at PFIX_*), and count_tol the
@@ -133,10 +142,13 @@ struct DGeom {
 };
 
 // Layout of the transform tables in device memory: the float DCT table
-// (2 GEN_TOTAL floats, see above) and at TAB64_OFFSET bytes the double
-// matrices (GEN_TOTAL doubles, same offsets).
-constexpr int TAB64_OFFSET = ((2 * GEN_TOTAL * 4) + 255) & ~255;
-constexpr int TAB_BYTES = TAB64_OFFSET + GEN_TOTAL * 8;
+// (2 GEN_TOTAL floats, see above), at float TAB_BIOR the bior1.5 analysis
+// matrices and at TAB_BIOR + GEN_TOTAL their synthesis matrices (power-of-two
+// sizes, same offsets), and at TAB64_OFFSET bytes the double DCT matrices
+// followed by the double bior1.5 analysis matrices (GEN_TOTAL doubles each).
+constexpr int TAB_BIOR = 2 * GEN_TOTAL;
+constexpr int TAB64_OFFSET = ((4 * GEN_TOTAL * 4) + 255) & ~255;
+constexpr int TAB_BYTES = TAB64_OFFSET + 2 * GEN_TOTAL * 8;
 
 constexpr int MOMENT_NMAX = 4096;
 
