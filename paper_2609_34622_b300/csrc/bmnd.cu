@@ -286,11 +286,16 @@ struct Plan {
 
 // Patch side of the specialized stage kernels for a shape: they take cubic
 // patches (side jL on every axis) of the sizes instantiated with the kernels,
-// with a Haar group transform and the diagonal variance model; 0 selects the
+// with a Haar group transform and the DCT spatial transform; 0 selects the
 // generic kernel of the rank.
 int cube_side(int D, const int *j, int gtrans, int kex, int spatial) {
   const int jL = j[D - 1];
-  if (gtrans != BMND_GROUP_HAAR || kex > 0 || spatial != BMND_SPATIAL_DCT) return 0;
+  if (gtrans != BMND_GROUP_HAAR || spatial != BMND_SPATIAL_DCT) return 0;
+  // the register filter (patches of <= 32 entries) takes at most 4
+  // shared-source planes
+  int P = 1;
+  for (int a = 0; a < D; ++a) P *= j[a];
+  if (kex > 4 && P <= 32) return 0;
   for (int a = 0; a < D; ++a)
     if (j[a] != jL) return 0;
   if ((D == 1 && (jL == 32 || jL == 16)) || (D == 2 && (jL == 8 || jL == 4)) || (D == 3 && jL == 4)) return jL;
@@ -304,7 +309,7 @@ int stage_smem(const DGeom &g, int M, int nreg, bool cached = false) {
   else if (g.lean) nreg = 1;  // only the matching guide is staged
   size_t b = al16(sizeof(DJob));
   b = al16(b + (size_t)g.P * 12 + (size_t)g.rows * 4 + KMAXD * 4 + (g.fp ? (size_t)g.P * 4 : 0) +
-           (size_t)g.fp * 4);
+           (size_t)g.fp * 4 + (g.kex ? (size_t)g.P * 4 : 0));
   b = al16(b + (g.lean ? (size_t)g.P * 8 : 0));
   size_t mats = 0;
   for (int a = 0; a < g.D; ++a) mats += (size_t)mat_block(g.j[a]) * 4;
@@ -566,6 +571,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.metric = pr.match_metric;
   pl.kex = pr.cov_planes;
   pl.spatial = pr.spatial_transform;
+  g.kex = pr.cov_planes;  // the shared-memory plan holds the coordinate table
   g.dct64 = ctx->tab64;
   g.diag = ctx->diag;
   if (pl.metric != BMND_METRIC_SSD) {

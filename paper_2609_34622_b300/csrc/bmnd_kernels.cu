@@ -1542,65 +1542,216 @@ __device__ __forceinline__ float group_axis_entry(const DGeom &g, const float *t
   return m < r * b + b / 2 ? v : -v;
 }
 
-// Def. "Partial shared-source Poisson variance model": for the leading kex
-// group-axis planes l, the variance of coefficient (l, q) sums the effective
-// weights of entries that share a source location (Def. "Effective transform
-// weights").  bufA holds the diagonal model sum_i T_ki^2 m_v(u_i); with
-// T_(l,q),(m,p) = A0[l][m] F_q(p), the shared locations add, for every
-// member pair m < m2 whose patches overlap (origin offset delta = o_m2 - o_m),
-//   2 A0[l][m] A0[l][m2] sum_p F_q(p) F_q(p - delta) m_v(o_m + p)
-// over the entries p of m that are entries p - delta of m2.  Lanes own
-// spatial coefficients q, so each updates its own column of bufA.
-__device__ __noinline__ void shared_source_planes(const DGeom &g, int n, int lane, const int *__restrict__ mem,
-                                                  const int *__restrict__ vbuf, const float *__restrict__ Sg,
-                                                  float *__restrict__ bufA, int MS, const float *mats,
-                                                  const int *moff, const float *tab) {
-  const int D = g.D;
+// Def. "Partial shared-source Poisson variance model" for the leading kex
+// group-axis planes, in per-location form.  The diagonal model sum_i T_ki^2
+// m_v(u_i) (T_(l,q),(m,p) = A0[l][m] F_q(p)) counts every entry's own weight
+// once; the exact variance sums over the distinct source locations u the
+// squared effective weight t_ku = sum of the weights a_i of the entries taken
+// from u (Def. "Effective transform weights").  The two differ only at
+// locations covered by two or more members, so each such u adds
+// m_v(u) (t_ku^2 - sum_i a_i^2).  One pass over the group: overlap masks of
+// the members by ballot; per member m, its entries (lanes) covered by a
+// later overlapping member and by no earlier one are the shared locations
+// that m owns; each is then processed by the whole warp with lanes over the
+// spatial coefficients q (NS per lane: q = 32 s0 + lane + 32 h, h < NS),
+// reading the transposed analysis factors F^T (block 3 of the shared axis
+// matrices).  With the Haar group transform the planes l0..l0+3 < 4 are
+// signed sums of the four member quarters, so a covering entry costs one
+// weight F_q and two accumulations; otherwise the group-axis entries of the
+// four planes come from the member lanes.  corr[h][k] receives the
+// correction of plane l0 + k (planes >= min(kex, n) stay 0).  vcrd:
+// patch-entry coordinates, 5 bits per axis.  Returns the largest number of
+// members covering one location (for the FP32 error band).
+template <int D, int NS>
+__device__ __noinline__ int shared_source_pass(const DGeom &g, int n, int lane, int s0, int l0,
+                                               const int *__restrict__ mem, const int *__restrict__ vreg,
+                                               const int *__restrict__ vcrd, const float *__restrict__ Sg,
+                                               const float *mats, const int *moff, const float *tab,
+                                               float (&corr)[NS][4]) {
+  const unsigned FULL = 0xffffffffu;
   const int L = min(g.kex, n);
-  for (int q = lane; q < g.P; q += 32) {
-    int qc[KMAXD];
-    {
-      int r = q;
-      for (int d = D - 1; d >= 0; --d) {
-        qc[d] = r % g.j[d];
-        r /= g.j[d];
-      }
+#pragma unroll
+  for (int h = 0; h < NS; ++h)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) corr[h][k] = 0.f;
+  if (n < 2 || l0 >= L) return 1;
+  int J[D];
+  const float *FT[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    J[d] = g.j[d];
+    FT[d] = mats + moff[d] + 3 * J[d] * J[d];
+  }
+  // lane m: region coordinates of member m and its overlap mask
+  int cm[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) cm[d] = lane < n ? (mem[lane] / g.rst[d]) % g.RG[d] : 0;
+  unsigned ov = 0u;
+  for (int m = 0; m < n; ++m) {
+    // every lane takes part in every shuffle (none under a condition)
+    bool o = lane < n && lane != m;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int c = __shfl_sync(FULL, cm[d], m);
+      o = o && abs(cm[d] - c) < J[d];
     }
-    for (int m = 0; m < n; ++m) {
-      int cm[KMAXD];
-      for (int d = 0; d < D; ++d) cm[d] = (mem[m] / g.rst[d]) % g.RG[d];
-      for (int m2 = m + 1; m2 < n; ++m2) {
-        int dl[KMAXD], ext[KMAXD], cnt = 1;
-        bool ov = true;
+    const unsigned b = __ballot_sync(FULL, o);
+    if (lane == m) ov = b;
+  }
+  if (__ballot_sync(FULL, ov != 0u) == 0u) return 1;
+  const bool haar = g.gtrans == 0 && L <= 4;
+  // member quarter of the Haar planes: m >> (log2 n - 2), n = 2: 2 m
+  const int tn = 31 - __clz(n);
+  const int qshl = tn >= 2 ? 0 : 2 - tn, qshr = tn >= 2 ? tn - 2 : 0;
+  const float r1 = rsqrtf((float)n), r2 = sqrtf(2.f / (float)n);
+  // group-axis entries of planes l0..l0+3 held by the member lanes
+  float a0[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a0[k] = (!haar && lane < n && l0 + k < L) ? group_axis_entry(g, tab, n, l0 + k, lane) : 0.f;
+  // this lane's coefficients and their axis coordinates
+  int qc[NS][D];
+#pragma unroll
+  for (int h = 0; h < NS; ++h) {
+    const int q = 32 * (s0 + h) + lane;
+    const int c = q < g.P ? vcrd[q] : 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) qc[h][d] = (c >> (5 * d)) & 31;
+  }
+  int cmax = 1;
+  for (int m = 0; m < n; ++m) {
+    const unsigned ovm = __shfl_sync(FULL, ov, m);
+    if (ovm == 0u) continue;
+    int cmm[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) cmm[d] = __shfl_sync(FULL, cm[d], m);
+    const unsigned earlier = (1u << m) - 1u;
+    for (int p0 = 0; p0 < g.P; p0 += 32) {
+      const int p = p0 + lane;
+      const int pc = p < g.P ? vcrd[p] : 0;
+      int ud[D];  // location coordinates of this lane's entry of m
+#pragma unroll
+      for (int d = 0; d < D; ++d) ud[d] = ((pc >> (5 * d)) & 31) + cmm[d];
+      unsigned cover = 0u;
+      for (unsigned r = ovm; r; r &= r - 1u) {
+        const int m2 = __ffs(r) - 1;
+        bool in = p < g.P;
+#pragma unroll
         for (int d = 0; d < D; ++d) {
-          dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - cm[d];
-          ext[d] = g.j[d] - abs(dl[d]);
-          ov = ov && ext[d] > 0;
-          cnt *= ext[d] > 0 ? ext[d] : 0;
+          const int c2 = __shfl_sync(FULL, cm[d], m2);
+          in = in && (unsigned)(ud[d] - c2) < (unsigned)J[d];
         }
-        if (!ov) continue;
-        float X = 0.f;
-        for (int e = 0; e < cnt; ++e) {
-          int r = e, off = mem[m];
-          float f1 = 1.f, f2 = 1.f;
-          for (int d = D - 1; d >= 0; --d) {
-            const int pd = (dl[d] > 0 ? dl[d] : 0) + r % ext[d];
-            r /= ext[d];
-            const int J = g.j[d];
-            const float *F = mats + moff[d];
-            f1 *= F[qc[d] * J + pd];
-            f2 *= F[qc[d] * J + pd - dl[d]];
-            off += pd * g.rst[d];
+        if (in) cover |= 1u << m2;
+      }
+      unsigned todo = __ballot_sync(FULL, cover != 0u && (cover & earlier) == 0u);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const unsigned cv = __shfl_sync(FULL, cover, src) | (1u << m);
+        int us[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) us[d] = __shfl_sync(FULL, ud[d], src);
+        cmax = max(cmax, __popc(cv));
+        const float mv = g.s_p * fmaxf(Sg[mem[m] + vreg[p0 + src]], 0.f);
+        float Q[NS][4], R[NS][4];
+#pragma unroll
+        for (int h = 0; h < NS; ++h)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) Q[h][k] = R[h][k] = 0.f;
+        for (unsigned r = cv; r; r &= r - 1u) {
+          const int m2 = __ffs(r) - 1;
+          float f[NS];
+#pragma unroll
+          for (int h = 0; h < NS; ++h) f[h] = 1.f;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const float *row = FT[d] + (us[d] - __shfl_sync(FULL, cm[d], m2)) * J[d];
+#pragma unroll
+            for (int h = 0; h < NS; ++h) f[h] *= row[qc[h][d]];
           }
-          X = fmaf(f1 * f2, g.s_p * fmaxf(Sg[off], 0.f), X);
+          if (haar) {
+            switch ((m2 << qshl) >> qshr) {
+#define BMND_Q(K)                                                       \
+  case K:                                                               \
+    _Pragma("unroll") for (int h = 0; h < NS; ++h) {                    \
+      Q[h][K] += f[h];                                                  \
+      R[h][K] = fmaf(f[h], f[h], R[h][K]);                              \
+    }                                                                   \
+    break;
+              BMND_Q(0) BMND_Q(1) BMND_Q(2) BMND_Q(3)
+#undef BMND_Q
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float a = __shfl_sync(FULL, a0[k], m2);
+#pragma unroll
+              for (int h = 0; h < NS; ++h) {
+                const float x = a * f[h];
+                Q[h][k] += x;
+                R[h][k] = fmaf(x, x, R[h][k]);
+              }
+            }
+          }
         }
-        for (int l = 0; l < L; ++l) {
-          const float w = group_axis_entry(g, tab, n, l, m) * group_axis_entry(g, tab, n, l, m2);
-          if (w != 0.f) bufA[l * MS + vbuf[q]] += 2.f * w * X;
+#pragma unroll
+        for (int h = 0; h < NS; ++h) {
+          float t[4], sq[4];
+          if (haar) {
+            // planes 0..3 of the Haar rows: all members, the two halves,
+            // the quarters of the first and of the second half
+            t[0] = (Q[h][0] + Q[h][1] + Q[h][2] + Q[h][3]) * r1;
+            t[1] = (Q[h][0] + Q[h][1] - Q[h][2] - Q[h][3]) * r1;
+            t[2] = (Q[h][0] - Q[h][1]) * r2;
+            t[3] = (Q[h][2] - Q[h][3]) * r2;
+            sq[0] = sq[1] = (R[h][0] + R[h][1] + R[h][2] + R[h][3]) * (r1 * r1);
+            sq[2] = (R[h][0] + R[h][1]) * (r2 * r2);
+            sq[3] = (R[h][2] + R[h][3]) * (r2 * r2);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              t[k] = Q[h][k];
+              sq[k] = R[h][k];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) corr[h][k] = fmaf(mv, fmaf(t[k], t[k], -sq[k]), corr[h][k]);
         }
       }
     }
   }
+#pragma unroll
+  for (int h = 0; h < NS; ++h)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (l0 + k >= L) corr[h][k] = 0.f;
+  return cmax;
+}
+
+// The shared-source corrections of every coefficient of the leading planes
+// added to the variances in bufA (plane rows, buffer offsets vbuf), two
+// coefficients per lane and four planes per pass.
+template <int D>
+__device__ __forceinline__ int shared_source_planes(const DGeom &g, int n, int lane, const int *__restrict__ mem,
+                                                    const int *__restrict__ vreg, const int *__restrict__ vbuf,
+                                                    const int *__restrict__ vcrd, const float *__restrict__ Sg,
+                                                    float *__restrict__ bufA, int MS, const float *mats,
+                                                    const int *moff, const float *tab) {
+  const int L = min(g.kex, n);
+  int cmax = 1;
+  for (int s0 = 0; 32 * s0 < g.P; s0 += 2)
+    for (int l0 = 0; l0 < L; l0 += 4) {
+      float corr[2][4];
+      cmax = max(cmax, shared_source_pass<D, 2>(g, n, lane, s0, l0, mem, vreg, vcrd, Sg, mats, moff, tab, corr));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = 32 * (s0 + h) + lane;
+        if (q < g.P)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (l0 + k < L) bufA[(l0 + k) * MS + vbuf[q]] += corr[h][k];
+      }
+    }
+  return cmax;
 }
 
 // Entry (l, m) of the group-axis transform in double precision (rows as in
@@ -1929,7 +2080,8 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
                                          const float *__restrict__ Sy, const float *__restrict__ Se,
                                          float *__restrict__ bufA, float *__restrict__ bufB, float *__restrict__ wts,
                                          float *__restrict__ rr_s, const float *mats, const int *moff,
-                                         const float *tab, const float *__restrict__ gy,
+                                         const int *__restrict__ vcrd, const float *tab,
+                                         const float *__restrict__ gy,
                                          const float *__restrict__ ge, const int64_t *__restrict__ gb,
                                          const int64_t *__restrict__ vgl, float *alpha_out,
                                          unsigned long long *diag) {
@@ -1985,17 +2137,22 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       tb = bufB;
       tmode = 0;
     } else if (ph == 2) {
+      int cmax = 0;
       if (g.kex > 0 && g.poisson) {
-        shared_source_planes(g, n, lane, mem, vbuf, Sg, bufA, MS, mats, moff, tab);
+        cmax = shared_source_planes<D>(g, n, lane, mem, vreg, vbuf, vcrd, Sg, bufA, MS, mats, moff, tab);
         __syncwarp();
       }
-      float eX = 0.f, eS0 = 0.f;
+      float eX = 0.f, eS0 = 0.f, eSx = 0.f;
       if (hard) {
         n2 = warp_sum(n2);
         sm = warp_sum(sm);
         const float a2 = n == 1 ? 1.f : (g.gtrans == 0 ? 0.5f : 2.f / (float)n);
         eX = 1.9073e-6f * g.ht_band * sqrtf(n2);
-        eS0 = 9.537e-7f * g.ht_band * sm * a2 * g.ht_t2 * (g.kex > 0 ? 16.f : 1.f);
+        eS0 = 9.537e-7f * g.ht_band * sm * a2 * g.ht_t2;
+        // shared-source planes: FP32 error of the per-location terms
+        // m_v (t^2 - sum a^2), at most a few ulps per covering member of
+        // sum_u m_v sum_i a_i^2 <= a2 max F^2 sum m_v
+        eSx = 4.77e-7f * (float)cmax * sm * a2 * g.ht_t2;
       }
       // undecided hard-threshold coefficients of this lane, by visit number
       // (entries lane + 32 k); kept until settled below
@@ -2017,7 +2174,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
           wterm = att * att * (g.wmodel == 0 ? 1.f : s2);
         } else if (!stage2) {
           // |X| > lambda sigma; undecided in FP32: kept until settled
-          int kp = ht_decide32(X, s2, lam2, eX, eS0);
+          int kp = ht_decide32(X, s2, lam2, eX, m < g.kex ? eS0 + eSx : eS0);
           if (kp < 0) {
             if (visit < 64) undecided |= 1ull << visit;
             else kp = ht_keep64(g, n, m, v, mem, vreg, Sg) ? 1 : 0;  // past 64 visits: at once
@@ -2134,9 +2291,18 @@ __device__ __forceinline__ void col_store(float *buf, int v, const float (&y)[N]
 // then H^T of the kept coefficients back into bufB.
 // Returns the planes whose hard-threshold decision FP32 cannot take
 // (bitmask); they are kept for now and settled by col_ht_settle.
+// Shared-source corrections of the leading group-axis planes (column of
+// the register filter; cx holds planes 0..3, zero beyond k_ex).
+template <int N>
+__device__ __forceinline__ void add_shared_source(float (&S)[N], float4 cx) {
+  const float c[4] = {cx.x, cx.y, cx.z, cx.w};
+#pragma unroll
+  for (int m = 0; m < (N < 4 ? N : 4); ++m) S[m] += c[m];
+}
+
 template <int N, int MS>
 __device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bufA, float *bufB, int v, float lam2,
-                                                       float eX, float eS0) {
+                                                       float eX, float eS0, float4 cx, float eSx) {
   unsigned undecided = 0u;
   float X[N], S[N];
   col_load<N, MS>(X, bufB, v);
@@ -2144,6 +2310,7 @@ __device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bu
   if (g.poisson) {
     col_load<N, MS>(S, bufA, v);
     haar_fwd_levels<N, N, true>(S);
+    add_shared_source<N>(S, cx);
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) S[m] = g.var_g;
@@ -2162,7 +2329,7 @@ __device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bu
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       // |X| > lambda sigma; undecided in FP32: kept until col_ht_settle
-      const int kp = ht_decide32(X[m], S[m], lam2, eX, eS0);
+      const int kp = ht_decide32(X[m], S[m], lam2, eX, m < g.kex ? eS0 + eSx : eS0);
       if (kp < 0) undecided |= 1u << m;
       bufA[m * MS + v] = kp ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
       X[m] = kp ? X[m] : 0.f;
@@ -2194,13 +2361,14 @@ __device__ __forceinline__ void col_ht_drop(float *bufA, float *bufB, int v, uns
 // Stage 2, one column: sigma^2 as above from the pilot, Gamma = H gamma,
 // Wiener gains G into bufB and weight terms into bufA.
 template <int N, int MS>
-__device__ __forceinline__ void col_wiener_gain(const DGeom &g, float *bufA, float *bufB, int v) {
+__device__ __forceinline__ void col_wiener_gain(const DGeom &g, float *bufA, float *bufB, int v, float4 cx) {
   float X[N], S[N];
   col_load<N, MS>(X, bufB, v);
   haar_fwd_levels<N, N, false>(X);
   if (g.poisson) {
     col_load<N, MS>(S, bufA, v);
     haar_fwd_levels<N, N, true>(S);
+    add_shared_source<N>(S, cx);
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) S[m] = g.var_g;
@@ -2287,7 +2455,8 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
                                             float *__restrict__ rr_s, const float *__restrict__ gy,
                                             const float *__restrict__ ge, const int64_t *__restrict__ gb,
                                             const int64_t *__restrict__ vgl, float *alpha_out,
-                                            unsigned long long *diag) {
+                                            unsigned long long *diag, const float *mats, const int *moff,
+                                            const int *__restrict__ vcrd, const float *tab) {
   constexpr int P = ipow(JC, D);
   constexpr int MS = CubeShape<D, JC>::MS;
   static_assert(MS == (P | 1), "register filter layout");
@@ -2329,7 +2498,17 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   // stage-1 hard threshold: group norm and variance-map total (s_P times
   // the positive part of y_g) for the FP32 error band of the decision
   // (ht_decide32), from the gathered values
-  float eX = 0.f, eS0 = 0.f;
+  // partial shared-source variance of the leading planes (at most 4 here):
+  // corrections of this lane's column, added after the squared group-axis
+  // Haar; eSx widens their FP32 band (as in filter_group)
+  float4 cx = make_float4(0.f, 0.f, 0.f, 0.f);
+  int cmax = 0;
+  if (g.kex > 0 && g.poisson) {
+    float corr[1][4];
+    cmax = shared_source_pass<D, 1>(g, n, lane, 0, 0, mem, vreg, vcrd, Sg, mats, moff, tab, corr);
+    cx = make_float4(corr[0][0], corr[0][1], corr[0][2], corr[0][3]);
+  }
+  float eX = 0.f, eS0 = 0.f, eSx = 0.f;
   if (!stage2 && !g.soft) {
     float n2 = 0.f, sm = 0.f;
     for (int e = lane; e < n * P; e += 32) {
@@ -2343,6 +2522,7 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
       sm = warp_sum(sm) * g.s_p;
       const float a2 = n == 1 ? 1.f : 0.5f;
       eS0 = 9.537e-7f * sm * a2 * g.ht_t2;
+      eSx = 4.77e-7f * (float)cmax * sm * a2 * g.ht_t2;
     }
   }
   if (g.poisson && lane < n) {
@@ -2361,12 +2541,12 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
     const float lam2 = g.lambda * g.lambda;
     // one column per lane (P <= 32): the undecided planes of column `lane`
     unsigned undecided = 0u;
-#define BMND_OP(NN) undecided = col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2, eX, eS0)
+#define BMND_OP(NN) undecided = col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2, eX, eS0, cx, eSx)
     BMND_COLUMNS(BMND_OP)
 #undef BMND_OP
     if (__any_sync(0xffffffffu, undecided != 0u)) rf_ht_settle<MS>(g, n, lane, undecided, mem, vreg, Sg, bufA, bufB);
   } else {
-#define BMND_OP(NN) col_wiener_gain<NN, MS>(g, bufA, bufB, v)
+#define BMND_OP(NN) col_wiener_gain<NN, MS>(g, bufA, bufB, v, cx)
     BMND_COLUMNS(BMND_OP)
 #undef BMND_OP
   }
@@ -2440,6 +2620,7 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
 // Shared-memory layout of one job (the host computes the same sizes).
 struct SmemLayout {
   int *vreg, *vbuf, *rowoff, *moff, *fvoff, *fpreg;
+  int *vcrd;     // shared-source variance: patch-entry coordinates, 5 bits per axis
   int64_t *vgl;  // lean: global offset of every patch entry
   float *omega, *mats, *Sg, *Sy, *Se;
   float2 *acc;
@@ -2464,6 +2645,7 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
   s.moff = reinterpret_cast<int *>(p); p += sizeof(int) * KMAXD;
   s.fvoff = reinterpret_cast<int *>(p); p += sizeof(int) * (g.fp ? g.P : 0);
   s.fpreg = reinterpret_cast<int *>(p); p += sizeof(int) * g.fp;
+  s.vcrd = reinterpret_cast<int *>(p); p += sizeof(int) * (g.kex ? g.P : 0);
   p = al16p(p);
   s.vgl = reinterpret_cast<int64_t *>(p); p += sizeof(int64_t) * (g.lean ? g.P : 0);
   p = al16p(p);
@@ -2543,6 +2725,14 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
         L.vreg[v] = ro;
         L.vbuf[v] = (v / g.jL) * g.LS + (v % g.jL);
+        if (g.kex) {
+          int r4 = v, pc = 0;
+          for (int d = D - 1; d >= 0; --d) {
+            pc |= (r4 % g.j[d]) << (5 * d);
+            r4 /= g.j[d];
+          }
+          L.vcrd[v] = pc;
+        }
         if (g.lean) {
           int r3 = v;
           int64_t go = 0;
@@ -2847,10 +3037,12 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             int which;
             if constexpr (SH::rf)
               which = filter_group_rf<D, JL, ST>(g, n, mc2, lane, mem, vreg, omega, Sg, Sy, Se, bufA, bufB, wts, rr_s,
-                                             sj->y, sj->eta, gb, L.vgl, &alpha, g.diag);
+                                                 sj->y, sj->eta, gb, L.vgl, &alpha, g.diag, L.mats, L.moff, L.vcrd,
+                                                 tab);
             else
               which = filter_group<D, JL, ST>(g, n, mc2, lane, mem, vreg, vbuf, omega, Sg, Sy, Se, bufA, bufB, wts,
-                                          rr_s, L.mats, L.moff, tab, sj->y, sj->eta, gb, L.vgl, &alpha, g.diag);
+                                          rr_s, L.mats, L.moff, L.vcrd, tab, sj->y, sj->eta, gb, L.vgl, &alpha,
+                                          g.diag);
             syn = which ? bufA : bufB;
             if (!mc2 && cached && sj->groups) {
               // first sweep of a mass-conserving stage: keep the synthesis
