@@ -654,6 +654,12 @@ def main():
         ctx.bmnd_denoise_batch_host(hyn, hon, cfgs, prm, stream=stream)
         e2e_ms += 1e3 * (time.perf_counter() - t0)
 
+    # double-precision decisions of one step (outside any timing)
+    ctx.bmnd_decision_stats(reset=True)
+    step(ys, outs)
+    torch.cuda.synchronize()
+    decisions = ctx.bmnd_decision_stats(reset=True)
+
     dev_ms, e2e_ms, value, e2e_val = replica_totals(dev_ms, e2e_ms, vox_step, args.steps, world,
                                                     dist if dist else None, dev)
 
@@ -694,6 +700,8 @@ def main():
                 "path": "bmnd_denoise_batch_host: pinned host arrays in and out, copies inside the call, "
                         "host wall clock per call"},
         "gpu_launches": int(launches),
+        "decisions_per_step": dict(decisions, note="taken in double precision (or exact integer arithmetic) "
+                                                   "where the FP32 error bounds could not decide"),
         "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": captured_traffic(args.workload, len(jobs)),
