@@ -554,10 +554,11 @@ def main():
             # the second sweep repeats the filtering (not the matching)
             pass
 
-    # tile autotuning (outside any timing) for single-array workloads: it
-    # times one array alone on the whole GPU, which is not how the arrays of a
-    # batch run (they share the SMs), so a batch keeps the planner's tiles
+    # tile autotuning (outside any timing): a single array is timed alone, a
+    # batch as one batched call (the arrays share the SMs)
     tuned = {}
+    if not args.no_autotune and len(jobs) > 1:
+        tuned["batch"] = ctx.bmnd_autotune_batch(ys, outs, cfgs, prm, stream=stream)
     if not args.no_autotune and len(jobs) == 1:
         for j, y, o in zip(jobs, ys, outs):
             c = j.cfg
@@ -623,19 +624,27 @@ def main():
     kstats = ctx.bmnd_kernel_stats(reset=True)
     ctx.bmnd_set_profiling(False)
 
-    # ---- several arrays: the plain path, one call per array, same timing ----
+    # ---- several arrays: the plain path, one call per array, same timing,
+    # on a context of its own (the planner's tiles for a single array: the
+    # batch's tuned cores are chosen for arrays that share the GPU) ----
     plain_ms = None
     if len(jobs) > 1:
+        pctx = bm.Context(local)
+        for y, o, c in zip(ys, outs, cfgs):  # untimed: scratch and tables of the new context
+            pctx.bmnd_denoise(y, o, c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
+                              c["stages"], c["mass_conserve"], prm, stream=stream)
+        torch.cuda.synchronize()
         evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for k in range(args.steps):
             flush.fill_(float(k))
             evp[k][0].record(stream)
             for y, o, c in zip(ys, outs, cfgs):
-                ctx.bmnd_denoise(y, o, c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
-                                 c["stages"], c["mass_conserve"], prm, stream=stream)
+                pctx.bmnd_denoise(y, o, c["noise"], c["patch"], c["step"], c["search"], c["group_size"],
+                                  c["stages"], c["mass_conserve"], prm, stream=stream)
             evp[k][1].record(stream)
         torch.cuda.synchronize()
         plain_ms = sum(a.elapsed_time(b) for a, b in evp)
+        pctx.close()
 
     # ---- end to end through the C ABI with host buffers: the host-array
     # batch call copies pinned host inputs in, runs both stages, copies the
@@ -692,7 +701,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "voxels_per_step_per_gpu": vox_step, "l2": "flushed (256 MiB) before each step",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "tiles": ("autotuned cores %s (bmnd_autotune, before the warm-up)" % sorted(set(tuned.values()))
+                   "tiles": ("autotuned cores %s (%s, before the warm-up)"
+                             % (sorted(set(tuned.values())),
+                                "bmnd_autotune_batch on the whole batch" if len(jobs) > 1 else "bmnd_autotune")
                              if tuned else "planner")},
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                    "samples": clk["samples"]},
@@ -746,7 +757,7 @@ def main():
     if plain_ms is not None:
         line["plain"] = {"value": vox_step * args.steps / (plain_ms / 1e3), "unit": UNIT,
                          "ms_per_step": plain_ms / args.steps,
-                         "path": "one bmnd_denoise call per array, same stream, same timing"}
+                         "path": "one bmnd_denoise call per array, same stream, same timing, planner tiles"}
         line["config"]["batched"] = "one bmnd_denoise_batch call over all %d arrays per step" % len(jobs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, sdesc = oracle_sample(args.workload, jobs)

@@ -424,6 +424,16 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
                           const int *patch, const int *step, const int *search, const int *group_size, int stages,
                           int mass_conserve, const bmnd_params *params, float *out, void *stream, int *core);
 
+/* Batched autotuning: as bmnd_autotune, but timing bmnd_denoise_batch on the
+ * whole batch `jobs` (where the arrays share the SMs, which a single array
+ * timed alone does not show).  The fastest core is kept for the problem key
+ * of jobs[0] and applies to every job of that key; jobs of other keys keep
+ * their cores.  Every job's out receives its estimate with the chosen
+ * cores; core (host int[jobs[0].ndim], may be NULL) receives jobs[0]'s.
+ * Synchronous.  Errors: those of bmnd_denoise_batch. */
+bmnd_status bmnd_autotune_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs, const bmnd_params *params,
+                                void *stream, int *core);
+
 /* ---- Replayable graphs ----------------------------------------------------
  * The computation of bmnd_denoise_ex (both stages, Sec. 4-5 as for that call)
  * on one array, recorded once as a CUDA graph and replayed: for arrays that

@@ -79,7 +79,7 @@ EXPORTS = ["bmnd_default_params", "bmnd_create", "bmnd_destroy", "bmnd_last_erro
            "bmnd_denoise_ex", "bmnd_stage", "bmnd_schedule", "bmnd_match", "bmnd_denoise_batch",
            "bmnd_set_profiling", "bmnd_kernel_stats", "bmnd_denoise_noalloc", "bmnd_server_create",
            "bmnd_server_submit", "bmnd_server_wait", "bmnd_server_get_stats", "bmnd_server_destroy",
-           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune",
+           "bmnd_graph_create", "bmnd_graph_launch", "bmnd_graph_destroy", "bmnd_autotune", "bmnd_autotune_batch",
            "bmnd_match_moments", "bmnd_coverage", "bmnd_decision_stats", "bmnd_denoise_batch_host",
            "bmnd_plan_info", "bmnd_fp32_fma_peak"]
 KERNEL_KINDS = {"schedule": 0, "stage1": 1, "stage2": 2, "reduce": 3, "mc_sweep": 4, "match": 5}
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.bmnd_match.argtypes = [vp, vp, ctypes.c_int, i64p, bmnd_noise, ip, ip, ip, ctypes.c_int,
                                ctypes.c_int, P(bmnd_params), vp, vp, vp, ctypes.c_int64, i64p, vp]
     lib.bmnd_denoise_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp]
+    lib.bmnd_autotune_batch.argtypes = [vp, ctypes.c_int, P(bmnd_job), P(bmnd_params), vp, ip]
     lib.bmnd_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.bmnd_server_create.argtypes = [P(vp), ctypes.c_int, P(bmnd_server_config)]
     lib.bmnd_server_submit.argtypes = [vp, P(bmnd_job), i64p]
@@ -351,9 +352,7 @@ class Context:
         R = n.value
         return origins[:R], groups[: R * group_max].view(R, group_max), counts[:R]
 
-    def bmnd_denoise_batch(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
-        """ys/outs: lists of CUDA tensors; cfgs: list of dicts with keys noise,
-        patch, step, search, group_size, stages, mass_conserve."""
+    def _device_jobs(self, ys, outs, cfgs):
         n = len(ys)
         arr = (bmnd_job * n)()
         for i, (y, o, c) in enumerate(zip(ys, outs, cfgs)):
@@ -372,11 +371,27 @@ class Context:
             j.group_size[0], j.group_size[1] = int(gs[0]), int(gs[1])
             j.stages = int(c.get("stages", 2))
             j.mass_conserve = int(c.get("mass_conserve", 0))
-        st = self._lib.bmnd_denoise_batch(self.handle, n, arr, ctypes.byref(prm) if prm is not None else None,
+        return arr
+
+    def bmnd_denoise_batch(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
+        """ys/outs: lists of CUDA tensors; cfgs: list of dicts with keys noise,
+        patch, step, search, group_size, stages, mass_conserve."""
+        arr = self._device_jobs(ys, outs, cfgs)
+        st = self._lib.bmnd_denoise_batch(self.handle, len(ys), arr, ctypes.byref(prm) if prm is not None else None,
                                           _stream(stream))
         self._check(st)
         return outs
 
+    def bmnd_autotune_batch(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
+        """Time several tile cores on the whole batch (as bmnd_denoise_batch
+        runs it) and keep the fastest for the first job's problem key;
+        returns the chosen core of the first job."""
+        arr = self._device_jobs(ys, outs, cfgs)
+        core = (ctypes.c_int * ys[0].dim())()
+        st = self._lib.bmnd_autotune_batch(self.handle, len(ys), arr,
+                                           ctypes.byref(prm) if prm is not None else None, _stream(stream), core)
+        self._check(st)
+        return tuple(core)
 
     def bmnd_denoise_batch_host(self, ys, outs, cfgs, prm: bmnd_params | None = None, stream=None):
         """ys/outs: lists of C-contiguous float32 numpy arrays (host memory;

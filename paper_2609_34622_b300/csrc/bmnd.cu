@@ -304,7 +304,7 @@ int cube_side(int D, const int *j, int gtrans, int kex, int spatial) {
 
 // Dynamic shared memory of a stage launch; cached: second mass-conservation
 // sweep from the synthesis cache (y and eta staged, one group buffer).
-int stage_smem(const DGeom &g, int M, int nreg, bool cached = false) {
+int stage_smem(const DGeom &g, int M, int nreg, bool cached = false, bool st1 = false) {
   if (cached) nreg = 2;
   else if (g.lean) nreg = 1;  // only the matching guide is staged
   size_t b = al16(sizeof(DJob));
@@ -314,6 +314,7 @@ int stage_smem(const DGeom &g, int M, int nreg, bool cached = false) {
   size_t mats = 0;
   for (int a = 0; a < g.D; ++a) mats += (size_t)mat_block(g.j[a]) * 4;
   b = al16(b + mats);
+  b = al16(b + (g.bsm && st1 && !cached ? (size_t)(g.region + RPAD) * 4 : 0));
   b = al16(b + (size_t)nreg * (g.region + RPAD) * 4);
   b = al16(b + (size_t)g.region * 8);
   b += (size_t)NW * (cached ? warp_bytes(M, g.MS, g.fp, 0, 1) : warp_bytes(M, g.MS, g.fp, g.lean));
@@ -572,6 +573,9 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.kex = pr.cov_planes;
   pl.spatial = pr.spatial_transform;
   g.kex = pr.cov_planes;  // the shared-memory plan holds the coordinate table
+  // patch-sum map for the stage-1 noise bias: specialized kernels with one
+  // or two axes (with three, the lean tiles spend the memory on cores)
+  g.bsm = (D <= 2 && cube_side(D, g.j, pl.gtrans, pl.kex, pl.spatial)) ? 1 : 0;
   g.dct64 = ctx->tab64;
   g.diag = ctx->diag;
   if (pl.metric != BMND_METRIC_SSD) {
@@ -611,6 +615,11 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   int C[KMAXD];
   for (int a = 0; a < D; ++a) C[a] = (int)std::min<int64_t>(target[D], g.ell[a] + 1);
   int nreg_max = (stages == 2 ? 2 : 1) + (mass_conserve ? 1 : 0);
+  // shared memory of the largest launch of the plan: stage 1 (with its
+  // patch-sum map), stage 2 and the mass-conservation sweep
+  auto plan_smem = [&](const DGeom &gg) {
+    return std::max(stage_smem(gg, pl.Mmax, nreg_max), stage_smem(gg, group_size[0], 1, false, true));
+  };
   if (D >= 3) {
     // every core shape up to the target: the smallest staged region per core
     // location, discounted while there are fewer than 2 tiles per SM
@@ -619,7 +628,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
     for (int a = 0; a < D; ++a) { lim[a] = C[a]; C[a] = 1; }
     for (;;) {
       set_tiles(g, C);
-      if (stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem) {
+      if (plan_smem(g) <= ctx->max_smem) {
         const double cost = (double)g.region / (double)g.cap / (double)std::min<int64_t>(g.ntiles, 2 * 148);
         if (best[0] == 0 || cost < best_cost) {
           best_cost = cost;
@@ -639,7 +648,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   // there are 2 tiles per SM (or the cores reach their minimum)
   while (D < 3) {
     set_tiles(g, C);
-    bool fits = stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem;
+    bool fits = plan_smem(g) <= ctx->max_smem;
     int big = 0;
     for (int a = 1; a < D; ++a) if (C[a] > C[big]) big = a;
     if (fits && (g.ntiles >= 2 * 148 || C[big] < 2 * minc[D])) break;
@@ -666,7 +675,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
       }
       if (ok) {
         set_tiles(g, T);
-        if (stage_smem(g, pl.Mmax, nreg_max) <= ctx->max_smem) {
+        if (plan_smem(g) <= ctx->max_smem) {
           for (int a = 0; a < D; ++a) C[a] = T[a];
         } else {
           set_tiles(g, C);
@@ -677,13 +686,13 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   // enable the private footprint if it costs no resident CTA per SM
   if (pl.fp_candidate) {
     const int per_sm = 233472;  // shared memory per SM
-    int without = stage_smem(g, pl.Mmax, nreg_max);
+    int without = plan_smem(g);
     g.fp = pl.fp_candidate;
-    int with = stage_smem(g, pl.Mmax, nreg_max);
+    int with = plan_smem(g);
     int b0 = std::min(2, per_sm / std::max(without, 1)), b1 = std::min(2, per_sm / std::max(with, 1));
     if (with > ctx->max_smem || b1 < b0) g.fp = 0;
   }
-  pl.smem[0] = stage_smem(g, group_size[0], 1);
+  pl.smem[0] = stage_smem(g, group_size[0], 1, false, true);
   pl.smem[1] = stages == 2 ? stage_smem(g, group_size[1], 2) : 0;
   pl.smem[2] = stage_smem(g, pl.Mmax, nreg_max);
   // schedule geometry on the full shape
@@ -1296,6 +1305,35 @@ bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t 
                          mass_conserve, nullptr, out, stream);
 }
 
+// Tile cores the tuners time for a plan: the planner's core first, powers
+// of two per axis for one or two axes, steps of one and two around the
+// planner's core for more.
+std::vector<std::vector<int>> tune_candidates(const Plan &p0) {
+  const int D = p0.D;
+  std::vector<std::vector<int>> cand;
+  auto add = [&](std::vector<int> c) {
+    for (int a = 0; a < D; ++a) c[a] = (int)std::max<int64_t>(1, std::min<int64_t>(c[a], p0.g.ell[a] + 1));
+    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+  };
+  std::vector<int> def(D);
+  for (int a = 0; a < D; ++a) def[a] = p0.g.C[a];
+  add(def);
+  if (D == 1) {
+    for (int v : {16, 32, 64, 128, 256, 512}) add({v});
+  } else if (D == 2) {
+    for (int v0 : {4, 8, 16, 32})
+      for (int v1 : {4, 8, 16, 32}) add({v0, v1});
+  } else {
+    for (int a = 0; a < D; ++a)
+      for (int dl : {-2, -1, 1, 2}) {
+        std::vector<int> c = def;
+        c[a] += dl;
+        if (c[a] >= 1) add(c);
+      }
+  }
+  return cand;
+}
+
 bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
                           const int *patch, const int *step, const int *search, const int *group_size, int stages,
                           int mass_conserve, const bmnd_params *params, float *out, void *stream, int *core) {
@@ -1318,29 +1356,8 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
   const int D = p0.D;
   const int64_t N = p0.g.N;
   if (!(y + N <= out || out + N <= y)) return fail(ctx, BMND_EINVAL, "out overlaps y");
-  // candidates: the planner's core, powers of two per axis for one or two
-  // axes, steps of one and two around the planner's core for more
-  std::vector<std::vector<int>> cand;
-  auto add = [&](std::vector<int> c) {
-    for (int a = 0; a < D; ++a) c[a] = (int)std::max<int64_t>(1, std::min<int64_t>(c[a], p0.g.ell[a] + 1));
-    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
-  };
-  std::vector<int> def(D);
-  for (int a = 0; a < D; ++a) def[a] = p0.g.C[a];
-  add(def);
-  if (D == 1) {
-    for (int v : {16, 32, 64, 128, 256, 512}) add({v});
-  } else if (D == 2) {
-    for (int v0 : {4, 8, 16, 32})
-      for (int v1 : {4, 8, 16, 32}) add({v0, v1});
-  } else {
-    for (int a = 0; a < D; ++a)
-      for (int dl : {-2, -1, 1, 2}) {
-        std::vector<int> c = def;
-        c[a] += dl;
-        if (c[a] >= 1) add(c);
-      }
-  }
+  std::vector<std::vector<int>> cand = tune_candidates(p0);
+  std::vector<int> def = cand[0];
   const JobIO io{y, out, noise, {group_size[0], stages == 2 ? group_size[1] : group_size[0]}, stages,
                  mass_conserve & (stages == 2 ? 3 : 1)};
   const std::vector<JobIO> ios{io};
@@ -1549,7 +1566,7 @@ static bmnd_status match_or_schedule(bmnd_ctx *ctx, const float *guide, int ndim
                (int *)(B + pl.o_rcount), st);
   CU(cudaGetLastError());
   if (do_match) {
-    int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1);
+    int sm = stage_smem(J.g, gs[0], J.g.stage == 2 ? 2 : 1, false, J.g.stage != 2);
     ProfScope ps(ctx, BMND_KERNEL_MATCH, st);
     rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), stage == 2 ? 2 : kernel_stage(pl.metric, 1), ctx->djobs,
                       1, pl.g.ntiles, 1, sm, st);
@@ -1665,6 +1682,94 @@ bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
                   stages, jb.mass_conserve & (stages == 2 ? 3 : 1)};
   }
   return run_jobs(ctx, plans, io, pr, 1, stages, nullptr, (cudaStream_t)stream);
+}
+
+bmnd_status bmnd_autotune_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs, const bmnd_params *params,
+                                void *stream, int *core) {
+  if (!ctx) return BMND_EINVAL;
+  ctx->err[0] = 0;
+  if (n_jobs < 1 || !jobs) return fail(ctx, BMND_EINVAL, "no jobs");
+  bmnd_params pr;
+  if (params) pr = *params; else bmnd_default_params(&pr);
+  CU(cudaSetDevice(ctx->device));
+  const int stages = jobs[0].stages;
+  std::vector<JobIO> io(n_jobs);
+  std::vector<std::string> keys(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    const bmnd_job &jb = jobs[i];
+    if (!jb.y || !jb.out) return fail(ctx, BMND_EINVAL, "job %d: null y or out", i);
+    bmnd_status rc = check_noise(ctx, jb.noise, &pr);
+    if (rc != BMND_OK) return rc;
+    if (jb.stages != stages) return fail(ctx, BMND_EUNSUPPORTED, "job %d: all jobs must use the same stage count", i);
+    if (jb.mass_conserve < 0 || jb.mass_conserve > 3) return fail(ctx, BMND_EINVAL, "job %d: bad mass_conserve", i);
+    keys[i] = tune_key(jb.ndim, jb.shape, jb.patch, jb.step, jb.search, jb.group_size, jb.stages, jb.mass_conserve, pr);
+    io[i] = JobIO{jb.y, jb.out, jb.noise, {jb.group_size[0], stages == 2 ? jb.group_size[1] : jb.group_size[0]},
+                  stages, jb.mass_conserve & (stages == 2 ? 3 : 1)};
+  }
+  // the jobs sharing the first job's problem key are tuned together
+  const std::string key = keys[0];
+  ctx->tuned.erase(key);
+  auto plan_all = [&](const std::vector<int> *c, std::vector<Plan> &plans) -> bmnd_status {
+    plans.assign(n_jobs, Plan());
+    for (int i = 0; i < n_jobs; ++i) {
+      const bmnd_job &jb = jobs[i];
+      ctx->force_core = keys[i] == key ? c : nullptr;
+      bmnd_status rc = make_plan(ctx, jb.ndim, jb.shape, jb.patch, jb.step, jb.search, jb.group_size, jb.stages,
+                                 jb.mass_conserve, pr, plans[i]);
+      ctx->force_core = nullptr;
+      if (rc != BMND_OK) return rc;
+      const int64_t N = plans[i].g.N;
+      if (!(jb.y + N <= jb.out || jb.out + N <= jb.y)) return fail(ctx, BMND_EINVAL, "job %d: out overlaps y", i);
+    }
+    return BMND_OK;
+  };
+  std::vector<Plan> plans;
+  bmnd_status rc = plan_all(nullptr, plans);
+  if (rc != BMND_OK) return rc;
+  const std::vector<std::vector<int>> cand = tune_candidates(plans[0]);
+  const int D = plans[0].D;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  double best_ms = 1e30;
+  std::vector<int> best = cand[0];
+  for (const std::vector<int> &c : cand) {
+    rc = plan_all(&c, plans);
+    if (rc != BMND_OK) break;
+    bool fits = true;
+    for (int a = 0; a < D; ++a) fits = fits && plans[0].g.C[a] == c[a];
+    if (!fits) continue;
+    // one untimed batch, then two timed ones
+    rc = run_jobs(ctx, plans, io, pr, 1, stages, nullptr, st);
+    if (rc != BMND_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == BMND_OK; ++r) rc = run_jobs(ctx, plans, io, pr, 1, stages, nullptr, st);
+    if (rc != BMND_OK) break;
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = fail(ctx, BMND_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != BMND_OK) return rc;
+  ctx->tuned[key] = best;
+  rc = plan_all(nullptr, plans);
+  if (rc == BMND_OK) rc = run_jobs(ctx, plans, io, pr, 1, stages, nullptr, st);
+  if (rc == BMND_OK && core) {
+    for (int d = 0; d < jobs[0].ndim; ++d) core[d] = 1;
+    for (int a = 0; a < D; ++a) core[plans[0].kax_of[a]] = plans[0].g.C[a];
+  }
+  return rc;
 }
 
 bmnd_status bmnd_denoise_batch_host(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs, const bmnd_params *params,

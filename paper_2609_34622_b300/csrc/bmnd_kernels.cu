@@ -1229,7 +1229,8 @@ template <int D, int JL, int KB, int ST>
 // the FP32 scores are exact (decide_group).
 __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restrict__ S, const int *rr,
                           const int *org, const int *rowoff, int lane, int *mem, bool nonneg, bool exact,
-                          int emin, int span, float vmaxf, bool counts, unsigned long long *diag) {
+                          int emin, int span, float vmaxf, bool counts, unsigned long long *diag,
+                          const float *__restrict__ bsm) {
   int lo[D], W[D];
   int64_t ncand = 1;
 #pragma unroll
@@ -1333,7 +1334,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           float q[KB];
 #pragma unroll
           for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
-          if (ST != 2 && g.bias_on && nonneg) {
+          if (ST != 2 && g.bias_on && nonneg && bsm == nullptr) {
 #pragma unroll 1
             for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
@@ -1351,7 +1352,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
                 for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
               }
             }
-          } else if (ST != 2 && g.bias_on) {
+          } else if (ST != 2 && g.bias_on && bsm == nullptr) {
 #pragma unroll 1
             for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
@@ -1399,6 +1400,12 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
             }
           }
         }
+      }
+      if (JL > 0 && bsm != nullptr) {
+        // the bias sums from the patch-sum map (sum p + sum q, all terms >= 0)
+        const float ps = bsm[rbase];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) bs[b] = b < kb ? ps + bsm[cbase + b] : 0.f;
       }
 #pragma unroll
       for (int b = 0; b < KB; ++b) {
@@ -2619,6 +2626,7 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
 
 // Shared-memory layout of one job (the host computes the same sizes).
 struct SmemLayout {
+  float *bsm;    // stage-1 noise bias: patch sums of the guide per region position
   int *vreg, *vbuf, *rowoff, *moff, *fvoff, *fpreg;
   int *vcrd;     // shared-source variance: patch-entry coordinates, 5 bits per axis
   int64_t *vgl;  // lean: global offset of every patch entry
@@ -2651,6 +2659,9 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
   p = al16p(p);
   s.mats = reinterpret_cast<float *>(p);
   for (int a = 0; a < g.D; ++a) p += sizeof(float) * mat_block(g.j[a]);
+  p = al16p(p);
+  s.bsm = reinterpret_cast<float *>(p);
+  p += sizeof(float) * (g.bsm && !stage2 && !mc2 && !cached ? g.region + RPAD : 0);
   p = al16p(p);
   const int RS = g.region + RPAD;
   s.Sg = reinterpret_cast<float *>(p); p += sizeof(float) * RS;
@@ -2811,7 +2822,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     float *wts = reinterpret_cast<float *>(wp + MMAX * 4);
     float *rr_s = reinterpret_cast<float *>(wp + 2 * MMAX * 4);
     int *lvl = reinterpret_cast<int *>(wp + 3 * MMAX * 4);
-    float *bufA = reinterpret_cast<float *>(wp + 5 * MMAX * 4);
+    float *bufA = reinterpret_cast<float *>(wp + 4 * MMAX * 4);
     float *bufB = cmode ? bufA : bufA + g.M * MS;
     // the private footprint (float2) follows the group buffer(s), their
     // float count rounded up to even so that it stays 8-byte aligned (one
@@ -2923,6 +2934,42 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
       tile_span = (int)(s_vmax >> 23) - 126 - s_emin;  // |v| < 2^(exponent + 1)
     }
 
+    // stage-1 SSD noise bias on a non-negative tile (Prop. "Scaled-Poisson
+    // SSD noise bias": B = s_P sum_i (p_i + q_i), every term >= 0): the
+    // patch sum of the guide at every region position where a patch fits,
+    // so that a candidate's bias is s_P (sum p + sum q) from two reads
+    const bool use_bsm = JL > 0 && D <= 2 && g.bsm && !mc2 && !stage2 && g.bias_on && tile_nonneg && g.metric == 0;
+    if (use_bsm) {
+      // sums along the last axis (into acc[].x, zeroed again below), then
+      // along the first; positions whose patch does not fit get 0
+      const int RL = g.RG[D - 1], JJL = JL > 0 ? JL : 1;
+      float *hs = D == 2 ? reinterpret_cast<float *>(acc) : L.bsm;
+      const int hstride = D == 2 ? 2 : 1;
+      for (int e = threadIdx.x; e < g.region; e += blockDim.x) {
+        float t = 0.f;
+        if (e % RL <= RL - JJL) {
+#pragma unroll
+          for (int i = 0; i < JJL; ++i) t += Sg[e + i];
+        }
+        hs[hstride * e] = t;
+      }
+      if (D == 2) {
+        __syncthreads();
+        const int R0 = g.RG[0];
+        for (int e = threadIdx.x; e < g.region; e += blockDim.x) {
+          float t = 0.f;
+          if (e / RL <= R0 - JJL) {
+#pragma unroll
+            for (int r = 0; r < JJL; ++r) t += hs[2 * (e + r * RL)];
+          }
+          L.bsm[e] = t;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < g.region; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+    }
+
     const int nref = sj->ref_count[tile];
     const int rounds = (nref + NW - 1) / NW;
     const int64_t tslot = (int64_t)tile * g.cap;
@@ -2941,7 +2988,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         }
         if (!mc2) {
           n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg, tile_exact, tile_emin,
-                                        tile_span, tile_vmax, tile_counts, g.diag);
+                                        tile_span, tile_vmax, tile_counts, g.diag, use_bsm ? L.bsm : nullptr);
           if (sj->groups) {
             for (int m = lane; m < g.M; m += 32)
               sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
@@ -3174,40 +3221,67 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
     }
     const DJob &J = jobs[lo];
     const DGeom &g = J.g;
-    int64_t u = t - J.vox_base;
-    int64_t uc[D];
-    {
+    const int64_t u = t - J.vox_base;
+    // coordinates (32-bit arithmetic below 2^31 locations)
+    int uc[D];
+    if (g.N < 2147483648ll) {
+      int rem = (int)u;
+#pragma unroll
+      for (int d = D - 1; d >= 0; --d) {
+        const int L = (int)g.L[d];
+        uc[d] = rem % L;
+        rem /= L;
+      }
+    } else {
       int64_t rem = u;
 #pragma unroll
-      for (int d = D - 1; d >= 0; --d) { uc[d] = rem % g.L[d]; rem /= g.L[d]; }
+      for (int d = D - 1; d >= 0; --d) { uc[d] = (int)(rem % g.L[d]); rem /= g.L[d]; }
     }
+    // covering tiles per axis: t C - rad <= u <= t C - rad + RG - 1
     int tlo[D], thi[D], tcur[D];
     bool any = true;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      int64_t a = uc[d] + g.rad[d] - g.RG[d] + 1;   // t C >= a
-      int64_t b = uc[d] + g.rad[d];                 // t C <= b
-      int64_t l = a <= 0 ? -((-a) / g.C[d]) : (a + g.C[d] - 1) / g.C[d];
-      int64_t h = b / g.C[d];
-      if (l < 0) l = 0;
+      const int a = uc[d] + g.rad[d] - g.RG[d] + 1;  // t C >= a
+      const int b = uc[d] + g.rad[d];                // t C <= b
+      int l = a <= 0 ? 0 : (a + g.C[d] - 1) / g.C[d];
+      int h = b / g.C[d];
       if (h > g.NT[d] - 1) h = g.NT[d] - 1;
-      tlo[d] = (int)l;
-      thi[d] = (int)h;
-      tcur[d] = (int)l;
+      tlo[d] = l;
+      thi[d] = h;
+      tcur[d] = l;
       if (l > h) any = false;
     }
+    // partials in ascending tile order; along the last axis four tiles per
+    // step, loaded before they are added, so that their latencies overlap
+    const int CL = g.C[D - 1], RL = g.rad[D - 1], UL = uc[D - 1];
     float num = 0.f, den = 0.f;
     while (any) {
-      int tile = 0, local = 0;
+      int tile0 = 0, local0 = 0;
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        tile = tile * g.NT[d] + tcur[d];
-        local += (int)(uc[d] - ((int64_t)tcur[d] * g.C[d] - g.rad[d])) * g.rst[d];
+      for (int d = 0; d < D - 1; ++d) {
+        tile0 = tile0 * g.NT[d] + tcur[d];
+        local0 += (uc[d] - (tcur[d] * g.C[d] - g.rad[d])) * g.rst[d];
       }
-      float2 v = J.partial[(int64_t)tile * g.region + local];
-      num += v.x;
-      den += v.y;
-      int d = D - 1;
+      tile0 *= g.NT[D - 1];
+      for (int tl = tlo[D - 1]; tl <= thi[D - 1]; tl += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int tt = tl + k;
+          v[k] = tt <= thi[D - 1]
+                     ? J.partial[(int64_t)(tile0 + tt) * g.region + local0 + (UL - (tt * CL - RL))]
+                     : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (tl + k <= thi[D - 1]) {
+            num += v[k].x;
+            den += v[k].y;
+          }
+        }
+      }
+      int d = D - 2;
       while (d >= 0) {
         if (++tcur[d] <= thi[d]) break;
         tcur[d] = tlo[d];

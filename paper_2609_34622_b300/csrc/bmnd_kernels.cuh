@@ -38,14 +38,14 @@ constexpr int GEN_TOTAL = 11440;
 // scale12[2 log2 N] = sqrt(1/N), scale12[2 log2 N + 1] = sqrt(2/N), N = 1..32.
 cudaError_t upload_fast_dct_constants(const float *sec31, const float *scale12);
 
-// Bytes of one warp's shared block: member list, weights, plane sums, the
-// members' footprint offsets and one spare list (5 x MMAX words), nbuf group buffers of M x MS floats (two for
+// Bytes of one warp's shared block: member list, weights, plane sums and the
+// members' footprint offsets (4 x MMAX words), nbuf group buffers of M x MS floats (two for
 // filtering, one for a second mass-conservation sweep from the synthesis
 // cache; their float count rounded up to even), the private footprint (fp
 // float2, 8-byte aligned) and, when y and eta are read from global memory
 // (lean), the members' global origins (MMAX int64), rounded up to 16.
 __host__ __device__ constexpr int warp_bytes(int M, int MS, int fp, int lean, int nbuf = 2) {
-  return (5 * MMAX * 4 + ((nbuf * M * MS + 1) & ~1) * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
+  return (4 * MMAX * 4 + ((nbuf * M * MS + 1) & ~1) * 4 + fp * 8 + (lean ? MMAX * 8 : 0) + 15) & ~15;
 }
 
 // Floats reserved in shared memory for the four J x J matrices of one patch
@@ -128,7 +128,9 @@ struct DGeom {
   int spatial;
   const double *sp64;
   float ht_band;
-  int pad_sp;
+  // bsm: the stage kernels keep a patch-sum map of the guide (one float per
+  // region position) for the stage-1 noise bias of non-negative tiles
+  int bsm;
   // Poisson distances on count data in exact integer arithmetic: pfix
   // holds fixed-point tables (units 2^-32) of the per-entry contributions
   // and the finite-count moments (layout at PFIX_*), and count_tol the

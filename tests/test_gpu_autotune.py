@@ -48,3 +48,32 @@ def test_autotune_kept_and_close_to_planner(k):
     g.close()
     ctx.close()
     ref_ctx.close()
+
+
+def test_autotune_batch_kept_and_bitwise():
+    """bmnd_autotune_batch: the core chosen on the whole batch is kept for the
+    problem key; the tuner's outputs, a later batched call and a later call per
+    array all give the same bits (a job's result does not depend on the batch
+    it runs in)."""
+    import torch
+    import paper_2609_34622_b300.bmnd as bm
+    rng = np.random.default_rng(98)
+    ys, cfgs = [], []
+    for k in range(4):
+        x = synth.disc_rect_image((72, 90), rng)
+        y, sp = synth.poisson_observe(x, 5.0 + 5 * k, rng)
+        ys.append(torch.from_numpy(np.ascontiguousarray(y, np.float32)).cuda())
+        cfgs.append(dict(noise=("poisson", sp), patch=(8, 8), step=(3, 3), search=(19, 19), group_size=(16, 32),
+                         stages=2, mass_conserve=0))
+    ctx = bm.Context(0)
+    tuned = [torch.empty_like(y) for y in ys]
+    core = ctx.bmnd_autotune_batch(ys, tuned, cfgs)
+    assert len(core) == 2 and all(1 <= v <= s for v, s in zip(core, ys[0].shape))
+    again = [torch.empty_like(y) for y in ys]
+    ctx.bmnd_denoise_batch(ys, again, cfgs)
+    for a, b in zip(tuned, again):
+        assert torch.equal(a, b)
+    for y, c, a in zip(ys, cfgs, again):
+        single = torch.empty_like(y)
+        ctx.bmnd_denoise(y, single, c["noise"], c["patch"], c["step"], c["search"], c["group_size"], 2, 0)
+        assert torch.equal(single, a)
