@@ -1420,30 +1420,43 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
         }
       }
     }
-    // once the running list is full (finite threshold), each lane's
-    // candidates go in ascending (score, index) order (odd-even transposition
-    // network): rotation b then offers every lane's b-th best, and when no
-    // lane's next candidate beats the threshold none of its later ones can,
-    // so the round ends
-    const bool sorted = thr != FLT_MAX;  // warp-uniform
-    if (sorted) {
+    // offer the candidates below the threshold, every lane its smallest
+    // pending one per round; a lane whose smallest no longer beats the
+    // threshold (which only falls) drops the rest.  The running list keeps
+    // its 32 smallest (score, index) entries whatever the order of the
+    // offers, so it ends as the 32 smallest candidates of the window.
+    unsigned pend = 0u;
 #pragma unroll
-      for (int p = 0; p < KB; ++p) {
+    for (int b = 0; b < KB; ++b)
+      if (kv_less(key[b], idx[b], thr, thri)) pend |= 1u << b;
+#pragma unroll 1
+    while (__any_sync(0xffffffffu, pend != 0u)) {
+      // the lane's smallest pending (score, index): a tree over its slots
+      float ek[KB];
+      int ei[KB], eb[KB];
 #pragma unroll
-        for (int t = p & 1; t + 1 < KB; t += 2) {
-          const bool sw = kv_less(key[t + 1], idx[t + 1], key[t], idx[t]);
-          const float k0 = sw ? key[t + 1] : key[t], k1 = sw ? key[t] : key[t + 1];
-          const int i0 = sw ? idx[t + 1] : idx[t], i1 = sw ? idx[t] : idx[t + 1];
-          key[t] = k0; key[t + 1] = k1;
-          idx[t] = i0; idx[t + 1] = i1;
+      for (int b = 0; b < KB; ++b) {
+        const bool pb = (pend >> b) & 1u;
+        ek[b] = pb ? key[b] : FLT_MAX;
+        ei[b] = pb ? idx[b] : INT_MAX;
+        eb[b] = b;
+      }
+#pragma unroll
+      for (int w = 1; w < KB; w *= 2) {
+#pragma unroll
+        for (int b = 0; b + w < KB; b += 2 * w) {
+          if (kv_less(ek[b + w], ei[b + w], ek[b], ei[b])) {
+            ek[b] = ek[b + w];
+            ei[b] = ei[b + w];
+            eb[b] = eb[b + w];
+          }
         }
       }
-    }
-    // merge into the running best list (one copy of the merge code: the
-    // candidates rotate through key[0] / idx[0])
-#pragma unroll 1
-    for (int b = 0; b < KB; ++b) {
-      bool offer = kv_less(key[0], idx[0], thr, thri);
+      const float ck = ek[0];
+      const int ci = ei[0];
+      const bool has = ci != INT_MAX;
+      const bool offer = has && kv_less(ck, ci, thr, thri);
+      if (has) pend = offer ? (pend & ~(1u << eb[0])) : 0u;
       unsigned omask = __ballot_sync(0xffffffffu, offer);
       if (omask) {
         if (__popc(omask) <= 8) {
@@ -1452,17 +1465,17 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           while (omask) {
             const int src = __ffs(omask) - 1;
             omask &= omask - 1;
-            const float ck = __shfl_sync(0xffffffffu, key[0], src);
-            const int ci = __shfl_sync(0xffffffffu, idx[0], src);
-            const int pos = __popc(__ballot_sync(0xffffffffu, kv_less(lk, li, ck, ci)));
+            const float sk = __shfl_sync(0xffffffffu, ck, src);
+            const int si = __shfl_sync(0xffffffffu, ci, src);
+            const int pos = __popc(__ballot_sync(0xffffffffu, kv_less(lk, li, sk, si)));
             const float uk = __shfl_up_sync(0xffffffffu, lk, 1);
             const int ui = __shfl_up_sync(0xffffffffu, li, 1);
             if (lane > pos) { lk = uk; li = ui; }
-            else if (lane == pos) { lk = ck; li = ci; }
+            else if (lane == pos) { lk = sk; li = si; }
           }
         } else {
-          float ok = offer ? key[0] : FLT_MAX;
-          int oi = offer ? idx[0] : INT_MAX;
+          float ok = offer ? ck : FLT_MAX;
+          int oi = offer ? ci : INT_MAX;
           warp_sort(ok, oi, lane);
           warp_merge(lk, li, ok, oi, lane);
         }
@@ -1476,11 +1489,7 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
             thr = t;
           }
         }
-      } else if (sorted) {
-        break;
       }
-#pragma unroll
-      for (int t = 0; t < KB - 1; ++t) { key[t] = key[t + 1]; idx[t] = idx[t + 1]; }
     }
   }
   int K = g.M - 1;
@@ -2293,11 +2302,6 @@ __device__ __forceinline__ void col_store(float *buf, int v, const float (&y)[N]
   for (int m = 0; m < N; ++m) buf[m * MS + v] = y[m];
 }
 
-// Stage 1, one column: sigma^2 = H^2 s (s = T_patch^2 m_v in bufA, or the
-// Gaussian variance), X = H x, hard threshold with weight terms into bufA,
-// then H^T of the kept coefficients back into bufB.
-// Returns the planes whose hard-threshold decision FP32 cannot take
-// (bitmask); they are kept for now and settled by col_ht_settle.
 // Shared-source corrections of the leading group-axis planes (column of
 // the register filter; cx holds planes 0..3, zero beyond k_ex).
 template <int N>
@@ -2307,6 +2311,11 @@ __device__ __forceinline__ void add_shared_source(float (&S)[N], float4 cx) {
   for (int m = 0; m < (N < 4 ? N : 4); ++m) S[m] += c[m];
 }
 
+// Stage 1, one column: sigma^2 = H^2 s (s = T_patch^2 m_v in bufA, or the
+// Gaussian variance), X = H x, hard threshold with weight terms into bufA,
+// then H^T of the kept coefficients back into bufB.
+// Returns the planes whose hard-threshold decision FP32 cannot take
+// (bitmask); they are kept for now and settled by col_ht_settle.
 template <int N, int MS>
 __device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bufA, float *bufB, int v, float lam2,
                                                        float eX, float eS0, float4 cx, float eSx) {
