@@ -2129,15 +2129,44 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       // gather the guide group (y in stage 1, pilot in stage 2) and, for
       // Poisson data, its variance map m_v = s_P [guide]_+; then
       // sigma_k^2 = sum_i T_ki^2 m_v(u_i)
-      BMND_FOR_ENTRIES({
-        const float gv = Sg[mem[m] + vreg[v]];
-        const int a = m * MS + vbuf[v];
-        bufB[a] = gv;
-        const float mv = g.poisson ? g.s_p * fmaxf(gv, 0.f) : g.var_g;
-        bufA[a] = mv;
-        n2 = fmaf(gv, gv, n2);
-        sm += mv;
-      });
+      {
+        const bool pois = g.poisson;
+        const float sp = g.s_p, var_g = g.var_g;
+        auto put = [&](int a, float gv) {
+          bufB[a] = gv;
+          const float mv = pois ? sp * fmaxf(gv, 0.f) : var_g;
+          bufA[a] = mv;
+          n2 = fmaf(gv, gv, n2);
+          sm += mv;
+        };
+        if constexpr (SH::fixed && SH::P % 32 == 0) {
+          // two members' entries loaded before they are stored
+          constexpr int KV = SH::P / 32;
+          int vb[KV], vr[KV];
+#pragma unroll
+          for (int k = 0; k < KV; ++k) {
+            vb[k] = vbuf[lane + 32 * k];
+            vr[k] = vreg[lane + 32 * k];
+          }
+          for (int m0 = 0; m0 < n; m0 += 2) {
+            const bool two = m0 + 1 < n;
+            const int o0 = mem[m0], o1 = two ? mem[m0 + 1] : o0;
+            float t0[KV], t1[KV];
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              t0[k] = Sg[o0 + vr[k]];
+              t1[k] = Sg[o1 + vr[k]];
+            }
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              put(m0 * MS + vb[k], t0[k]);
+              if (two) put((m0 + 1) * MS + vb[k], t1[k]);
+            }
+          }
+        } else {
+          BMND_FOR_ENTRIES(put(m * MS + vbuf[v], Sg[mem[m] + vreg[v]]));
+        }
+      }
       __syncwarp();
       tb = bufA;
       tmode = 2;
@@ -2174,55 +2203,104 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       // (entries lane + 32 k); kept until settled below
       unsigned long long undecided = 0ull;
       int visit = 0;
-      // ---- shrinkage; per-coefficient weight terms into bufA ----
-      BMND_FOR_ENTRIES({
-        const int a = m * MS + vbuf[v];
-        const float s2 = varT ? bufA[a] : g.var_g;
-        const float X = bufB[a];
+      // ---- shrinkage; per-coefficient weight terms into bufA.  The
+      // profile's scalars are read once: the group buffers share the shared
+      // memory with the job descriptor, so the compiler would otherwise
+      // reload them after every store ----
+      const bool soft = g.soft, wdomain = g.wdomain != 0;
+      const int wmodel = g.wmodel, kex = g.kex;
+      const float var_g = g.var_g, lambda = g.lambda, a_power = g.a_power, s_v = g.s_v;
+      // the shrinkage of coefficient a = (m, v) with value X and variance s2,
+      // entry number vis of this lane
+      auto shrink = [&](int m, int v, int a, float X, float s2, int vis) {
         float wterm;
-        if (!stage2 && g.soft) {
+        if (!stage2 && soft) {
           // Eq. (soft-threshold) as an attenuation att = [|X| - lambda
           // sigma]_+ / |X|; weight terms |att|^2 (times sigma^2)
           const float ax = fabsf(X);
-          const float t = g.lambda * sqrtf(s2);
+          const float t = lambda * sqrtf(s2);
           const float att = ax > t ? (ax - t) / ax : 0.f;
           bufB[a] = att * X;
-          wterm = att * att * (g.wmodel == 0 ? 1.f : s2);
+          wterm = att * att * (wmodel == 0 ? 1.f : s2);
         } else if (!stage2) {
           // |X| > lambda sigma; undecided in FP32: kept until settled
-          int kp = ht_decide32(X, s2, lam2, eX, m < g.kex ? eS0 + eSx : eS0);
+          int kp = ht_decide32(X, s2, lam2, eX, m < kex ? eS0 + eSx : eS0);
           if (kp < 0) {
-            if (visit < 64) undecided |= 1ull << visit;
+            if (vis < 64) undecided |= 1ull << vis;
             else kp = ht_keep64(g, n, m, v, mem, vreg, Sg) ? 1 : 0;  // past 64 visits: at once
           }
           bufB[a] = kp ? X : 0.f;
-          wterm = kp ? (g.wmodel == 0 ? 1.f : s2) : 0.f;
+          wterm = kp ? (wmodel == 0 ? 1.f : s2) : 0.f;
         } else {
-          const float S = fmaxf(X * X - g.a_power * s2, 0.f);
-          const float den = S + g.s_v * s2;
+          const float S = fmaxf(X * X - a_power * s2, 0.f);
+          const float den = S + s_v * s2;
           const float G = den > 0.f ? __fdividef(S, den) : 0.f;
           bufB[a] = G;
-          wterm = g.wmodel == 0 ? G * G
-                                : (g.wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
+          wterm = wmodel == 0 ? G * G : (wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
         }
-        if (g.wdomain) wterm *= syn_energy(g, v);
+        if (wdomain) wterm *= syn_energy(g, v);
         bufA[a] = wterm;
-        ++visit;
-      });
+      };
+      if constexpr (SH::fixed && SH::P % 32 == 0 && ST == 2) {
+        // Wiener stage, compile-time patches: this lane's entries v = lane +
+        // 32 k of two members are loaded before any of them is written back
+        // (the hard-threshold stage keeps one entry at a time: four inlined
+        // copies of its decision measured slower)
+        constexpr int KV = SH::P / 32;
+        int vb[KV];
+#pragma unroll
+        for (int k = 0; k < KV; ++k) vb[k] = vbuf[lane + 32 * k];
+        for (int m0 = 0; m0 < n; m0 += 2) {
+          const bool two = m0 + 1 < n;
+          float Xv[2][KV], Sv[2][KV];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              const int a = (m0 + h) * MS + vb[k];
+              const bool in = h == 0 || two;
+              Xv[h][k] = in ? bufB[a] : 0.f;
+              Sv[h][k] = in && varT ? bufA[a] : var_g;
+            }
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < KV; ++k)
+              if (h == 0 || two)
+                shrink(m0 + h, lane + 32 * k, (m0 + h) * MS + vb[k], Xv[h][k], Sv[h][k], (m0 + h) * KV + k);
+        }
+      } else {
+        BMND_FOR_ENTRIES({
+          const int a = m * MS + vbuf[v];
+          shrink(m, v, a, bufB[a], varT ? bufA[a] : var_g, visit);
+          ++visit;
+        });
+      }
       if (hard && __any_sync(0xffffffffu, undecided != 0ull))
         smem_ht_settle(g, n, P, MS, lane, undecided, mem, vreg, vbuf, Sg, bufA, bufB);
       __syncwarp();
       // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums
-      // its row, starting at its own entry so the reads spread over banks) ----
+      // its row, starting at its own entry so the reads spread over banks;
+      // four partial sums, so that the adds do not wait on one another) ----
       if (lane < n) {
-        float r = 0.f;
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
         const float *row = bufA + lane * MS;
-        int v = lane % P;
-        for (int t = 0; t < P; ++t) {
-          r += row[vbuf[v]];
-          if (++v == P) v = 0;
+        int v = lane % P, t = 0;
+        for (; t + 4 <= P; t += 4) {
+          const int v1 = v + 1 == P ? 0 : v + 1;
+          const int v2 = v1 + 1 == P ? 0 : v1 + 1;
+          const int v3 = v2 + 1 == P ? 0 : v2 + 1;
+          r0 += row[vbuf[v]];
+          r1 += row[vbuf[v1]];
+          r2 += row[vbuf[v2]];
+          r3 += row[vbuf[v3]];
+          v = v3 + 1 == P ? 0 : v3 + 1;
         }
-        rr_s[lane] = r;
+        for (; t < P; ++t) {
+          r0 += row[vbuf[v]];
+          v = v + 1 == P ? 0 : v + 1;
+        }
+        rr_s[lane] = (r0 + r1) + (r2 + r3);
       }
       __syncwarp();
       // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
@@ -2248,8 +2326,33 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
         if (D >= 3 && g.lean)
           gather_global(gy, nullptr, gb, vgl, n, P, lane,
                         [&](int m, int v, float x, float) { bufA[m * MS + vbuf[v]] = x; });
-        else
+        else if constexpr (SH::fixed && SH::P % 32 == 0) {
+          // two members' entries loaded before they are stored
+          constexpr int KV = SH::P / 32;
+          int vb[KV], vr[KV];
+#pragma unroll
+          for (int k = 0; k < KV; ++k) {
+            vb[k] = vbuf[lane + 32 * k];
+            vr[k] = vreg[lane + 32 * k];
+          }
+          for (int m0 = 0; m0 < n; m0 += 2) {
+            const bool two = m0 + 1 < n;
+            const int o0 = mem[m0], o1 = two ? mem[m0 + 1] : o0;
+            float t0[KV], t1[KV];
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              t0[k] = Sy[o0 + vr[k]];
+              t1[k] = Sy[o1 + vr[k]];
+            }
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              bufA[m0 * MS + vb[k]] = t0[k];
+              if (two) bufA[(m0 + 1) * MS + vb[k]] = t1[k];
+            }
+          }
+        } else {
           BMND_FOR_ENTRIES({ bufA[m * MS + vbuf[v]] = Sy[mem[m] + vreg[v]]; });
+        }
         __syncwarp();
         tb = bufA;
         tmode = 0;
@@ -2259,10 +2362,34 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       }
     } else if (ph == 3) {
       if (stage2) {
-        BMND_FOR_ENTRIES({
-          const int a = m * MS + vbuf[v];
-          bufA[a] *= bufB[a];
-        });
+        if constexpr (SH::fixed && SH::P % 32 == 0) {
+          constexpr int KV = SH::P / 32;
+          int vb[KV];
+#pragma unroll
+          for (int k = 0; k < KV; ++k) vb[k] = vbuf[lane + 32 * k];
+          for (int m0 = 0; m0 < n; m0 += 2) {
+            const bool two = m0 + 1 < n;
+            float x0[KV], x1[KV], g0[KV], g1[KV];
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              const int a0 = m0 * MS + vb[k], a1 = two ? a0 + MS : a0;
+              x0[k] = bufA[a0];
+              g0[k] = bufB[a0];
+              x1[k] = bufA[a1];
+              g1[k] = bufB[a1];
+            }
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+              bufA[m0 * MS + vb[k]] = x0[k] * g0[k];
+              if (two) bufA[(m0 + 1) * MS + vb[k]] = x1[k] * g1[k];
+            }
+          }
+        } else {
+          BMND_FOR_ENTRIES({
+            const int a = m * MS + vbuf[v];
+            bufA[a] *= bufB[a];
+          });
+        }
         __syncwarp();
         tb = bufA;
         tmode = 1;
