@@ -202,13 +202,14 @@ def time_oracle(jobs, min_seconds: float, max_reps: int = 1000, matching=("ssd",
 
 # ---------------------------------------------------------------------------
 
-def captured_traffic(workload: str, n_arrays: int):
+def captured_traffic(workload: str, n_arrays: int, cores=None):
     """DRAM bytes of the stage kernel per step from the committed ncu summary
     of the workload, if the kernel source is unchanged since the capture
     (else None).  The 1-D signal: one stage launch as captured.  The 2-D
     batch: stage 1 + stage 2 bytes per image of a smaller batch of the same
     images and tiles, times the images of the step (every image is its own
-    set of tiles, so the traffic grows in proportion)."""
+    set of tiles, so the traffic grows in proportion), when the step runs
+    the captured tile cores."""
     import hashlib
     import re
     summ = {"c2": "k_stage_1d_262144.md", "c3": "k_stage_2d_512_batch.md"}.get(workload)
@@ -227,6 +228,9 @@ def captured_traffic(workload: str, n_arrays: int):
         m2 = re.search(r"traffic_bytes_per_launch: (\d+)", text)
         return int(m2.group(1)) if m2 else None
     m2 = re.search(r"traffic_bytes_per_image: stage1 (\d+), stage2 (\d+)", text)
+    m3 = re.search(r"capture_cores: (\d+)x(\d+)", text)
+    if cores is not None and m3 and tuple(cores) != (int(m3.group(1)), int(m3.group(2))):
+        return None  # other tiles write other partials
     return (int(m2.group(1)) + int(m2.group(2))) * n_arrays if m2 else None
 
 
@@ -672,6 +676,11 @@ def main():
     dev_ms, e2e_ms, value, e2e_val = replica_totals(dev_ms, e2e_ms, vox_step, args.steps, world,
                                                     dist if dist else None, dev)
 
+    # tile cores of the first array as the step ran it
+    c0 = cfgs[0]
+    inf0 = ctx.bmnd_plan_info(jobs[0].y.shape, c0["patch"], c0["step"], c0["search"], c0["group_size"],
+                              c0["stages"], c0["mass_conserve"], prm)
+    plan_cores = tuple(inf0["core"]) if "core" in inf0 else None
     # roofline of the dominant kernel (the stage kernel, both stages)
     n1, ms1 = kstats["stage1"]
     n2, ms2 = kstats["stage2"]
@@ -715,7 +724,7 @@ def main():
                                                    "where the FP32 error bounds could not decide"),
         "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": captured_traffic(args.workload, len(jobs)),
+                     "traffic": captured_traffic(args.workload, len(jobs), plan_cores),
                      "traffic_basis": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stage launches "
                                        "of one step (profiles/), null once the kernel source changed"),
                      "peak_basis": ("measured FP32 FMA throughput (bmnd_fp32_fma_peak, this run); nominal "

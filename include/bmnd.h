@@ -293,9 +293,11 @@ typedef struct {
 
 /* Denoise n_jobs independent arrays in shared launches: every kernel of a
  * stage covers the tiles of all jobs at once (a flat (job, tile) work list).
- * Each job's result equals that of bmnd_denoise_ex on the job alone.  All
- * jobs must have the same number of non-singleton axes.  Errors as
- * bmnd_denoise, reported for the first invalid job. */
+ * Each job's result equals that of bmnd_denoise_ex on the job alone.  Jobs
+ * with different numbers of non-singleton axes are accepted: the stage
+ * kernels are compiled per rank, so each rank class runs as its own batch,
+ * one class after another on `stream`.  All jobs use the same stage count.
+ * Errors as bmnd_denoise, reported for the first invalid job. */
 bmnd_status bmnd_denoise_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
                                const bmnd_params *params, void *stream);
 

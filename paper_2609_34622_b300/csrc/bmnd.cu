@@ -1102,8 +1102,26 @@ bmnd_status run_jobs(bmnd_ctx *ctx, std::vector<Plan> &plans, const std::vector<
                      const bmnd_params &pr, int first_stage, int last_stage, const float *ext_pilot,
                      cudaStream_t st) {
   const int D = plans[0].D;
-  for (auto &pl : plans)
-    if (pl.D != D) return fail(ctx, BMND_EUNSUPPORTED, "batched jobs must share the number of non-singleton axes");
+  bool mixed = false;
+  for (auto &pl : plans) mixed = mixed || pl.D != D;
+  if (mixed) {
+    // jobs of different ranks run one rank class after another on the same
+    // stream (the stage kernels are compiled per rank); each class is one
+    // persistent launch per kernel as for a batch of one rank
+    for (int d = 1; d <= KMAXD; ++d) {
+      std::vector<Plan> sub;
+      std::vector<JobIO> sio;
+      for (size_t i = 0; i < plans.size(); ++i)
+        if (plans[i].D == d) {
+          sub.push_back(plans[i]);
+          sio.push_back(io[i]);
+        }
+      if (sub.empty()) continue;
+      bmnd_status rc = run_jobs(ctx, sub, sio, pr, first_stage, last_stage, nullptr, st);
+      if (rc != BMND_OK) return rc;
+    }
+    return BMND_OK;
+  }
   std::vector<size_t> base;
   const size_t need = layout_jobs(plans, io, ctx->budget, base);
   bmnd_status rc = ensure_arena(ctx, need, st);

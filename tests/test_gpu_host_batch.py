@@ -66,3 +66,30 @@ def test_fp32_peak_sane():
     v = bm.bmnd_fp32_fma_peak(0)
     nominal = 148 * 128 * 2 * 2.032e9 / 1e12
     assert 0.5 * nominal < v < 1.2 * nominal, v
+
+
+def test_mixed_rank_batch_equals_single():
+    """A batch of 1-D, 2-D and 3-D arrays in one call: each array gets the
+    bits of its own call (the rank classes run one after another)."""
+    import torch
+    import paper_2609_34622_b300.bmnd as bm
+    rng = np.random.default_rng(77)
+    x1 = synth.ecg_signal(4000, 250.0, rng)
+    y1, s1 = synth.poisson_observe(x1, 30.0, rng)
+    x2 = synth.disc_rect_image((70, 66), rng)
+    y2, s2 = synth.poisson_observe(x2, 10.0, rng)
+    lam = synth.ellipsoid_phantom((20, 18, 16), rng)
+    y3, s3 = synth.poisson_observe(lam / lam.max(), 4.0, rng)
+    jobs = [(y2, dict(noise=("poisson", s2), patch=(8, 8), step=(3, 3), search=(15, 15))),
+            (y1, dict(noise=("poisson", s1), patch=(32,), step=(4,), search=(65,))),
+            (y3, dict(noise=("poisson", s3), patch=(4, 4, 4), step=(2, 2, 2), search=(7, 7, 7))),
+            (y2[::-1].copy(), dict(noise=("poisson", s2), patch=(8, 8), step=(3, 3), search=(15, 15)))]
+    ctx = bm.Context(0)
+    ys = [torch.from_numpy(np.ascontiguousarray(y, np.float32)).cuda() for y, _ in jobs]
+    outs = [torch.empty_like(y) for y in ys]
+    cfgs = [dict(c, group_size=(16, 32), stages=2, mass_conserve=0) for _, c in jobs]
+    ctx.bmnd_denoise_batch(ys, outs, cfgs)
+    for y, o, c in zip(ys, outs, cfgs):
+        single = torch.empty_like(y)
+        ctx.bmnd_denoise(y, single, c["noise"], c["patch"], c["step"], c["search"], c["group_size"], 2, 0)
+        assert torch.equal(single, o)
