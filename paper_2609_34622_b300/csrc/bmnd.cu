@@ -355,12 +355,13 @@ void set_tiles(DGeom &g, const int *C) {
     g.C[d] = C[d];
     g.NT[d] = (int)((g.ell[d] + 1 + C[d] - 1) / C[d]);
     g.RG[d] = C[d] + 2 * g.rad[d] + g.j[d] - 1;
+    g.RGP[d] = (d == g.D - 1 && g.D >= 2) ? (g.RG[d] | 1) : g.RG[d];
     g.ntiles *= g.NT[d];
     g.cap *= C[d];
-    g.region *= g.RG[d];
+    g.region *= g.RGP[d];
   }
   int s = 1;
-  for (int d = g.D - 1; d >= 0; --d) { g.rst[d] = s; s *= g.RG[d]; }
+  for (int d = g.D - 1; d >= 0; --d) { g.rst[d] = s; s *= g.RGP[d]; }
 }
 
 // Key of a problem for the tile tuner: everything the tiling depends on

@@ -1601,7 +1601,7 @@ __device__ __noinline__ int shared_source_pass(const DGeom &g, int n, int lane, 
   // lane m: region coordinates of member m and its overlap mask
   int cm[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) cm[d] = lane < n ? (mem[lane] / g.rst[d]) % g.RG[d] : 0;
+  for (int d = 0; d < D; ++d) cm[d] = lane < n ? (mem[lane] / g.rst[d]) % g.RGP[d] : 0;
   unsigned ov = 0u;
   for (int m = 0; m < n; ++m) {
     // every lane takes part in every shuffle (none under a condition)
@@ -1846,13 +1846,13 @@ __device__ __noinline__ bool ht_keep64(const DGeom &g, int n, int l, int q, cons
       const double am = group_axis_entry64(g, n, l, m);
       if (am == 0.0) continue;
       int cm[KMAXD];
-      for (int d = 0; d < D; ++d) cm[d] = (mem[m] / g.rst[d]) % g.RG[d];
+      for (int d = 0; d < D; ++d) cm[d] = (mem[m] / g.rst[d]) % g.RGP[d];
       for (int m2 = m + 1; m2 < n; ++m2) {
         const double am2 = group_axis_entry64(g, n, l, m2);
         if (am2 == 0.0) continue;
         int dl[KMAXD], ext[KMAXD], cnt = 1;
         for (int d = 0; d < D; ++d) {
-          dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - cm[d];
+          dl[d] = (mem[m2] / g.rst[d]) % g.RGP[d] - cm[d];
           ext[d] = g.j[d] - abs(dl[d]);
           cnt *= ext[d] > 0 ? ext[d] : 0;
         }
@@ -1925,7 +1925,7 @@ __device__ __noinline__ bool ht_keep64_warp(const DGeom &g, int n, int l, int q,
       if (am == 0.0 || am2 == 0.0) continue;
       int dl[KMAXD], ext[KMAXD], cnt = 1;
       for (int d = 0; d < D; ++d) {
-        dl[d] = (mem[m2] / g.rst[d]) % g.RG[d] - (mem[m] / g.rst[d]) % g.RG[d];
+        dl[d] = (mem[m2] / g.rst[d]) % g.RGP[d] - (mem[m] / g.rst[d]) % g.RGP[d];
         ext[d] = g.j[d] - abs(dl[d]);
         cnt *= ext[d] > 0 ? ext[d] : 0;
       }
@@ -2998,10 +2998,10 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         bool in = true;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) {
-          int c = rem % g.RG[d];
-          rem /= g.RG[d];
+          int c = rem % g.RGP[d];
+          rem /= g.RGP[d];
           int64_t x = (int64_t)org[d] + c;
-          if (x < 0 || x >= g.L[d]) in = false;
+          if (x < 0 || x >= g.L[d] || c >= g.RG[d]) in = false;  // outside the array, or layout padding
           gi += x * g.st[d];
         }
         if (in) {
@@ -3078,12 +3078,12 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
     if (use_bsm) {
       // sums along the last axis (into acc[].x, zeroed again below), then
       // along the first; positions whose patch does not fit get 0
-      const int RL = g.RG[D - 1], JJL = JL > 0 ? JL : 1;
+      const int RL = g.RGP[D - 1], RLr = g.RG[D - 1], JJL = JL > 0 ? JL : 1;
       float *hs = D == 2 ? reinterpret_cast<float *>(acc) : L.bsm;
       const int hstride = D == 2 ? 2 : 1;
       for (int e = threadIdx.x; e < g.region; e += blockDim.x) {
         float t = 0.f;
-        if (e % RL <= RL - JJL) {
+        if (e % RL <= RLr - JJL) {
 #pragma unroll
           for (int i = 0; i < JJL; ++i) t += Sg[e + i];
         }
@@ -3178,8 +3178,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
               int64_t o = 0;
 #pragma unroll
               for (int d = D - 1; d >= 0; --d) {
-                o += (int64_t)(org[d] + rem % g.RG[d]) * g.st[d];
-                rem /= g.RG[d];
+                o += (int64_t)(org[d] + rem % g.RGP[d]) * g.st[d];
+                rem /= g.RGP[d];
               }
               gb[lane] = o;
             }
@@ -3302,8 +3302,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
           int rem = mem[lane], fo = 0, fs = 1;
 #pragma unroll
           for (int d = D - 1; d >= 0; --d) {
-            fo += (rem % g.RG[d] - c[d]) * fs;
-            rem /= g.RG[d];
+            fo += (rem % g.RGP[d] - c[d]) * fs;
+            rem /= g.RGP[d];
             fs *= g.FW[d];
           }
           lvl[lane] = fo;
@@ -3469,8 +3469,8 @@ __global__ void k_export_groups(const DJob *__restrict__ jobs, const int64_t *__
         lin = 0;
 #pragma unroll
         for (int d = D - 1; d >= 0; --d) {
-          int c = rem % g.RG[d];
-          rem /= g.RG[d];
+          int c = rem % g.RGP[d];
+          rem /= g.RGP[d];
           lin += ((int64_t)tc[d] * g.C[d] - g.rad[d] + c) * g.st[d];
         }
       }

@@ -79,6 +79,10 @@ struct DGeom {
   int64_t L[KMAXD], st[KMAXD], ell[KMAXD];
   int j[KMAXD], rad[KMAXD];
   int C[KMAXD], NT[KMAXD], RG[KMAXD], rst[KMAXD];
+  // extents of the staged region's layout: RG, with the last axis padded to
+  // an odd length when there are two or more axes (window rows a row stride
+  // apart then fall into distinct banks); region and rst follow the layout
+  int RGP[KMAXD];
   float kaiser[KMAXD][JMAX];
   // private group footprint (2 rad_d + j_d per axis) used to accumulate a
   // group before merging it into the tile region; fp = 0 disables it
