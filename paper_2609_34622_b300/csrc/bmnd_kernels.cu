@@ -3388,42 +3388,53 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
       tcur[d] = l;
       if (l > h) any = false;
     }
-    // partials in ascending tile order; along the last axis four tiles per
-    // step, loaded before they are added, so that their latencies overlap
-    const int CL = g.C[D - 1], RL = g.rad[D - 1], UL = uc[D - 1];
+    // partials in ascending tile order, eight covering tiles per step: their
+    // offsets come from an odometer over the covering tile ranges and all
+    // eight loads are issued before any is added, so that their latencies
+    // overlap
+    int NT[D], CC[D], off[D], rs[D];  // the job's geometry in registers
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      NT[d] = g.NT[d];
+      CC[d] = g.C[d];
+      off[d] = uc[d] + g.rad[d];
+      rs[d] = g.rst[d];
+    }
+    const int64_t region = g.region;
+    const float2 *__restrict__ part = J.partial;
     float num = 0.f, den = 0.f;
-    while (any) {
-      int tile0 = 0, local0 = 0;
+    bool more = any;
+    while (more) {
+      float2 v[8];
+      unsigned valid = 0u;
 #pragma unroll
-      for (int d = 0; d < D - 1; ++d) {
-        tile0 = tile0 * g.NT[d] + tcur[d];
-        local0 += (uc[d] - (tcur[d] * g.C[d] - g.rad[d])) * g.rst[d];
-      }
-      tile0 *= g.NT[D - 1];
-      for (int tl = tlo[D - 1]; tl <= thi[D - 1]; tl += 4) {
-        float2 v[4];
+      for (int k = 0; k < 8; ++k) {
+        v[k] = make_float2(0.f, 0.f);
+        if (more) {
+          int tile = 0, local = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int tt = tl + k;
-          v[k] = tt <= thi[D - 1]
-                     ? J.partial[(int64_t)(tile0 + tt) * g.region + local0 + (UL - (tt * CL - RL))]
-                     : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (tl + k <= thi[D - 1]) {
-            num += v[k].x;
-            den += v[k].y;
+          for (int d = 0; d < D; ++d) {
+            tile = tile * NT[d] + tcur[d];
+            local += (off[d] - tcur[d] * CC[d]) * rs[d];
           }
+          v[k] = part[(int64_t)tile * region + local];
+          valid |= 1u << k;
+          int d = D - 1;
+          while (d >= 0) {
+            if (++tcur[d] <= thi[d]) break;
+            tcur[d] = tlo[d];
+            --d;
+          }
+          more = d >= 0;
         }
       }
-      int d = D - 2;
-      while (d >= 0) {
-        if (++tcur[d] <= thi[d]) break;
-        tcur[d] = tlo[d];
-        --d;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if ((valid >> k) & 1u) {
+          num += v[k].x;
+          den += v[k].y;
+        }
       }
-      if (d < 0) break;
     }
     J.out[u] = den > 0.f ? num / den : J.y[u];
     if (write_eta && J.eta) J.eta[u] = den;
