@@ -539,9 +539,11 @@ def main():
     flops = {1: 0.0, 2: 0.0}
     mflops = {1: 0.0, 2: 0.0}
     pilots = []
+    refs_step = 0  # reference patches per step, both stages
     for j, y in zip(jobs, ys):
         c = j.cfg
         o, _, cnt1 = ctx.bmnd_match(y, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1, prm)
+        refs_step += int(o.numel()) * c["stages"]
         pilot = torch.empty_like(y)
         ctx.bmnd_stage(y, None, pilot, c["noise"], c["patch"], c["step"], c["search"], c["group_size"][0], 1,
                        c["mass_conserve"] & 1, prm)
@@ -720,6 +722,7 @@ def main():
                 "path": "bmnd_denoise_batch_host: pinned host arrays in and out, copies inside the call, "
                         "host wall clock per call"},
         "gpu_launches": int(launches),
+        "reference_patches_per_s": refs_step * args.steps * world / (dev_ms / 1e3),
         "decisions_per_step": dict(decisions, note="taken in double precision (or exact integer arithmetic) "
                                                    "where the FP32 error bounds could not decide"),
         "roofline": {"kernel": "k_stage (stage 1 + stage 2 launches)", "bound": "alu", "achieved": achieved,
