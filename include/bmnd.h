@@ -410,8 +410,10 @@ bmnd_status bmnd_server_destroy(bmnd_server *srv);
  * Times the computation of bmnd_denoise_ex on this array with several tile
  * cores (the part of the array whose reference patches one CTA owns; the
  * planner's choice, powers of two per axis for one or two axes, steps of one
- * and two around the planner's choice for more) and keeps the fastest in the
- * context, keyed by shape, patch, step, search, group sizes, stages, mass
+ * and two around the planner's choice for more), each also with one resident
+ * CTA per SM where the shared memory would allow two (the stage kernels then
+ * keep the whole register file instead of a cap of 128 per thread), and keeps
+ * the fastest in the context, keyed by shape, patch, step, search, group sizes, stages, mass
  * conservation and profile (not the noise level).  Later calls on this
  * context with the same key -- bmnd_denoise, bmnd_denoise_ex, the batched
  * and graph entry points -- plan with that core.  The paper has no
@@ -420,7 +422,8 @@ bmnd_status bmnd_server_destroy(bmnd_server *srv);
  *   - Synchronous: it runs each candidate three times on `stream` and waits.
  *   - out receives the estimate with the chosen core.
  *   - core (host int[ndim], may be NULL) receives the chosen core per axis
- *     (1 for axes of length 1).
+ *     (1 for axes of length 1); the CTAs-per-SM choice is kept with it but
+ *     not reported.
  * Errors: those of bmnd_denoise_ex. */
 bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t *shape, bmnd_noise noise,
                           const int *patch, const int *step, const int *search, const int *group_size, int stages,

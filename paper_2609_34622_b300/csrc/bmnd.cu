@@ -272,6 +272,7 @@ struct Plan {
   int metric;            // stage-1 matching distance (BMND_METRIC_*)
   int kex;               // shared-source variance planes (0 = diagonal)
   int spatial;           // stage-1 spatial transform (BMND_SPATIAL_*)
+  int minb;              // CTAs per SM asked of the stage kernels: 0 by shared memory, 1 or 2
   int fp_candidate;
   int smem[3];           // dynamic shared bytes: stage 1, stage 2, +eta region
   // scratch offsets (bytes, relative to the job's block)
@@ -573,6 +574,7 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
   pl.metric = pr.match_metric;
   pl.kex = pr.cov_planes;
   pl.spatial = pr.spatial_transform;
+  pl.minb = 0;
   g.kex = pr.cov_planes;  // the shared-memory plan holds the coordinate table
   // patch-sum map for the stage-1 noise bias: specialized kernels with one
   // or two axes (with three, the lean tiles spend the memory on cores)
@@ -667,7 +669,8 @@ bmnd_status make_plan(bmnd_ctx *ctx, int ndim, const int64_t *shape, const int *
       auto it = ctx->tuned.find(tune_key(ndim, shape, patch, step, search, group_size, stages, mass_conserve, pr));
       if (it != ctx->tuned.end()) core = &it->second;
     }
-    if (core && (int)core->size() == D) {
+    if (core && ((int)core->size() == D || (int)core->size() == D + 1)) {
+      if ((int)core->size() == D + 1) pl.minb = (*core)[D];
       int T[KMAXD];
       bool ok = true;
       for (int a = 0; a < D; ++a) {
@@ -876,9 +879,12 @@ bmnd_status ensure_arena(bmnd_ctx *ctx, size_t need, cudaStream_t st) {
 // block scheduler place higher-priority work between tiles.  Every job of the
 // launch runs the given stage (1 or 2).
 bmnd_status launch_stage(bmnd_ctx *ctx, int D, int jL, int kb, int stage, const DJob *dj, int nj, int tiles,
-                         int mode, int smem, cudaStream_t st, int *counter = nullptr, bool tile_ctas = false) {
-  // two CTAs per SM when their shared memory fits, else the full register file
-  const int minb = 2 * (smem + 1024) <= 233472 ? 2 : 1;
+                         int mode, int smem, cudaStream_t st, int *counter = nullptr, bool tile_ctas = false,
+                         int minb_pref = 0) {
+  // two CTAs per SM (a register cap of 128) when their shared memory fits,
+  // else the full register file; a tuned preference of one CTA per SM wins
+  int minb = 2 * (smem + 1024) <= 233472 ? 2 : 1;
+  if (minb_pref == 1) minb = 1;
   stage_fn f = select_stage_kernel(D, jL, kb, minb, stage);
   CU(set_stage_smem(f, smem));
   int per_sm = 0;
@@ -951,6 +957,7 @@ struct JobTables {
   bool any_mc[2] = {false, false};
   int kjL = 0, kkb = 4;
   int kmetric = 0;        // stage-1 matching distance shared by the jobs
+  int kminb = 0;          // CTAs per SM asked of the stage kernels (0: by shared memory)
 };
 
 void build_tables(const std::vector<Plan> &plans, const std::vector<JobIO> &io, const bmnd_params &pr,
@@ -1002,6 +1009,7 @@ void build_tables(const std::vector<Plan> &plans, const std::vector<JobIO> &io, 
   t.kjL = kernel_jl(plans[0]);
   t.kkb = pick_kb(plans[0]);
   t.kmetric = plans[0].metric;
+  t.kminb = plans[0].minb;
   for (int i = 1; i < nj; ++i)
     if (kernel_jl(plans[i]) != t.kjL) { t.kjL = 0; t.kkb = 4; }
 }
@@ -1032,7 +1040,7 @@ bmnd_status record_launches(bmnd_ctx *ctx, const std::vector<Plan> &plans, const
     {
       ProfScope ps(ctx, s == 1 ? BMND_KERNEL_STAGE1 : BMND_KERNEL_STAGE2, st);
       rc = launch_stage(ctx, D, t.kjL, t.kkb, kernel_stage(t.kmetric, s), dj, nj, t.tiles, 0, t.smax[s - 1], st,
-                        counter);
+                        counter, false, t.kminb);
     }
     if (rc != BMND_OK) return rc;
     {
@@ -1044,7 +1052,7 @@ bmnd_status record_launches(bmnd_ctx *ctx, const std::vector<Plan> &plans, const
       {
         ProfScope ps(ctx, BMND_KERNEL_MC_SWEEP, st);
         rc = launch_stage(ctx, D, t.kjL, t.kkb, kernel_stage(t.kmetric, s), dj, nj, t.tiles, 2, t.smax2[s - 1], st,
-                          counter);
+                          counter, false, t.kminb);
       }
       if (rc != BMND_OK) return rc;
       {
@@ -1327,6 +1335,13 @@ bmnd_status bmnd_denoise(bmnd_ctx *ctx, const float *y, int ndim, const int64_t 
 // Tile cores the tuners time for a plan: the planner's core first, powers
 // of two per axis for one or two axes, steps of one and two around the
 // planner's core for more.
+// Whether a plan's stage launches would run two CTAs per SM by shared memory
+// (the tuners then also time one CTA per SM, with the full register file).
+bool two_ctas_possible(const Plan &pl) {
+  const int s = std::max(pl.smem[0], pl.smem[1]);
+  return 2 * (s + 1024) <= 233472;
+}
+
 std::vector<std::vector<int>> tune_candidates(const Plan &p0) {
   const int D = p0.D;
   std::vector<std::vector<int>> cand;
@@ -1386,6 +1401,14 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
   CU(cudaEventCreate(&e1));
   double best_ms = 1e30;
   std::vector<int> best = def;
+  // every core also with one CTA per SM (the full register file) where the
+  // shared memory would allow two
+  const size_t ncore = cand.size();
+  for (size_t i = 0; i < ncore; ++i) {
+    std::vector<int> c1 = cand[i];
+    c1.push_back(1);
+    cand.push_back(c1);
+  }
   for (const std::vector<int> &c : cand) {
     ctx->force_core = &c;
     std::vector<Plan> pc(1);
@@ -1393,7 +1416,7 @@ bmnd_status bmnd_autotune(bmnd_ctx *ctx, const float *y, int ndim, const int64_t
     if (rc != BMND_OK) break;
     bool fits = true;
     for (int a = 0; a < D; ++a) fits = fits && pc[0].g.C[a] == c[a];
-    if (!fits) continue;
+    if (!fits || ((int)c.size() > D && !two_ctas_possible(pc[0]))) continue;
     // one untimed run, then two timed ones
     rc = run_jobs(ctx, pc, ios, pr, 1, stages, nullptr, st);
     if (rc != BMND_OK) break;
@@ -1753,12 +1776,18 @@ bmnd_status bmnd_autotune_batch(bmnd_ctx *ctx, int n_jobs, const bmnd_job *jobs,
   CU(cudaEventCreate(&e1));
   double best_ms = 1e30;
   std::vector<int> best = cand[0];
-  for (const std::vector<int> &c : cand) {
+  std::vector<std::vector<int>> cands = cand;
+  for (const std::vector<int> &c0 : cand) {
+    std::vector<int> c1 = c0;
+    c1.push_back(1);
+    cands.push_back(c1);
+  }
+  for (const std::vector<int> &c : cands) {
     rc = plan_all(&c, plans);
     if (rc != BMND_OK) break;
     bool fits = true;
     for (int a = 0; a < D; ++a) fits = fits && plans[0].g.C[a] == c[a];
-    if (!fits) continue;
+    if (!fits || ((int)c.size() > D && !two_ctas_possible(plans[0]))) continue;
     // one untimed batch, then two timed ones
     rc = run_jobs(ctx, plans, io, pr, 1, stages, nullptr, st);
     if (rc != BMND_OK) break;
@@ -2031,12 +2060,14 @@ bmnd_status noalloc_run(bmnd_ctx *ctx, NoallocDevice *dev, const float *y, int n
   const int rgrid = (int)std::min<int64_t>((vox + 255) / 256, 148 * 32);
   for (int s = 1; s <= stages; ++s) {
     const DJob *dj = ctx->djobs + (s - 1);
-    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 0, smax[s - 1], st);
+    rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 0, smax[s - 1], st,
+                        nullptr, false, pl.minb);
     if (rc != BMND_OK) return rc;
     launch_reduce(pl.D, dj, 1, vox, any_mc[s - 1] ? 1 : 0, rgrid, st);
     CU(cudaGetLastError());
     if (any_mc[s - 1]) {
-      rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 2, smax[s - 1], st);
+      rc = launch_stage(ctx, pl.D, kernel_jl(pl), pick_kb(pl), s, dj, 1, pl.g.ntiles, 2, smax[s - 1], st,
+                        nullptr, false, pl.minb);
       if (rc != BMND_OK) return rc;
       launch_reduce(pl.D, dj, 1, vox, 0, rgrid, st);
       CU(cudaGetLastError());
