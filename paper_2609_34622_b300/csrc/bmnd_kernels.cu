@@ -1222,6 +1222,58 @@ __device__ __forceinline__ int decide_group(const DGeom &g, const float *__restr
   return __popc(__ballot_sync(FULL, lane < KK && lk < tlo));
 }
 
+// Squared distances and noise-bias sums of the KB candidates q + b (b < KB,
+// consecutive on the last axis) against the reference p, over all patch
+// rows of JJ entries (Sec. 4.1: the SSD and the B term of the stage-1
+// distance).  bs sums [p + q]_+, or p + q when every value is >= 0
+// (NONNEG).
+template <int KB, int JJ, bool NONNEG>
+__device__ __forceinline__ void ssd_bias_rows(const float *__restrict__ p, const float *__restrict__ q,
+                                              const int *__restrict__ rowoff, int rows, float *acc, float *bs) {
+  constexpr int IB = JJ < 8 ? JJ : 8;
+  float a[KB], t[KB];
+#pragma unroll
+  for (int b = 0; b < KB; ++b) { a[b] = 0.f; t[b] = 0.f; }
+  for (int r = 0; r < rows; ++r) {
+    const float *prow = p + rowoff[r];
+    const float *qrow = q + rowoff[r];
+    float w[KB];
+#pragma unroll
+    for (int b = 0; b < KB - 1; ++b) w[b] = qrow[b];
+#pragma unroll 1
+    for (int i0 = 0; i0 < JJ; i0 += IB) {
+#pragma unroll
+      for (int ii = 0; ii < IB; ++ii) {
+        const int i = i0 + ii;
+        w[KB - 1] = qrow[i + KB - 1];
+        const float pv = prow[i];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+          const float df = __fsub_rn(w[b], pv);
+          a[b] = fmaf(df, df, a[b]);
+          const float sp = __fadd_rn(pv, w[b]);
+          t[b] = __fadd_rn(t[b], NONNEG ? sp : fmaxf(sp, 0.f));
+        }
+#pragma unroll
+        for (int b = 0; b < KB - 1; ++b) w[b] = w[b + 1];
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < KB; ++b) { acc[b] = a[b]; bs[b] = t[b]; }
+}
+
+// The same out of line, for the planar kernels: only their tiles without
+// the patch-sum map take it, and inlined beside the plain SSD loop it costs
+// the stage kernel registers.  The 3-D kernels (no patch-sum map) inline it.
+template <int KB, int JJ>
+__device__ __noinline__ void ssd_bias_block(const float *__restrict__ p, const float *__restrict__ q,
+                                            const int *__restrict__ rowoff, int rows, bool nonneg, float *acc,
+                                            float *bs) {
+  if (nonneg) ssd_bias_rows<KB, JJ, true>(p, q, rowoff, rows, acc, bs);
+  else ssd_bias_rows<KB, JJ, false>(p, q, rowoff, rows, acc, bs);
+}
+
 template <int D, int JL, int KB, int ST>
 // nonneg: every staged guide value is >= 0 (count data), where
 // [p + q]_+ = p + q exactly and the bias term skips the max.
@@ -1323,7 +1375,19 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
       const int jl = JL > 0 ? JL : g.jL;
       if (pfix) metric_keys_fix<KB>(g, S + rbase, S + cbase, rowoff, acc);
       else if (pmetric) metric_scores<KB>(g, S + rbase, S + cbase, rowoff, acc);
-      for (int r = 0; r < (pmetric ? 0 : g.rows); ++r) {
+      if (JL > 0 && ST != 2 && !pmetric && g.bias_on && bsm == nullptr) {
+        if (D == 3) {
+          if (nonneg) ssd_bias_rows<KB, JL, true>(S + rbase, S + cbase, rowoff, g.rows, acc, bs);
+          else ssd_bias_rows<KB, JL, false>(S + rbase, S + cbase, rowoff, g.rows, acc, bs);
+        } else {
+          float ta[KB], tb[KB];
+          ssd_bias_block<KB, JL>(S + rbase, S + cbase, rowoff, g.rows, nonneg, ta, tb);
+#pragma unroll
+          for (int b = 0; b < KB; ++b) { acc[b] = ta[b]; bs[b] = tb[b]; }
+        }
+      }
+      const int rows_plain = pmetric || (JL > 0 && ST != 2 && g.bias_on && bsm == nullptr) ? 0 : g.rows;
+      for (int r = 0; r < rows_plain; ++r) {
         const float *prow = S + rbase + rowoff[r];
         const float *qrow = S + cbase + rowoff[r];
         if (JL > 0) {
@@ -1334,58 +1398,20 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
           float q[KB];
 #pragma unroll
           for (int b = 0; b < KB - 1; ++b) q[b] = qrow[b];
-          if (ST != 2 && g.bias_on && nonneg && bsm == nullptr) {
 #pragma unroll 1
-            for (int i0 = 0; i0 < JJ; i0 += IB) {
+          for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
-              for (int ii = 0; ii < IB; ++ii) {
-                const int i = i0 + ii;
-                q[KB - 1] = qrow[i + KB - 1];
-                const float pv = prow[i];
+            for (int ii = 0; ii < IB; ++ii) {
+              const int i = i0 + ii;
+              q[KB - 1] = qrow[i + KB - 1];
+              const float pv = prow[i];
 #pragma unroll
-                for (int b = 0; b < KB; ++b) {
-                  float df = __fsub_rn(q[b], pv);
-                  acc[b] = fmaf(df, df, acc[b]);
-                  bs[b] = __fadd_rn(bs[b], __fadd_rn(pv, q[b]));
-                }
-#pragma unroll
-                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
+              for (int b = 0; b < KB; ++b) {
+                float df = __fsub_rn(q[b], pv);
+                acc[b] = fmaf(df, df, acc[b]);
               }
-            }
-          } else if (ST != 2 && g.bias_on && bsm == nullptr) {
-#pragma unroll 1
-            for (int i0 = 0; i0 < JJ; i0 += IB) {
 #pragma unroll
-              for (int ii = 0; ii < IB; ++ii) {
-                const int i = i0 + ii;
-                q[KB - 1] = qrow[i + KB - 1];
-                const float pv = prow[i];
-#pragma unroll
-                for (int b = 0; b < KB; ++b) {
-                  float df = __fsub_rn(q[b], pv);
-                  acc[b] = fmaf(df, df, acc[b]);
-                  bs[b] = __fadd_rn(bs[b], fmaxf(__fadd_rn(pv, q[b]), 0.f));
-                }
-#pragma unroll
-                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
-              }
-            }
-          } else {
-#pragma unroll 1
-            for (int i0 = 0; i0 < JJ; i0 += IB) {
-#pragma unroll
-              for (int ii = 0; ii < IB; ++ii) {
-                const int i = i0 + ii;
-                q[KB - 1] = qrow[i + KB - 1];
-                const float pv = prow[i];
-#pragma unroll
-                for (int b = 0; b < KB; ++b) {
-                  float df = __fsub_rn(q[b], pv);
-                  acc[b] = fmaf(df, df, acc[b]);
-                }
-#pragma unroll
-                for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
-              }
+              for (int b = 0; b < KB - 1; ++b) q[b] = q[b + 1];
             }
           }
         } else {
