@@ -1347,7 +1347,22 @@ __device__ __forceinline__ int warp_match(const DGeom &g, const float *__restric
   }
   const float kmar = (exact || (pmetric && !pfix)) ? 0.f : 3.f * g.ku;
   int iters = (total + 31) / 32;
-  for (int it = 0; it < iters; ++it) {
+  // the iterations from the one holding the reference outwards, alternating
+  // after and before it: near candidates tend to score low, so the offer
+  // threshold falls early (the list is the same in any order)
+  int itc;
+  {
+    const int oref = ridx / WL;
+    itc = min((oref * nchk + (ridx - oref * WL) / KB) / 32, iters - 1);
+  }
+  for (int s = 0, nlo = itc - 1, nhi = itc + 1; s < iters; ++s) {
+    int it = itc;
+    if (s > 0) {
+      bool up = (s & 1) != 0;
+      if (up && nhi >= iters) up = false;
+      if (!up && nlo < 0) up = true;
+      it = up ? nhi++ : nlo--;
+    }
     int c = it * 32 + lane;
     float key[KB];
     int idx[KB];
@@ -3372,7 +3387,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
 // Sum the partials of the tiles covering every location in tile order and
 // normalize (Def. "Weighted overlap-add estimate").  Locations without weight
 // keep the observation.  If write_eta, the denominator is stored as well.
-template <int D>
+template <int D, int K>
 __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total, int write_eta) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -3414,10 +3429,9 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
       tcur[d] = l;
       if (l > h) any = false;
     }
-    // partials in ascending tile order, eight covering tiles per step: their
-    // offsets come from an odometer over the covering tile ranges and all
-    // eight loads are issued before any is added, so that their latencies
-    // overlap
+    // partials in ascending tile order, K covering tiles per step: their
+    // offsets come from an odometer over the covering tile ranges and all K
+    // loads are issued before any is added, so that their latencies overlap
     int NT[D], CC[D], off[D], rs[D];  // the job's geometry in registers
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -3431,10 +3445,10 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
     float num = 0.f, den = 0.f;
     bool more = any;
     while (more) {
-      float2 v[8];
+      float2 v[K];
       unsigned valid = 0u;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < K; ++k) {
         v[k] = make_float2(0.f, 0.f);
         if (more) {
           int tile = 0, local = 0;
@@ -3455,7 +3469,7 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
         }
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < K; ++k) {
         if ((valid >> k) & 1u) {
           num += v[k].x;
           den += v[k].y;
@@ -3615,12 +3629,12 @@ void launch_ref_base(const int *count, int ntiles, int *ref_base, cudaStream_t s
 void launch_reduce(int D, const DJob *jobs, int njobs, int64_t total, int write_eta, int grid,
                    cudaStream_t st) {
   switch (D) {
-    case 1: k_reduce<1><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
-    case 2: k_reduce<2><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
-    case 3: k_reduce<3><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
-    case 4: k_reduce<4><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
-    case 5: k_reduce<5><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
-    case 6: k_reduce<6><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 1: k_reduce<1, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 2: k_reduce<2, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 3: k_reduce<3, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 4: k_reduce<4, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 5: k_reduce<5, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
+    case 6: k_reduce<6, 8><<<grid, 256, 0, st>>>(jobs, njobs, total, write_eta); break;
   }
 }
 
