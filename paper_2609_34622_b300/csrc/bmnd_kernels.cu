@@ -258,6 +258,13 @@ __device__ __noinline__ void dct_line_generic(float *__restrict__ buf, int base,
   }
 }
 
+// The optional DCT along the group axis: every entry's line of n members
+// (stride MS) of the warp's group buffer.
+__device__ __noinline__ void dct_group_axis(float *buf, int P, int MS, int n, int mode, int lane,
+                                            const int *__restrict__ vbuf, const float *__restrict__ tab) {
+  for (int v = lane; v < P; v += 32) dct_line_generic(buf, vbuf[v], MS, n, mode, tab);
+}
+
 // Dense transform of nlines lines of length J held in a warp's shared group
 // buffer: line l starts at base_of(l) with element stride st.  M is a J x J
 // row-major matrix in shared memory (forward, transposed-for-inverse or
@@ -545,6 +552,39 @@ __device__ __forceinline__ const float *axis_matrix(const float *mats, const int
 // (g.spatial).  mode 0: T, 1: the synthesis T^{-1} (T^T for the DCT),
 // 2: T.^2.  The DCT runs as register butterflies on power-of-two axes;
 // bior1.5 and other lengths as dense products with the shared matrices.
+// Dense transform along patch axis a of a compile-time cubic shape (the
+// non-orthonormal bior1.5 spatial transform, matrix M in shared memory),
+// every line of the n member patches.  Out of line: only arrays with that
+// transform take it, and inlined beside the butterflies it costs the stage
+// kernels registers.
+template <int D, int JC>
+__device__ __noinline__ void dense_axis_fixed(float *buf, int n, int a, const float *M, int lane) {
+  using SH = CubeShape<D, JC>;
+  constexpr int per = SH::P / JC;  // lines per member along any axis
+  int bs[D];
+  {
+    int s = 1;
+#pragma unroll
+    for (int e = D - 1; e >= 0; --e) {
+      if (e == D - 1) { bs[e] = 1; s = SH::LS; }
+      else { bs[e] = s; s *= JC; }
+    }
+  }
+  auto base_of = [&](int l) {
+    int m = l / per, li = l - m * per;
+    int base = m * SH::MS, rem = li;
+#pragma unroll
+    for (int e = D - 1; e >= 0; --e) {
+      if (e == a) continue;
+      int c = rem % JC;
+      rem /= JC;
+      base += c * bs[e];
+    }
+    return base;
+  };
+  xform_lines<JC>(buf, n * per, base_of, bs[a], M, lane);
+}
+
 template <int D, int JC>
 __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, int mode, int lane, const int *vbuf,
                             const float *mats, const int *moff, const float *tab) {
@@ -582,7 +622,13 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
     const float *M = axis_matrix(mats, moff, a, ja, mode);
     const int nl = n * per, st = bs[a];
     const bool vec4 = a == D - 1 && (LS & 3) == 0;
-    if ((ja & (ja - 1)) == 0 && !g.spatial) {
+    if constexpr (SH::fixed) {
+      if (g.spatial) {
+        dense_axis_fixed<D, JC>(buf, n, a, M, lane);
+        continue;
+      }
+    }
+    if ((ja & (ja - 1)) == 0 && (SH::fixed || !g.spatial)) {
       // power-of-two length: register butterflies, one lane per line
 #pragma unroll 1
       for (int l = lane; l < nl; l += 32) {
@@ -615,11 +661,12 @@ __device__ __forceinline__ void group_xform(float *buf, const DGeom &g, int n, i
     }
   }
   // group axis
-  if (n > 1) {
+  if (n > 1 && g.gtrans == 1) {
+    dct_group_axis(buf, P, MS, n, mode, lane, vbuf, tab);
+  } else if (n > 1) {
 #pragma unroll 1
     for (int v = lane; v < P; v += 32) {
       const int base = vbuf[v];
-      if (g.gtrans == 1) { dct_line_generic(buf, base, MS, n, mode, tab); continue; }
       switch (n) {
         case 2: haar_line_mode<2>(buf, base, MS, mode); break;
         case 4: haar_line_mode<4>(buf, base, MS, mode); break;
@@ -2061,8 +2108,9 @@ __device__ __forceinline__ void gather_global(const float *__restrict__ a, const
 // d_g = zeta^T (y_g - p_g), and the sweep adds alpha = d_g / zeta^T 1 to
 // every synthesized entry.  p_g: syn[m * MS + vbuf[v]] (vbuf null: column v).
 // Entries are visited lane + 32 k in (member, entry) order on every path.
+// Out of line: only the second sweep takes it.
 template <int D, int PC>
-__device__ __forceinline__ float mc_alpha(const DGeom &g, int n, int lane, const int *__restrict__ mem,
+__device__ __noinline__ float mc_alpha(const DGeom &g, int n, int lane, const int *__restrict__ mem,
                                           const int *__restrict__ vreg, const int *__restrict__ vbuf,
                                           const float *__restrict__ omega, const float *__restrict__ wts,
                                           const float *__restrict__ syn, int MS, const float *__restrict__ Sy,
@@ -2090,6 +2138,54 @@ __device__ __forceinline__ float mc_alpha(const DGeom &g, int n, int lane, const
   dg = warp_sum(dg);
   z1 = warp_sum(z1);
   return z1 > 0.f ? dg / z1 : 0.f;
+}
+
+// Aggregation weight sum of member `lane` from the plane sums r_l in rr_s:
+// group scope sum_l r_l, or patch scope sum_l |V_jl|^2 r_l with
+// the group-axis DCT.  Out of line: the Haar patch scope is the common case.
+__device__ __noinline__ float group_weight_sum(const DGeom &g, int n, int lane, const float *rr_s,
+                                               const float *__restrict__ tab) {
+  float R = 0.f;
+  if (g.wscope == 1) {
+    for (int l = 0; l < n; ++l) R += rr_s[l];
+  } else {
+    const float *Mt = tab + gen_off(n);
+    for (int l = 0; l < n; ++l) {
+      const float c = __ldg(Mt + l * n + lane);
+      R += c * c * rr_s[l];
+    }
+  }
+  return R;
+}
+
+// Stage-1 soft thresholding (Eq. soft-threshold) of the group coefficients
+// in bufB (variances in bufA when varT, else var_g), as an attenuation
+// att = [|X| - lambda sigma]_+ / |X|: bufB receives att X, bufA the weight
+// term att^2 (times sigma^2 unless wmodel is 0).  Out of line: inlined beside
+// the hard threshold it costs the stage kernels registers.
+__device__ __noinline__ void soft_threshold_group(int n, int P, int MS, int lane, const int *__restrict__ vbuf,
+                                                  float *bufA, float *bufB, bool varT, float var_g, float lambda,
+                                                  int wmodel) {
+  BMND_FOR_ENTRIES({
+    const int a = m * MS + vbuf[v];
+    const float X = bufB[a];
+    const float s2 = varT ? bufA[a] : var_g;
+    const float ax = fabsf(X);
+    const float t = lambda * sqrtf(s2);
+    const float att = ax > t ? (ax - t) / ax : 0.f;
+    bufB[a] = att * X;
+    bufA[a] = att * att * (wmodel == 0 ? 1.f : s2);
+  });
+}
+
+// Windowed synthesis weights (Def. "Windowed synthesis metrics"): every
+// weight term in bufA times the diagonal factor of its spatial coefficient.
+__device__ __noinline__ void windowed_weight_terms(const DGeom &g, int n, int P, int MS, int lane,
+                                                   const int *__restrict__ vbuf, float *bufA) {
+  BMND_FOR_ENTRIES({
+    const int a = m * MS + vbuf[v];
+    bufA[a] *= syn_energy(g, v);
+  });
 }
 
 // Settles the hard-threshold coefficients that FP32 left undecided in the
@@ -2255,15 +2351,7 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       // entry number vis of this lane
       auto shrink = [&](int m, int v, int a, float X, float s2, int vis) {
         float wterm;
-        if (!stage2 && soft) {
-          // Eq. (soft-threshold) as an attenuation att = [|X| - lambda
-          // sigma]_+ / |X|; weight terms |att|^2 (times sigma^2)
-          const float ax = fabsf(X);
-          const float t = lambda * sqrtf(s2);
-          const float att = ax > t ? (ax - t) / ax : 0.f;
-          bufB[a] = att * X;
-          wterm = att * att * (wmodel == 0 ? 1.f : s2);
-        } else if (!stage2) {
+        if (!stage2) {
           // |X| > lambda sigma; undecided in FP32: kept until settled
           int kp = ht_decide32(X, s2, lam2, eX, m < kex ? eS0 + eSx : eS0);
           if (kp < 0) {
@@ -2279,7 +2367,6 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
           bufB[a] = G;
           wterm = wmodel == 0 ? G * G : (wmodel == 1 ? G * G * s2 : G * G * s2 + (1.f - G) * (1.f - G) * S);
         }
-        if (wdomain) wterm *= syn_energy(g, v);
         bufA[a] = wterm;
       };
       if constexpr (SH::fixed && SH::P % 32 == 0 && ST == 2) {
@@ -2310,6 +2397,8 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
               if (h == 0 || two)
                 shrink(m0 + h, lane + 32 * k, (m0 + h) * MS + vb[k], Xv[h][k], Sv[h][k], (m0 + h) * KV + k);
         }
+      } else if (!stage2 && soft) {
+        soft_threshold_group(n, P, MS, lane, vbuf, bufA, bufB, varT, var_g, lambda, wmodel);
       } else {
         BMND_FOR_ENTRIES({
           const int a = m * MS + vbuf[v];
@@ -2320,6 +2409,10 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       if (hard && __any_sync(0xffffffffu, undecided != 0ull))
         smem_ht_settle(g, n, P, MS, lane, undecided, mem, vreg, vbuf, Sg, bufA, bufB);
       __syncwarp();
+      if (wdomain) {
+        windowed_weight_terms(g, n, P, MS, lane, vbuf, bufA);
+        __syncwarp();
+      }
       // ---- r_l = sum_q (term) for every group-axis plane l (lane l sums
       // its row, starting at its own entry so the reads spread over banks;
       // four partial sums, so that the adds do not wait on one another) ----
@@ -2347,17 +2440,11 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
       // ---- weights: patch scope R_j = sum_l |V_jl|^2 r_l, group scope sum_l r_l
       if (lane < n) {
         float R = 0.f;
-        if (g.wscope == 1) {
-          for (int l = 0; l < n; ++l) R += rr_s[l];
-        } else if (g.gtrans == 0) {
+        if (g.wscope == 0 && g.gtrans == 0) {
           R = rr_s[0] / (float)n;
           for (int bb = n; bb >= 2; bb >>= 1) R += rr_s[n / bb + lane / bb] / (float)bb;
         } else {
-          const float *Mt = tab + gen_off(n);
-          for (int l = 0; l < n; ++l) {
-            const float c = __ldg(Mt + l * n + lane);
-            R += c * c * rr_s[l];
-          }
+          R = group_weight_sum(g, n, lane, rr_s, tab);
         }
         wts[lane] = R > 0.f ? 1.f / R : 1.f;
       }
@@ -2499,29 +2586,45 @@ __device__ __forceinline__ unsigned col_hard_threshold(const DGeom &g, float *bu
 #pragma unroll
     for (int m = 0; m < N; ++m) S[m] = g.var_g;
   }
-  if (g.soft) {
-    // Eq. (soft-threshold) as an attenuation att = [|X| - lambda sigma]_+ /
-    // |X|; weight terms |att|^2 (times sigma^2)
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-      const float ax = fabsf(X[m]), t = g.lambda * sqrtf(S[m]);
-      const float att = ax > t ? (ax - t) / ax : 0.f;
-      bufA[m * MS + v] = att * att * (g.wmodel == 0 ? 1.f : S[m]);
-      X[m] = att * X[m];
-    }
-  } else {
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      // |X| > lambda sigma; undecided in FP32: kept until col_ht_settle
-      const int kp = ht_decide32(X[m], S[m], lam2, eX, m < g.kex ? eS0 + eSx : eS0);
-      if (kp < 0) undecided |= 1u << m;
-      bufA[m * MS + v] = kp ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
-      X[m] = kp ? X[m] : 0.f;
-    }
+  for (int m = 0; m < N; ++m) {
+    // |X| > lambda sigma; undecided in FP32: kept until col_ht_settle
+    const int kp = ht_decide32(X[m], S[m], lam2, eX, m < g.kex ? eS0 + eSx : eS0);
+    if (kp < 0) undecided |= 1u << m;
+    bufA[m * MS + v] = kp ? (g.wmodel == 0 ? 1.f : S[m]) : 0.f;
+    X[m] = kp ? X[m] : 0.f;
   }
   haar_inv_levels<N, 2>(X);
   col_store<N, MS>(bufB, v, X);
   return undecided;
+}
+
+// Stage 1 with soft thresholding, one column (as col_hard_threshold): Eq.
+// (soft-threshold) as an attenuation att = [|X| - lambda sigma]_+ / |X|,
+// weight terms |att|^2 (times sigma^2).  Out of line: inlined beside the
+// hard threshold it costs the stage kernels registers.
+template <int N, int MS>
+__device__ __noinline__ void col_soft_threshold(const DGeom &g, float *bufA, float *bufB, int v, float4 cx) {
+  float X[N], S[N];
+  col_load<N, MS>(X, bufB, v);
+  haar_fwd_levels<N, N, false>(X);
+  if (g.poisson) {
+    col_load<N, MS>(S, bufA, v);
+    haar_fwd_levels<N, N, true>(S);
+    add_shared_source<N>(S, cx);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) S[m] = g.var_g;
+  }
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const float ax = fabsf(X[m]), t = g.lambda * sqrtf(S[m]);
+    const float att = ax > t ? (ax - t) / ax : 0.f;
+    bufA[m * MS + v] = att * att * (g.wmodel == 0 ? 1.f : S[m]);
+    X[m] = att * X[m];
+  }
+  haar_inv_levels<N, 2>(X);
+  col_store<N, MS>(bufB, v, X);
 }
 
 // Drops the planes in `drop` from the stored column v (H^T of the kept
@@ -2724,11 +2827,18 @@ __device__ __forceinline__ int filter_group_rf(const DGeom &g, int n, bool mc2, 
   if (!stage2) {
     const float lam2 = g.lambda * g.lambda;
     // one column per lane (P <= 32): the undecided planes of column `lane`
-    unsigned undecided = 0u;
-#define BMND_OP(NN) undecided = col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2, eX, eS0, cx, eSx)
-    BMND_COLUMNS(BMND_OP)
+    if (g.soft) {
+#define BMND_OP(NN) col_soft_threshold<NN, MS>(g, bufA, bufB, v, cx)
+      BMND_COLUMNS(BMND_OP)
 #undef BMND_OP
-    if (__any_sync(0xffffffffu, undecided != 0u)) rf_ht_settle<MS>(g, n, lane, undecided, mem, vreg, Sg, bufA, bufB);
+    } else {
+      unsigned undecided = 0u;
+#define BMND_OP(NN) undecided = col_hard_threshold<NN, MS>(g, bufA, bufB, v, lam2, eX, eS0, cx, eSx)
+      BMND_COLUMNS(BMND_OP)
+#undef BMND_OP
+      if (__any_sync(0xffffffffu, undecided != 0u))
+        rf_ht_settle<MS>(g, n, lane, undecided, mem, vreg, Sg, bufA, bufB);
+    }
   } else {
 #define BMND_OP(NN) col_wiener_gain<NN, MS>(g, bufA, bufB, v, cx)
     BMND_COLUMNS(BMND_OP)
@@ -2862,6 +2972,93 @@ __device__ SmemLayout smem_layout(unsigned char *smem, const DGeom &g, bool stag
 // mode 1: match only, group tables written; mode 2: mass-conservation sweep 2
 // (groups read back, corrected patches aggregated with the sweep-1 weights).
 // Persistent: each CTA takes tiles from *counter until all are done.
+// Adds the group's weighted synthesized patches to dst in member order
+// (Def. "Weighted overlap-add estimate"): member m's entry v (synthesized
+// value syn[m MS + vbuf[v]]) at dst[mbase[m] + eoff[v]], numerator
+// w_m omega_v (value + alpha), denominator w_m omega_v; the warp's lanes
+// over the entries (distinct locations), one member after another.  PF:
+// the patch size when it is a compile-time multiple of 32, else 0.
+template <int PF>
+__device__ __forceinline__ void add_members_to(float2 *dst, const int *mbase, const int *__restrict__ eoff, int n,
+                                               int P, int MS, int lane, const float *syn, const float *wts,
+                                               float alpha, const float *__restrict__ omega,
+                                               const int *__restrict__ vbuf) {
+  if constexpr (PF > 0) {
+    constexpr int KV = PF / 32;
+    int eo[KV], vb[KV];
+    float om[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+      eo[k] = eoff[lane + 32 * k];
+      vb[k] = vbuf[lane + 32 * k];
+      om[k] = omega[lane + 32 * k];
+    }
+    for (int m = 0; m < n; ++m) {
+      const int b = mbase[m];
+      const float wm = wts[m];
+      const float *sr = syn + m * MS;
+#pragma unroll
+      for (int k = 0; k < KV; ++k) {
+        const float wo = wm * om[k];
+        float2 t = dst[b + eo[k]];
+        t.x = fmaf(wo, sr[vb[k]] + alpha, t.x);
+        t.y += wo;
+        dst[b + eo[k]] = t;
+      }
+      __syncwarp();
+    }
+  } else {
+    for (int m = 0; m < n; ++m) {
+      const int b = mbase[m];
+      const float wm = wts[m];
+      const float *sr = syn + m * MS;
+      for (int v = lane; v < P; v += 32) {
+        const float wo = wm * omega[v];
+        float2 t = dst[b + eoff[v]];
+        t.x = fmaf(wo, sr[vbuf[v]] + alpha, t.x);
+        t.y += wo;
+        dst[b + eoff[v]] = t;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Private footprint of one reference (local index rl in its tile): the box
+// [core, core + 2 rad + j - 1] holds every member patch; lvl[m] receives
+// member m's offset in the box, the box (fpb, g.fp entries) the group's
+// weighted patches.  Returns the box's offset in the tile region.  Out of
+// line: inlined it costs the stage kernels registers.
+template <int D, int PF>
+__device__ __noinline__ int fp_export(const DGeom &g, int rl, int n, int P, int MS, int lane, const int *mem,
+                                      int *lvl, float2 *fpb, const int *__restrict__ fvoff, const float *syn,
+                                      const float *wts, float alpha, const float *__restrict__ omega,
+                                      const int *__restrict__ vbuf) {
+  int c[D];
+  {
+    int rem = rl;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) { c[d] = rem % g.C[d]; rem /= g.C[d]; }
+  }
+  int boxbase = 0;
+#pragma unroll
+  for (int d = D - 1; d >= 0; --d) boxbase += c[d] * g.rst[d];
+  if (lane < n) {
+    int rem = mem[lane], fo = 0, fs = 1;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) {
+      fo += (rem % g.RGP[d] - c[d]) * fs;
+      rem /= g.RGP[d];
+      fs *= g.FW[d];
+    }
+    lvl[lane] = fo;
+  }
+  for (int f = lane; f < g.fp; f += 32) fpb[f] = make_float2(0.f, 0.f);
+  __syncwarp();
+  add_members_to<PF>(fpb, lvl, fvoff, n, P, MS, lane, syn, wts, alpha, omega, vbuf);
+  return boxbase;
+}
+
 template <int D, int JL, int KB, int MINB, int ST>
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, const float *__restrict__ tab,
@@ -3286,73 +3483,11 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
       // ---- accumulation in the members' order: the warp adds one member
       // after another, lanes over its patch entries (distinct locations), so
       // every location receives its contributions in member order ----
-      auto add_members = [&](float2 *dst, const int *mbase, const int *eoff) {
-        if constexpr (SH::fixed && SH::P % 32 == 0) {
-          constexpr int KV = SH::P / 32;
-          int eo[KV], vb[KV];
-          float om[KV];
-#pragma unroll
-          for (int k = 0; k < KV; ++k) {
-            eo[k] = eoff[lane + 32 * k];
-            vb[k] = vbuf[lane + 32 * k];
-            om[k] = omega[lane + 32 * k];
-          }
-          for (int m = 0; m < n; ++m) {
-            const int b = mbase[m];
-            const float wm = wts[m];
-            const float *sr = syn + m * MS;
-#pragma unroll
-            for (int k = 0; k < KV; ++k) {
-              const float wo = wm * om[k];
-              float2 t = dst[b + eo[k]];
-              t.x = fmaf(wo, sr[vb[k]] + alpha, t.x);
-              t.y += wo;
-              dst[b + eo[k]] = t;
-            }
-            __syncwarp();
-          }
-        } else {
-          for (int m = 0; m < n; ++m) {
-            const int b = mbase[m];
-            const float wm = wts[m];
-            const float *sr = syn + m * MS;
-            for (int v = lane; v < P; v += 32) {
-              const float wo = wm * omega[v];
-              float2 t = dst[b + eoff[v]];
-              t.x = fmaf(wo, sr[vbuf[v]] + alpha, t.x);
-              t.y += wo;
-              dst[b + eoff[v]] = t;
-            }
-            __syncwarp();
-          }
-        }
-      };
+      constexpr int PF = (SH::fixed && SH::P % 32 == 0) ? SH::P : 0;
       int boxbase = 0;
-      if (has && g.fp) {
-        // private footprint: the box [core, core + 2 rad + j - 1] of the
-        // reference holds every member patch; lvl[m] = offset of member m
-        int c[D];
-        {
-          int rem = sj->ref_local[tslot + ri];
-#pragma unroll
-          for (int d = D - 1; d >= 0; --d) { c[d] = rem % g.C[d]; rem /= g.C[d]; }
-        }
-#pragma unroll
-        for (int d = D - 1; d >= 0; --d) boxbase += c[d] * g.rst[d];
-        if (lane < n) {
-          int rem = mem[lane], fo = 0, fs = 1;
-#pragma unroll
-          for (int d = D - 1; d >= 0; --d) {
-            fo += (rem % g.RGP[d] - c[d]) * fs;
-            rem /= g.RGP[d];
-            fs *= g.FW[d];
-          }
-          lvl[lane] = fo;
-        }
-        for (int f = lane; f < g.fp; f += 32) fpb[f] = make_float2(0.f, 0.f);
-        __syncwarp();
-        add_members(fpb, lvl, L.fvoff);
-      }
+      if (has && g.fp)
+        boxbase = fp_export<D, PF>(g, sj->ref_local[tslot + ri], n, P, MS, lane, mem, lvl, fpb, L.fvoff, syn, wts,
+                                   alpha, omega, vbuf);
       // ---- ordered, atomic-free accumulation into the tile region ----
       if (!(warp == 0 && rd == 0)) named_sync(1 + warp, 64);
       if (has) {
@@ -3368,7 +3503,7 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             }
           }
         } else {
-          add_members(acc, mem, vreg);
+          add_members_to<PF>(acc, mem, vreg, n, P, MS, lane, syn, wts, alpha, omega, vbuf);
         }
       }
       __threadfence_block();
