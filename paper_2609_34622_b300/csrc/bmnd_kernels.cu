@@ -2355,8 +2355,10 @@ __device__ __forceinline__ int filter_group(const DGeom &g, int n, bool mc2, int
           // |X| > lambda sigma; undecided in FP32: kept until settled
           int kp = ht_decide32(X, s2, lam2, eX, m < kex ? eS0 + eSx : eS0);
           if (kp < 0) {
-            if (vis < 64) undecided |= 1ull << vis;
-            else kp = ht_keep64(g, n, m, v, mem, vreg, Sg) ? 1 : 0;  // past 64 visits: at once
+            // at most 64 visits per lane with compile-time patches of <= 64
+            // entries (32 members at most); past 64 visits: at once
+            if (vis < 64 || (SH::fixed && SH::P <= 64)) undecided |= 1ull << (vis & 63);
+            else kp = ht_keep64(g, n, m, v, mem, vreg, Sg) ? 1 : 0;
           }
           bufB[a] = kp ? X : 0.f;
           wterm = kp ? (wmodel == 0 ? 1.f : s2) : 0.f;
@@ -3059,6 +3061,108 @@ __device__ __noinline__ int fp_export(const DGeom &g, int rl, int n, int P, int 
   return boxbase;
 }
 
+// ---- mass-conservation sweeps: group tables and the synthesis cache.  Out
+// of line: only mass-conserving stages take them, and inlined they cost the
+// stage kernels registers. ----
+
+// Group-table entry `slot` (members' region offsets, -1 past the group).
+__device__ __noinline__ void export_group(const DJob *sj, int64_t slot, int M, int n, const int *mem, int lane) {
+  for (int m = lane; m < M; m += 32) sj->groups[slot * M + m] = m < n ? mem[m] : -1;
+  if (lane == 0) sj->gcount[slot] = n;
+}
+
+// Members of group-table entry `slot` into mem; returns the group size.
+__device__ __noinline__ int table_group_load(const DJob *sj, int64_t slot, int M, int lane, int *mem) {
+  const int n = sj->gcount[slot];
+  for (int m = lane; m < n; m += 32) mem[m] = sj->groups[slot * M + m];
+  __syncwarp();
+  return n;
+}
+
+// Second sweep from the cache, CQ float4 per lane: the group-table entry
+// `slot` (members into mem), the cached synthesis of reference cr (into
+// bufA, member rows at vbuf) and its weights, requested together.  Returns
+// the group size (0 for a reference without a cache slot).  P is a multiple
+// of 4.
+template <int CQ>
+__device__ __noinline__ int cached_group_load(const DJob *sj, int64_t slot, int64_t cr, int M, int P, int MS,
+                                              int lane, int *mem, float *wts, float *bufA,
+                                              const int *__restrict__ vbuf) {
+  const bool ok = cr < sj->pcache_refs;
+  const int gm = lane < M ? sj->groups[slot * M + lane] : 0;
+  const int gc = sj->gcount[slot];
+  const float wv = (ok && lane < M) ? sj->wcache[cr * M + lane] : 0.f;
+  const float4 *pc4 = reinterpret_cast<const float4 *>(sj->pcache + (ok ? cr : 0) * M * P);
+  const int nq = ok ? M * P / 4 : 0;
+  float4 q[CQ > 0 ? CQ : 1];
+#pragma unroll
+  for (int k = 0; k < CQ; ++k) {
+    const int i = lane + 32 * k;
+    q[k] = i < nq ? __ldg(pc4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int n = ok ? gc : 0;
+  if (lane < n) {
+    mem[lane] = gm;
+    wts[lane] = wv;
+  }
+#pragma unroll
+  for (int k = 0; k < CQ; ++k) {
+    const int e = 4 * (lane + 32 * k);
+    if (e < n * P) {
+      // the four entries belong to one member
+      const int m = e / P, v = e - m * P;
+      float *d = bufA + m * MS;
+      d[vbuf[v]] = q[k].x;
+      d[vbuf[v + 1]] = q[k].y;
+      d[vbuf[v + 2]] = q[k].z;
+      d[vbuf[v + 3]] = q[k].w;
+    }
+  }
+  __syncwarp();
+  return n;
+}
+
+// The cached synthesis of reference cr (n members of P entries) into bufA
+// and its weights into wts.
+__device__ __noinline__ void cached_synthesis_load(const DJob *sj, int64_t cr, int M, int n, int P, int MS,
+                                                   int lane, float *wts, float *bufA,
+                                                   const int *__restrict__ vbuf) {
+  const float *pc = sj->pcache + cr * M * P;
+  const int tot = n * P;
+  for (int e0 = 0; e0 < tot; e0 += 32 * 8) {
+    float t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + 32 * k + lane;
+      t[k] = e < tot ? __ldg(pc + e) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + 32 * k + lane;
+      if (e < tot) {
+        const int m = e / P, v = e - m * P;
+        bufA[m * MS + vbuf[v]] = t[k];
+      }
+    }
+  }
+  if (lane < n) wts[lane] = sj->wcache[cr * M + lane];
+  __syncwarp();
+}
+
+// First sweep: the synthesis (syn, member rows at vbuf) and weights of
+// reference cr into the cache.
+__device__ __noinline__ void export_synthesis(const DJob *sj, int64_t cr, int M, int n, int P, int MS, int lane,
+                                              const float *syn, const float *wts, const int *__restrict__ vbuf) {
+  float *pc = sj->pcache + cr * M * P;
+  int m = lane / P, v = lane - (lane / P) * P;
+  for (int e = lane; e < n * P; e += 32) {
+    pc[e] = syn[m * MS + vbuf[v]];
+    v += 32;
+    while (v >= P) { v -= P; ++m; }
+  }
+  if (lane < n) sj->wcache[cr * M + lane] = wts[lane];
+}
+
 template <int D, int JL, int KB, int MINB, int ST>
 __global__ void __launch_bounds__(NW * 32, MINB)
 k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, const float *__restrict__ tab,
@@ -3363,50 +3467,13 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
         if (!mc2) {
           n = warp_match<D, JL, KB, ST>(g, Sg, rr, org, rowoff, lane, mem, tile_nonneg, tile_exact, tile_emin,
                                         tile_span, tile_vmax, tile_counts, g.diag, use_bsm ? L.bsm : nullptr);
-          if (sj->groups) {
-            for (int m = lane; m < g.M; m += 32)
-              sj->groups[(tslot + ri) * g.M + m] = m < n ? mem[m] : -1;
-            if (lane == 0) sj->gcount[tslot + ri] = n;
-          }
+          if (sj->groups) export_group(sj, tslot + ri, g.M, n, mem, lane);
         } else if (CQ > 0 && cmode) {
           // second sweep from the cache: the group-table entry, the cached
-          // synthesis (float4) and the weights are requested together
-          const int64_t slot = tslot + ri, cr = (int64_t)tile_ref0 + ri;
-          const bool ok = cr < sj->pcache_refs;
-          const int gm = lane < g.M ? sj->groups[slot * g.M + lane] : 0;
-          const int gc = sj->gcount[slot];
-          const float wv = (ok && lane < g.M) ? sj->wcache[cr * g.M + lane] : 0.f;
-          const float4 *pc4 = reinterpret_cast<const float4 *>(sj->pcache + (ok ? cr : 0) * g.M * P);
-          const int nq = ok ? g.M * P / 4 : 0;
-          float4 q[CQ > 0 ? CQ : 1];
-#pragma unroll
-          for (int k = 0; k < CQ; ++k) {
-            const int i = lane + 32 * k;
-            q[k] = i < nq ? __ldg(pc4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-          n = ok ? gc : 0;
-          if (lane < n) {
-            mem[lane] = gm;
-            wts[lane] = wv;
-          }
-#pragma unroll
-          for (int k = 0; k < CQ; ++k) {
-            const int e = 4 * (lane + 32 * k);
-            if (e < n * P) {
-              // P is a multiple of 4: the four entries belong to one member
-              const int m = e / P, v = e - m * P;
-              float *d = bufA + m * MS;
-              d[vbuf[v]] = q[k].x;
-              d[vbuf[v + 1]] = q[k].y;
-              d[vbuf[v + 2]] = q[k].z;
-              d[vbuf[v + 3]] = q[k].w;
-            }
-          }
-          __syncwarp();
+          // synthesis and the weights
+          n = cached_group_load<CQ>(sj, tslot + ri, (int64_t)tile_ref0 + ri, g.M, P, MS, lane, mem, wts, bufA, vbuf);
         } else {
-          n = sj->gcount[tslot + ri];
-          for (int m = lane; m < n; m += 32) mem[m] = sj->groups[(tslot + ri) * g.M + m];
-          __syncwarp();
+          n = table_group_load(sj, tslot + ri, g.M, lane, mem);
         }
         if (mode != 1) {
           if (D >= 3 && leanx) {
@@ -3431,26 +3498,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
             // second sweep: the first sweep's synthesis and weights, then
             // only the correction alpha
             if (!cached) n = 0;
-            const float *pc = sj->pcache + (cached ? cr : 0) * g.M * P;
-            const int tot = CQ > 0 ? 0 : n * P;  // CQ > 0: loaded with the group
-            for (int e0 = 0; e0 < tot; e0 += 32 * 8) {
-              float t[8];
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const int e = e0 + 32 * k + lane;
-                t[k] = e < tot ? __ldg(pc + e) : 0.f;
-              }
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const int e = e0 + 32 * k + lane;
-                if (e < tot) {
-                  const int m = e / P, v = e - m * P;
-                  bufA[m * MS + vbuf[v]] = t[k];
-                }
-              }
-            }
-            if (CQ == 0 && lane < n) wts[lane] = sj->wcache[cr * g.M + lane];
-            __syncwarp();
+            // CQ > 0: loaded with the group
+            if (CQ == 0) cached_synthesis_load(sj, cached ? cr : 0, g.M, n, P, MS, lane, wts, bufA, vbuf);
             syn = bufA;
             alpha = mc_alpha<D, SH::P>(g, n, lane, mem, vreg, vbuf, omega, wts, syn, MS, Sg, Se, sj->y, sj->eta,
                                        gb, L.vgl, false);
@@ -3465,17 +3514,8 @@ k_stage(const DJob *__restrict__ jobs, int njobs, int total_tiles, int mode, con
                                           rr_s, L.mats, L.moff, L.vcrd, tab, sj->y, sj->eta, gb, L.vgl, &alpha,
                                           g.diag);
             syn = which ? bufA : bufB;
-            if (!mc2 && cached && sj->groups) {
-              // first sweep of a mass-conserving stage: keep the synthesis
-              float *pc = sj->pcache + cr * g.M * P;
-              int m = lane / P, v = lane - (lane / P) * P;
-              for (int e = lane; e < n * P; e += 32) {
-                pc[e] = syn[m * MS + vbuf[v]];
-                v += 32;
-                while (v >= P) { v -= P; ++m; }
-              }
-              if (lane < n) sj->wcache[cr * g.M + lane] = wts[lane];
-            }
+            // first sweep of a mass-conserving stage: keep the synthesis
+            if (!mc2 && cached && sj->groups) export_synthesis(sj, cr, g.M, n, P, MS, lane, syn, wts, vbuf);
           }
         }
       }
