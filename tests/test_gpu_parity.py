@@ -261,14 +261,15 @@ def test_full_size_1d_sampled(ctx, oracle):
     ctx.bmnd_denoise(y, full, cfg["noise"], cfg["patch"], cfg["step"], cfg["search"], (16, 32), 2, 0)
     np.testing.assert_array_equal(full.cpu().numpy(), out.cpu().numpy())
     rng = np.random.default_rng(61)
-    pts = np.concatenate([[0, 1, 262143, 262112], rng.integers(0, 262144, 60)])
+    pts = np.concatenate([[0, 1, 2, 3, 262143, 262142, 262112, 262111], rng.integers(0, 262144, 2040)])
     pl = pilot.cpu().numpy().astype(np.float64)
     r1 = oracle.stage_points(p, job.y, None, 1, pts)
     r2 = oracle.stage_points(p, job.y, pl, 2, pts)
     g1 = pl[pts]
     g2 = out.cpu().numpy().astype(np.float64)[pts]
-    assert np.sum(np.abs(g1 - r1) > 1e-4) <= 1, np.abs(g1 - r1).max()
-    assert np.sum(np.abs(g2 - r2) > 1e-4) <= 1, np.abs(g2 - r2).max()
+    # the voxel contract on the samples: at least 99.9 % within 1e-4
+    PT.assert_voxels(g1, r1, 1.0, what="1-D stage 1 at %d samples" % len(pts))
+    PT.assert_voxels(g2, r2, 1.0, what="1-D stage 2 at %d samples" % len(pts))
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
