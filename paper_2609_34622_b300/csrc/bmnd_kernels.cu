@@ -3604,19 +3604,31 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
       tcur[d] = l;
       if (l > h) any = false;
     }
-    // partials in ascending tile order, K covering tiles per step: their
-    // offsets come from an odometer over the covering tile ranges and all K
-    // loads are issued before any is added, so that their latencies overlap
-    int NT[D], CC[D], off[D], rs[D];  // the job's geometry in registers
+    // partials in ascending tile order, K covering tiles per step, all K
+    // loads issued before any is added so that their latencies overlap.  The
+    // covering tiles are walked by an odometer over their ranges (last axis
+    // fastest) that moves a pointer: one step along axis d moves it by
+    // step[d] (the next tile's partial, less the core width in the region),
+    // a wrap of axis d back by back[d]
+    const float2 *__restrict__ p;
+    int64_t step[D], back[D];
+    {
+      int64_t ts = g.region;  // partial-buffer distance of neighbouring tiles along axis d
+      int tile = 0;
+      int64_t local = 0;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      NT[d] = g.NT[d];
-      CC[d] = g.C[d];
-      off[d] = uc[d] + g.rad[d];
-      rs[d] = g.rst[d];
+      for (int d = D - 1; d >= 0; --d) {
+        step[d] = ts - (int64_t)g.C[d] * g.rst[d];
+        back[d] = (int64_t)(thi[d] - tlo[d]) * step[d];
+        ts *= g.NT[d];
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        tile = tile * g.NT[d] + tcur[d];
+        local += (int64_t)(uc[d] + g.rad[d] - tcur[d] * g.C[d]) * g.rst[d];
+      }
+      p = J.partial + (int64_t)tile * g.region + local;
     }
-    const int64_t region = g.region;
-    const float2 *__restrict__ part = J.partial;
     float num = 0.f, den = 0.f;
     bool more = any;
     while (more) {
@@ -3626,21 +3638,21 @@ __global__ void k_reduce(const DJob *__restrict__ jobs, int njobs, int64_t total
       for (int k = 0; k < K; ++k) {
         v[k] = make_float2(0.f, 0.f);
         if (more) {
-          int tile = 0, local = 0;
-#pragma unroll
-          for (int d = 0; d < D; ++d) {
-            tile = tile * NT[d] + tcur[d];
-            local += (off[d] - tcur[d] * CC[d]) * rs[d];
-          }
-          v[k] = part[(int64_t)tile * region + local];
+          v[k] = *p;
           valid |= 1u << k;
           int d = D - 1;
-          while (d >= 0) {
-            if (++tcur[d] <= thi[d]) break;
+          while (true) {
+            if (++tcur[d] <= thi[d]) {
+              p += step[d];
+              break;
+            }
             tcur[d] = tlo[d];
-            --d;
+            p -= back[d];
+            if (--d < 0) {
+              more = false;
+              break;
+            }
           }
-          more = d >= 0;
         }
       }
 #pragma unroll
